@@ -1,0 +1,425 @@
+/*
+ * FP64 CPU oracle of the two-species lattice Boltzmann model with multirange
+ * Shan-Chen interactions (Benzi, Bernaschi, Sbragaglia, Succi, "Herschel-Bulkley
+ * rheology from lattice kinetic theory of soft-glassy materials").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain definition the CUDA
+ * path is checked against.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load it.  It shares no code, header, table or
+ * constant generator with the CUDA library; the two only receive the same input
+ * arrays.
+ *
+ * Every step follows the paper's statement of the model, in the paper's order:
+ *   Eq. (be)  f_is(r+c_i,t+1) - f_is(r,t) = -(1/tau)[f_is - f^eq_is(rho_s, u + tau F_s/rho_s)]
+ *   moments   rho_s = sum_i f_is,  u = sum_s sum_i f_is c_i / sum_s rho_s
+ *   f^eq      w_i rho_s (1 + u.c/cs^2 + uu:(cc - cs^2 I)/(2 cs^4)),  cs^2 = 1/3
+ *   Eq. (FFF) F_s = F^a_s + F^r_s + F^X_s with
+ *             F^{a,r}_s = -G^{a,r}_s psi_s(r) sum_{i in b1,b2} w_i c_i psi_s(r+c_i)
+ *             F^X_s     = -(G_AB/rho0) rho_s(r) sum_{i in b1} w_i c_i rho_s'(r+c_i)
+ *   psi(rho) = rho0 (1 - exp(-rho/rho0))  (Shan-Chen form, Section "Lattice
+ *             Boltzmann with multirange interactions").
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *  - populations live on D2Q9; the 25 velocities of Fig. 1 are the interaction
+ *    stencil only (c_s^2 = 1/3 holds for the D2Q9 weights);
+ *  - belt-1 interaction weights are the standard D2Q9 weights the paper names,
+ *    1/9 (|c|^2=1) and 1/36 (|c|^2=2); the two-belt weights are the 25-velocity
+ *    set 4/63, 4/135, 1/180, 2/945, 1/15120 for |c|^2 = 1,2,4,5,8 (the paper
+ *    defers them to its ref. [JCPnoi]).  Both sets have sum w c_x^2 = 1/3 = cs^2,
+ *    and their fourth moments sum w c_x^2 c_y^2 are in the ratio 12/7 that the
+ *    surface-tension combination G^a + (12/7) G^r of the paper requires;
+ *  - G < 0 attracts, G > 0 repels (from the formula; the footnote's wording is
+ *    reversed); G_BA = G_AB; the same rho0 enters psi and F^X;
+ *  - order inside a step: moments and forces from the post-streaming state,
+ *    collision, then streaming;
+ *  - Couette walls (not in the paper): halfway bounce-back with a moving-wall
+ *    term, walls at y=-1/2 (x-velocity -U) and y=ny-1/2 (+U); the interaction
+ *    stencil sees mirror ghosts psi(x,-k) = psi(x,k-1), rho likewise;
+ *  - sampled observables: physical velocity (j + F/2)/rho, wall x-momentum
+ *    delivered by bounce-back per step (Pi_top, Pi_bot).
+ *
+ * Layout of a population array: [species s=0(A),1(B)][i=0..8][y][x], x fastest.
+ * D2Q9 order: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no FMA contraction).
+ * Per-site loops may run on several OpenMP threads; every sum over sites is
+ * taken in one fixed sequential order, so results do not depend on the thread
+ * count.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int nx, ny;
+    double tau, rho0;
+    double g_aa1, g_aa2, g_bb1, g_bb2, g_ab;
+    double u_wall;
+    int bc; /* 0: periodic in x and y; 1: Couette (periodic x, walls in y) */
+} orc_params;
+
+/* Per-step observables of one sampled step (all FP64). */
+typedef struct {
+    double mass[2];      /* sum over sites of rho_A, rho_B (pre-collision) */
+    double mom[2];       /* sum over sites of j_x, j_y (raw, pre-collision) */
+    double pi_top;       /* x-momentum delivered by the top wall in this step */
+    double pi_bot;       /* x-momentum delivered by the bottom wall in this step */
+} orc_obs;
+
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                            1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+/* Interaction weights by squared length |c|^2 of the stencil vector. */
+static double belt1_weight(int c2)
+{
+    if (c2 == 1) return 1.0 / 9.0;
+    if (c2 == 2) return 1.0 / 36.0;
+    return 0.0;
+}
+static double belt2_weight(int c2)
+{
+    switch (c2) {
+    case 1: return 4.0 / 63.0;
+    case 2: return 4.0 / 135.0;
+    case 4: return 1.0 / 180.0;
+    case 5: return 2.0 / 945.0;
+    case 8: return 1.0 / 15120.0;
+    default: return 0.0;
+    }
+}
+
+/* Exposed so tests can check the tables against what the paper fixes. */
+double orc_belt_weight(int belt, int cx, int cy)
+{
+    int c2 = cx * cx + cy * cy;
+    return belt == 1 ? belt1_weight(c2) : belt2_weight(c2);
+}
+
+#define IDX(p, x, y) ((size_t)(y) * (size_t)(p)->nx + (size_t)(x))
+#define FIDX(p, s, i, x, y) ((((size_t)(s) * 9 + (size_t)(i)) * (size_t)(p)->ny + (size_t)(y)) * (size_t)(p)->nx + (size_t)(x))
+
+static int wrap(int a, int n)
+{
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Row seen by the interaction stencil at row y+dy: periodic, or mirrored across
+ * the walls at y=-1/2 and y=ny-1/2 (Couette). */
+static int stencil_row(const orc_params* p, int y)
+{
+    if (p->bc == 0) return wrap(y, p->ny);
+    if (y < 0) return -y - 1;
+    if (y >= p->ny) return 2 * p->ny - y - 1;
+    return y;
+}
+
+/* psi(rho) = rho0 (1 - exp(-rho/rho0)), written as -rho0*expm1(-rho/rho0). */
+static double psi_of(double rho, double rho0) { return -rho0 * expm1(-rho / rho0); }
+
+/* psi(rho)/rho with its limit 1 at rho -> 0. */
+static double psi_over_rho(double rho, double rho0)
+{
+    if (rho == 0.0) return 1.0;
+    return -rho0 * expm1(-rho / rho0) / rho;
+}
+
+static void set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* f_is = f^eq_is(rho_s, u) at every site.  ux/uy may be NULL (u = 0). */
+void orc_equilibrium(const orc_params* p, const double* rho_a, const double* rho_b,
+                     const double* ux, const double* uy, double* f)
+{
+    const double* rho[2] = {rho_a, rho_b};
+    for (int s = 0; s < 2; ++s)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                size_t k = IDX(p, x, y);
+                double u = ux ? ux[k] : 0.0, v = uy ? uy[k] : 0.0;
+                double usq = u * u + v * v;
+                for (int i = 0; i < 9; ++i) {
+                    double cu = CX[i] * u + CY[i] * v;
+                    f[FIDX(p, s, i, x, y)] = W[i] * rho[s][k] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                }
+            }
+}
+
+/* Moments: rho_s = sum_i f_is; j = sum_s sum_i f_is c_i, taken as differences of
+ * opposite populations so that a state at rest gives exactly j = 0. */
+static void site_moments(const orc_params* p, const double* f, int x, int y,
+                         double rho[2], double j[2])
+{
+    j[0] = 0.0;
+    j[1] = 0.0;
+    double jx_s[2], jy_s[2];
+    for (int s = 0; s < 2; ++s) {
+        double r = 0.0;
+        for (int i = 0; i < 9; ++i) r += f[FIDX(p, s, i, x, y)];
+        rho[s] = r;
+        double f1 = f[FIDX(p, s, 1, x, y)], f2 = f[FIDX(p, s, 2, x, y)];
+        double f3 = f[FIDX(p, s, 3, x, y)], f4 = f[FIDX(p, s, 4, x, y)];
+        double f5 = f[FIDX(p, s, 5, x, y)], f6 = f[FIDX(p, s, 6, x, y)];
+        double f7 = f[FIDX(p, s, 7, x, y)], f8 = f[FIDX(p, s, 8, x, y)];
+        jx_s[s] = (f1 - f3) + (f5 - f7) + (f8 - f6);
+        jy_s[s] = (f2 - f4) + (f5 - f7) + (f6 - f8);
+    }
+    j[0] = jx_s[0] + jx_s[1];
+    j[1] = jy_s[0] + jy_s[1];
+}
+
+void orc_moments(const orc_params* p, const double* f, double* rho_a, double* rho_b,
+                 double* jx, double* jy)
+{
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            double rho[2], j[2];
+            site_moments(p, f, x, y, rho, j);
+            size_t k = IDX(p, x, y);
+            if (rho_a) rho_a[k] = rho[0];
+            if (rho_b) rho_b[k] = rho[1];
+            if (jx) jx[k] = j[0];
+            if (jy) jy[k] = j[1];
+        }
+}
+
+/* Stencil sums of Eq. (FFF) at one site, for species s, taken over the half
+ * stencils b+ (one vector of each +-c pair) as w_c c (g(r+c) - g(r-c)):
+ *   S1 = sum_{b1} w c psi_s(r+c),  S2 = sum_{b1+b2} p c psi_s(r+c),
+ *   X  = sum_{b1} w c rho_s'(r+c). */
+static void stencil_sums(const orc_params* p, const double* psi_s, const double* rho_o,
+                         int x, int y, double S1[2], double S2[2], double X[2])
+{
+    S1[0] = S1[1] = S2[0] = S2[1] = X[0] = X[1] = 0.0;
+    for (int dy = 0; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+            if (dy == 0 && dx <= 0) continue; /* keep one vector of each pair */
+            int c2 = dx * dx + dy * dy;
+            int xp = wrap(x + dx, p->nx), yp = stencil_row(p, y + dy);
+            int xm = wrap(x - dx, p->nx), ym = stencil_row(p, y - dy);
+            double dpsi = psi_s[IDX(p, xp, yp)] - psi_s[IDX(p, xm, ym)];
+            double w1 = belt1_weight(c2), w2 = belt2_weight(c2);
+            if (w1 != 0.0) {
+                double drho = rho_o[IDX(p, xp, yp)] - rho_o[IDX(p, xm, ym)];
+                S1[0] += w1 * dx * dpsi;
+                S1[1] += w1 * dy * dpsi;
+                X[0] += w1 * dx * drho;
+                X[1] += w1 * dy * drho;
+            }
+            S2[0] += w2 * dx * dpsi;
+            S2[1] += w2 * dy * dpsi;
+        }
+}
+
+static void coupling(const orc_params* p, int s, double* ga, double* gr)
+{
+    *ga = s == 0 ? p->g_aa1 : p->g_bb1;
+    *gr = s == 0 ? p->g_aa2 : p->g_bb2;
+}
+
+/* Forces of Eq. (FFF) from given density fields (rho_a, rho_b: [ny][nx]).
+ * Outputs F_A and F_B components; any output may be NULL. */
+void orc_forces(const orc_params* p, const double* rho_a, const double* rho_b,
+                double* fax, double* fay, double* fbx, double* fby)
+{
+    size_t n = (size_t)p->nx * p->ny;
+    double* psi = (double*)malloc(2 * n * sizeof(double));
+    const double* rho[2] = {rho_a, rho_b};
+    for (int s = 0; s < 2; ++s)
+        for (size_t k = 0; k < n; ++k) psi[s * n + k] = psi_of(rho[s][k], p->rho0);
+    double* out[2][2] = {{fax, fay}, {fbx, fby}};
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            size_t k = IDX(p, x, y);
+            for (int s = 0; s < 2; ++s) {
+                double S1[2], S2[2], X[2], ga, gr;
+                stencil_sums(p, psi + s * n, rho[1 - s], x, y, S1, S2, X);
+                coupling(p, s, &ga, &gr);
+                for (int a = 0; a < 2; ++a) {
+                    double F = -psi[s * n + k] * (ga * S1[a] + gr * S2[a]) - (p->g_ab / p->rho0) * rho[s][k] * X[a];
+                    if (out[s][a]) out[s][a][k] = F;
+                }
+            }
+        }
+    free(psi);
+}
+
+/*
+ * One time step of Eq. (be): f_in (post-streaming state at t) -> f_out (t+1).
+ * If obs != NULL the step's observables are written to *obs, and profile
+ * (length ny, may be NULL) receives sum_x u_phys_x(x, y) with
+ * u_phys = (j + (F_A + F_B)/2) / rho at time t.
+ */
+void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* obs, double* profile)
+{
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = (size_t)nx * ny;
+    const double tau = p->tau, rho0 = p->rho0;
+    double* rho = (double*)malloc(2 * n * sizeof(double));
+    double* psi = (double*)malloc(2 * n * sizeof(double));
+    double* jj = (double*)malloc(2 * n * sizeof(double));
+    double* fst = (double*)malloc(18 * n * sizeof(double)); /* post-collision f* */
+    double* uphys = (double*)malloc(n * sizeof(double));
+
+    /* 1-2. moments and pseudopotential at every site */
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double r[2], j[2];
+            site_moments(p, f_in, x, y, r, j);
+            size_t k = IDX(p, x, y);
+            rho[k] = r[0];
+            rho[n + k] = r[1];
+            jj[k] = j[0];
+            jj[n + k] = j[1];
+            psi[k] = psi_of(r[0], rho0);
+            psi[n + k] = psi_of(r[1], rho0);
+        }
+
+    /* 3-6. forces, shifted equilibrium, BGK collision */
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t k = IDX(p, x, y);
+            double rtot = rho[k] + rho[n + k];
+            double u[2] = {jj[k] / rtot, jj[n + k] / rtot};
+            double Ftot[2] = {0.0, 0.0};
+            for (int s = 0; s < 2; ++s) {
+                double S1[2], S2[2], X[2], ga, gr;
+                stencil_sums(p, psi + s * n, rho + (1 - s) * n, x, y, S1, S2, X);
+                coupling(p, s, &ga, &gr);
+                double rs = rho[s * n + k];
+                double por = psi_over_rho(rs, rho0);
+                double us[2];
+                for (int a = 0; a < 2; ++a) {
+                    /* F_s and the shift tau F_s / rho_s, without dividing by rho_s */
+                    double G = ga * S1[a] + gr * S2[a];
+                    double F = -psi[s * n + k] * G - (p->g_ab / rho0) * rs * X[a];
+                    Ftot[a] += F;
+                    us[a] = u[a] - tau * (por * G + (p->g_ab / rho0) * X[a]);
+                }
+                double usq = us[0] * us[0] + us[1] * us[1];
+                for (int i = 0; i < 9; ++i) {
+                    double cu = CX[i] * us[0] + CY[i] * us[1];
+                    double feq = W[i] * rs * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                    double fi = f_in[FIDX(p, s, i, x, y)];
+                    fst[FIDX(p, s, i, x, y)] = fi - (fi - feq) / tau;
+                }
+            }
+            uphys[k] = (jj[k] + 0.5 * Ftot[0]) / rtot;
+        }
+
+    /* 7. streaming; Couette rows use halfway bounce-back with the moving wall term
+     *    f_ibar(x_b, t+1) = f*_i(x_b, t) - 2 w_i rho_s(x_b) (c_i . u_w) / cs^2.   */
+    double pi_top = 0.0, pi_bot = 0.0;
+    const double u_top = p->u_wall, u_bot = -p->u_wall;
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < 9; ++i)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    double v = fst[FIDX(p, s, i, x, y)];
+                    int yd = y + CY[i];
+                    if (p->bc == 1 && (yd < 0 || yd >= ny)) {
+                        double uw = yd < 0 ? u_bot : u_top;
+                        double rs = rho[s * n + IDX(p, x, y)];
+                        double back = v - 2.0 * W[i] * rs * (CX[i] * uw) * 3.0;
+                        f_out[FIDX(p, s, OPP[i], x, y)] = back;
+                        /* x-momentum delivered to the fluid by this wall link */
+                        double dpx = (double)CX[OPP[i]] * back - (double)CX[i] * v;
+                        if (yd < 0) pi_bot += dpx; else pi_top += dpx;
+                    } else {
+                        int xd = wrap(x + CX[i], nx);
+                        yd = wrap(yd, ny);
+                        f_out[FIDX(p, s, i, xd, yd)] = v;
+                    }
+                }
+
+    if (obs) {
+        double m[2] = {0.0, 0.0}, mo[2] = {0.0, 0.0};
+        for (size_t k = 0; k < n; ++k) {
+            m[0] += rho[k];
+            m[1] += rho[n + k];
+            mo[0] += jj[k];
+            mo[1] += jj[n + k];
+        }
+        obs->mass[0] = m[0];
+        obs->mass[1] = m[1];
+        obs->mom[0] = mo[0];
+        obs->mom[1] = mo[1];
+        obs->pi_top = pi_top;
+        obs->pi_bot = pi_bot;
+    }
+    if (profile)
+        for (int y = 0; y < ny; ++y) {
+            double acc = 0.0;
+            for (int x = 0; x < nx; ++x) acc += uphys[IDX(p, x, y)];
+            profile[y] = acc;
+        }
+    free(rho);
+    free(psi);
+    free(jj);
+    free(fst);
+    free(uphys);
+}
+
+/* Time averages collected over sampled steps. */
+typedef struct {
+    double sum_pi_top, sum_pi_bot;
+    long long n_samples;
+} orc_acc;
+
+/*
+ * n_steps steps starting at absolute step t0 (f is updated in place).  A step t
+ * is sampled if every > 0, t >= start and (t - start) % every == 0: then its
+ * Pi_top/Pi_bot are added to acc and its row sums of u_phys_x to prof_acc
+ * (length ny).  last_obs receives the observables of the last step (NULL ok).
+ * threads <= 0 keeps the OpenMP default.
+ */
+void orc_run(const orc_params* p, double* f, long long t0, long long n_steps,
+             long long start, long long every, orc_acc* acc, double* prof_acc,
+             orc_obs* last_obs, int threads)
+{
+    set_threads(threads);
+    size_t nf = (size_t)18 * p->nx * p->ny;
+    double* g = (double*)malloc(nf * sizeof(double));
+    double* prof = (double*)malloc((size_t)p->ny * sizeof(double));
+    for (long long s = 0; s < n_steps; ++s) {
+        long long t = t0 + s;
+        int sampled = every > 0 && t >= start && (t - start) % every == 0;
+        orc_obs o;
+        int want_obs = sampled || (last_obs && s == n_steps - 1);
+        orc_step(p, f, g, want_obs ? &o : NULL, sampled ? prof : NULL);
+        if (sampled && acc) {
+            acc->sum_pi_top += o.pi_top;
+            acc->sum_pi_bot += o.pi_bot;
+            acc->n_samples += 1;
+            if (prof_acc)
+                for (int y = 0; y < p->ny; ++y) prof_acc[y] += prof[y];
+        }
+        if (last_obs && s == n_steps - 1) *last_obs = o;
+        memcpy(f, g, nf * sizeof(double));
+    }
+    free(g);
+    free(prof);
+}
