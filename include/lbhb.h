@@ -1,0 +1,189 @@
+/*
+ * lbhb: GB300 (sm_103a) library for the two-species lattice Boltzmann model
+ * with multirange Shan-Chen interactions of Benzi, Bernaschi, Sbragaglia and
+ * Succi, "Herschel-Bulkley rheology from lattice kinetic theory of soft-glassy
+ * materials" (arXiv 1004.5058).
+ *
+ * Model (section "Lattice Boltzmann with multirange interactions"):
+ *   Eq. (be)  f_is(r+c_i,t+1) - f_is(r,t) = -(1/tau)[f_is - f^eq_is(rho_s, u + tau F_s/rho_s)],
+ *             s = A,B, D2Q9 populations, f^eq second order in u, cs^2 = 1/3;
+ *   Eq. (FFF) F_s = F^a_s + F^r_s + F^X_s: attractive belt-1 self force, repulsive
+ *             two-belt (24 neighbours) self force, belt-1 cross-species repulsion,
+ *             on the pseudopotential psi(rho) = rho0 (1 - exp(-rho/rho0)).
+ * Boundaries: periodic in x; in y periodic or Couette (halfway bounce-back walls
+ * at y = -1/2 and y = ny - 1/2 moving at -u_wall and +u_wall in x; the paper
+ * itself uses a fully periodic box, walls are an extension for shear-rate control).
+ *
+ * Conventions for every call:
+ *  - the return value is an lb_status; LB_OK = 0 on success;
+ *  - arrays the caller passes are caller-owned; the library copies what it needs
+ *    and never keeps or frees a caller pointer;
+ *  - host field arrays are float64, laid out [cell][y][x] with x fastest;
+ *  - one handle is used by one host thread at a time;
+ *  - work is enqueued on the handle's CUDA stream (the caller's stream given at
+ *    lb_create, or a library-owned stream); calls that return data to the host
+ *    synchronise that stream;
+ *  - errors found on the device (non-finite or non-positive density) are
+ *    reported by the next call that synchronises, as LB_ERR_NONFINITE; the handle
+ *    then refuses lb_step with LB_ERR_STATE until lb_init_fields or
+ *    lb_set_populations loads a new state;
+ *  - lb_last_error returns a message for the last failing call of a handle.
+ */
+#ifndef LBHB_H
+#define LBHB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_handle lb_handle; /* opaque; created and freed by the library */
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID = -1,     /* bad argument (null pointer, size, tau <= 1/2 ...) */
+    LB_ERR_CUDA = -2,        /* a CUDA runtime/driver call failed */
+    LB_ERR_NOMEM = -3,       /* device or host allocation failed */
+    LB_ERR_NONFINITE = -4,   /* the device found a non-finite or non-positive density */
+    LB_ERR_TIMEOUT = -5,     /* a bounded device wait ran out */
+    LB_ERR_STATE = -6,       /* call not valid in the handle's current state */
+    LB_ERR_UNSUPPORTED = -7  /* valid request this build or shape does not support */
+} lb_status;
+
+typedef enum { LB_BC_PERIODIC = 0, LB_BC_COUETTE = 1 } lb_bc;
+
+/* Storage precision of the populations.  Arithmetic is FP32 for LB_FP32 and
+ * LB_FP16_SHIFTED (populations stored as g_i = f_i - w_i rho_bar_s in FP16,
+ * round to nearest) and FP64 for LB_FP64.  Observables are reduced in FP64. */
+typedef enum { LB_FP32 = 0, LB_FP16_SHIFTED = 1, LB_FP64 = 2 } lb_precision;
+
+/* Kernel family: AUTO picks TILED when the shape allows it, else GENERIC. */
+typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_GENERIC = 1, LB_KERNEL_TILED = 2 } lb_kernel;
+
+/* One lattice cell, in the paper's symbols.  All cells of a handle share nx, ny
+ * and bc; the other fields may differ per cell (batched flow curves).
+ *   tau      BGK relaxation time (Eq. (be)); must be > 1/2
+ *   rho0     reference density of psi(rho) = rho0 (1 - exp(-rho/rho0)) and of F^X
+ *   g_aa1, g_bb1  G^a_AA, G^a_BB: belt-1 self couplings (negative attracts)
+ *   g_aa2, g_bb2  G^r_AA, G^r_BB: two-belt self couplings (positive repels)
+ *   g_ab     G_AB = G_BA: belt-1 cross-species coupling
+ *   u_wall   Couette wall speed U (bottom wall -U, top wall +U); ignored if periodic
+ *   rho_bar_a, rho_bar_b  shift reference of LB_FP16_SHIFTED storage
+ *   bc       lb_bc */
+typedef struct {
+    int nx, ny;
+    double tau, rho0;
+    double g_aa1, g_aa2, g_bb1, g_bb2, g_ab;
+    double u_wall;
+    double rho_bar_a, rho_bar_b;
+    int bc;
+} lb_cell_params;
+
+/* Creates a handle for n_cells cells (n_cells >= 1; nx >= 5, ny >= 5; same nx, ny,
+ * bc in every cell) and allocates all device memory it needs.  cuda_stream:
+ * a cudaStream_t of the current device, or NULL for a library-owned stream.
+ * The populations start undefined: call lb_init_fields or lb_set_populations.
+ * Errors: LB_ERR_INVALID, LB_ERR_NOMEM, LB_ERR_CUDA; *out is NULL on failure. */
+lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
+                    void* cuda_stream, lb_handle** out);
+
+/* Sets f_is = f^eq_is(rho_s, u) (moments and f^eq of Eq. (be)) at every site.
+ * rho_a, rho_b: host [n_cells][ny][nx] (required); ux, uy: same shape or NULL
+ * for zero.  Resets the step counter to 0, the time averages and the error
+ * state.  Synchronous. */
+lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b,
+                         const double* ux, const double* uy);
+
+/* Loads populations from host memory: f [n_cells][2][9][ny][nx] float64
+ * (species A then B, D2Q9 order 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
+ * 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)).  Rounded to the storage precision.
+ * Resets counters like lb_init_fields.  Synchronous. */
+lb_status lb_set_populations(lb_handle* h, const double* f);
+
+/* Copies the populations to host memory in the layout of lb_set_populations
+ * (FP16-shifted storage is returned as f = g + w_i rho_bar_s).  Synchronous. */
+lb_status lb_get_populations(lb_handle* h, double* f);
+
+/* Advances every cell by n_steps time steps of Eq. (be) (n_steps >= 0).
+ * Asynchronous on the handle's stream; returns after enqueueing.  Reports a
+ * device error of an earlier, already finished batch if one was recorded. */
+lb_status lb_step(lb_handle* h, long long n_steps);
+
+/* Time-averaging window of the shear observables: step t (counted from the
+ * last init) is sampled if every > 0, t >= start_step and
+ * (t - start_step) % every == 0.  every = 0 disables sampling.  Clears the
+ * accumulated averages. */
+lb_status lb_set_sampling(lb_handle* h, long long start_step, long long every);
+
+/* Per-cell time averages over the sampled steps (host outputs [n_cells]):
+ *   sigma_xy  = (Pi_top - Pi_bot) / (2 nx n_samples), Pi_wall being the x-momentum
+ *               the wall delivers to the fluid through bounce-back in one step;
+ *   shear_rate = (Ubar(ny-1) - Ubar(0)) / (ny-1), Ubar(y) the time average of the
+ *               line average over x of u_x = (j_x + (F_Ax + F_Bx)/2)/rho (the
+ *               paper's U_x(y) of section "Numerical Results", force-corrected);
+ *   shear_bulk (nullable) = least-squares slope of Ubar over rows [ny/4, ny-ny/4).
+ * NaN where no step was sampled.  Synchronous. */
+lb_status lb_shear_stress(lb_handle* h, double* sigma_xy, double* shear_rate,
+                          double* shear_bulk);
+
+/* Time-averaged line profile Ubar(y), host [n_cells][ny]; number of samples in
+ * *n_samples (nullable).  Synchronous. */
+lb_status lb_get_profile(lb_handle* h, double* ubar, long long* n_samples);
+
+/* Current fields (host [n_cells][ny][nx], any pointer may be NULL):
+ * rho_s = sum_i f_is and the paper's barycentric u = sum_s sum_i f_is c_i / rho.
+ * Synchronous; reports LB_ERR_NONFINITE if any density is not finite or <= 0. */
+lb_status lb_get_fields(lb_handle* h, double* rho_a, double* rho_b, double* ux, double* uy);
+
+/* FP64 reductions of the current state on the device (host outputs):
+ * mass_ab [n_cells][2] = sum of rho_A, rho_B; momentum_xy [n_cells][2] = sum of
+ * j_x, j_y.  Either may be NULL.  Synchronous; reports LB_ERR_NONFINITE. */
+lb_status lb_reductions(lb_handle* h, double* mass_ab, double* momentum_xy);
+
+/* Chooses the kernel family and tile (tile_x, tile_y; 0 = default) for
+ * subsequent steps.  LB_ERR_UNSUPPORTED if the shape does not allow it. */
+lb_status lb_set_kernel(lb_handle* h, lb_kernel kernel, int tile_x, int tile_y);
+
+/* Times the supported tiles on this handle's buffers (the state is left
+ * unchanged) and selects the fastest.  cache_path (nullable): a text file where
+ * results are looked up and stored, keyed by device, shape, cell count and
+ * precision.  Synchronous. */
+lb_status lb_autotune(lb_handle* h, const char* cache_path);
+
+/* Reads the kernel family and tile in use (outputs nullable). */
+lb_status lb_get_kernel(const lb_handle* h, lb_kernel* kernel, int* tile_x, int* tile_y);
+
+/* Waits for all enqueued work of the handle; reports device errors. */
+lb_status lb_sync(lb_handle* h);
+
+/* Number of time steps taken since the last init (0 for NULL). */
+long long lb_steps_done(const lb_handle* h);
+
+/* The cudaStream_t the handle enqueues on (the caller's, or the library's own
+ * non-blocking stream), for recording events around lb_step. */
+void* lb_stream(const lb_handle* h);
+
+/* Number of CUDA kernel launches the handle has enqueued since creation
+ * (kernels launched as nodes of a CUDA graph count one each). */
+long long lb_kernel_launches(const lb_handle* h);
+
+/* Message for the last failing call on h; a static string when h is NULL. */
+const char* lb_last_error(const lb_handle* h);
+
+/* Frees the handle and all its device memory.  NULL is a no-op. */
+void lb_destroy(lb_handle* h);
+
+/* Herschel-Bulkley fit sigma = sigma_Y + A S^beta (the law the paper fits in
+ * section "Numerical Results", written there as A + B S^beta) by variable
+ * projection: for each beta the best (sigma_Y, A) is a linear least-squares
+ * problem; beta minimises the residual, found by a scan over [beta_lo, beta_hi]
+ * and a golden-section refinement.  Host FP64.  Needs n >= 3 points with S > 0.
+ * out[0] = sigma_Y, out[1] = A, out[2] = beta, out[3] = residual sum of squares. */
+lb_status lb_hb_fit(const double* shear_rate, const double* sigma, int n,
+                    double beta_lo, double beta_hi, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBHB_H */

@@ -1,0 +1,87 @@
+"""ctypes binding of liblbhb.so: the C ABI of include/lbhb.h under the same
+names.  Argument marshalling only; every step of the lattice update runs in the
+library's CUDA kernels.  Loading fails loudly if the library was not built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbhb.so")
+
+LB_OK, LB_ERR_INVALID, LB_ERR_CUDA, LB_ERR_NOMEM = 0, -1, -2, -3
+LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_UNSUPPORTED = -4, -5, -6, -7
+STATUS_NAMES = {0: "LB_OK", -1: "LB_ERR_INVALID", -2: "LB_ERR_CUDA", -3: "LB_ERR_NOMEM",
+                -4: "LB_ERR_NONFINITE", -5: "LB_ERR_TIMEOUT", -6: "LB_ERR_STATE",
+                -7: "LB_ERR_UNSUPPORTED"}
+LB_BC_PERIODIC, LB_BC_COUETTE = 0, 1
+LB_FP32, LB_FP16_SHIFTED, LB_FP64 = 0, 1, 2
+LB_KERNEL_AUTO, LB_KERNEL_GENERIC, LB_KERNEL_TILED = 0, 1, 2
+
+# Every function the header declares, with its ctypes signature.
+_D = C.POINTER(C.c_double)
+_H = C.c_void_p
+
+
+class lb_cell_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("tau", C.c_double), ("rho0", C.c_double),
+                ("g_aa1", C.c_double), ("g_aa2", C.c_double), ("g_bb1", C.c_double),
+                ("g_bb2", C.c_double), ("g_ab", C.c_double), ("u_wall", C.c_double),
+                ("rho_bar_a", C.c_double), ("rho_bar_b", C.c_double), ("bc", C.c_int)]
+
+
+SIGNATURES = {
+    "lb_create": (C.c_int, [C.POINTER(lb_cell_params), C.c_int, C.c_int, C.c_void_p, C.POINTER(_H)]),
+    "lb_init_fields": (C.c_int, [_H, _D, _D, _D, _D]),
+    "lb_set_populations": (C.c_int, [_H, _D]),
+    "lb_get_populations": (C.c_int, [_H, _D]),
+    "lb_step": (C.c_int, [_H, C.c_longlong]),
+    "lb_set_sampling": (C.c_int, [_H, C.c_longlong, C.c_longlong]),
+    "lb_shear_stress": (C.c_int, [_H, _D, _D, _D]),
+    "lb_get_profile": (C.c_int, [_H, _D, C.POINTER(C.c_longlong)]),
+    "lb_get_fields": (C.c_int, [_H, _D, _D, _D, _D]),
+    "lb_reductions": (C.c_int, [_H, _D, _D]),
+    "lb_set_kernel": (C.c_int, [_H, C.c_int, C.c_int, C.c_int]),
+    "lb_autotune": (C.c_int, [_H, C.c_char_p]),
+    "lb_get_kernel": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lb_sync": (C.c_int, [_H]),
+    "lb_steps_done": (C.c_longlong, [_H]),
+    "lb_stream": (C.c_void_p, [_H]),
+    "lb_kernel_launches": (C.c_longlong, [_H]),
+    "lb_last_error": (C.c_char_p, [_H]),
+    "lb_destroy": (None, [_H]),
+    "lb_hb_fit": (C.c_int, [_D, _D, C.c_int, C.c_double, C.c_double, _D]),
+}
+
+_lib = None
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Loads liblbhb.so (built by paper_1004_5058_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("liblbhb.so is not built (%s); run __graft_entry__.build() or "
+                           "python -m paper_1004_5058_gb300.build" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status, handle=None):
+    if status != LB_OK:
+        msg = load().lb_last_error(handle)
+        raise LBError(status, msg.decode() if msg else "")
+    return status

@@ -1,0 +1,767 @@
+// C ABI of the library (declared in include/lbhb.h): handle life cycle,
+// argument validation, device memory, the step loop (with CUDA graphs for
+// chunks of steps), observables and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/lbhb.h"
+#include "lb_internal.h"
+
+using namespace lbhb;
+
+struct lb_handle {
+    int n_cells = 0, nx = 0, ny = 0, bc = 0;
+    lb_precision prec = LB_FP32;
+    int elem = 4;
+    std::vector<lb_cell_params> cells;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Geom g{};
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* aux = nullptr;               // generic family: rho/psi field
+    double* prof_part = nullptr;       // [cell][nbx][ny] partials of one sampled step
+    double* wall_part = nullptr;       // [cell][nbx][2]
+    int nbx_alloc = 0;
+    double* acc_prof = nullptr;        // [cell][ny] time sums of the line profile
+    double* acc_wall = nullptr;        // [cell][2] time sums of Pi_top, Pi_bot
+    unsigned* d_err = nullptr;
+    unsigned* h_err = nullptr;         // pinned mirror of d_err at the end of the last batch
+    cudaEvent_t batch_done = nullptr;
+    bool batch_pending = false;
+    CellDev* d_cells = nullptr;
+    double* red_part = nullptr;
+    double* red_out = nullptr;
+    double* staging = nullptr;         // [cell][4][ny][nx] float64
+    long long t = 0, start = 0, every = 0, n_samples = 0;
+    bool initialised = false;
+    bool faulted = false;
+    bool use_graphs = true;
+    lb_kernel kernel = LB_KERNEL_GENERIC;
+    int tile_x = 0, tile_y = 0;
+    TiledPlan* plan = nullptr;
+    long long launches = 0;
+    std::string last_error;
+    // CUDA graphs of step chunks, keyed by (source buffer, steps, sampled last step)
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
+};
+
+static const char* g_null_msg = "lb: handle is NULL";
+static thread_local char g_create_msg[512] = "";
+
+static lb_status fail(lb_handle* h, lb_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->last_error = buf;
+    else snprintf(g_create_msg, sizeof g_create_msg, "%s", buf);
+    return st;
+}
+
+#define CK(h, call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail((h), LB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void free_graphs(lb_handle* h)
+{
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+static void release(lb_handle* h)
+{
+    if (!h) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_graphs(h);
+    if (h->plan) tiled_destroy(h->plan);
+    cudaFree(h->f[0]);
+    cudaFree(h->f[1]);
+    cudaFree(h->aux);
+    cudaFree(h->prof_part);
+    cudaFree(h->wall_part);
+    cudaFree(h->acc_prof);
+    cudaFree(h->acc_wall);
+    cudaFree(h->d_err);
+    cudaFree(h->d_cells);
+    cudaFree(h->red_part);
+    cudaFree(h->red_out);
+    cudaFree(h->staging);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->batch_done) cudaEventDestroy(h->batch_done);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    cudaSetDevice(prev);
+    delete h;
+}
+
+static CellDev to_dev(const lb_cell_params& c)
+{
+    CellDev d{};
+    d.tau = c.tau;
+    d.omega = 1.0 / c.tau;
+    d.rho0 = c.rho0;
+    d.gab_over_rho0 = c.g_ab / c.rho0;
+    d.g1[0] = c.g_aa1;
+    d.g1[1] = c.g_bb1;
+    d.g2[0] = c.g_aa2;
+    d.g2[1] = c.g_bb2;
+    d.u_wall = c.u_wall;
+    d.rho_bar[0] = c.rho_bar_a;
+    d.rho_bar[1] = c.rho_bar_b;
+    return d;
+}
+
+// Dispatch on the storage type.
+template <class F>
+static cudaError_t with_type(const lb_handle* h, F&& fn)
+{
+    switch (h->prec) {
+    case LB_FP32: return fn((float*)nullptr);
+    case LB_FP64: return fn((double*)nullptr);
+    default: return fn((__half*)nullptr);
+    }
+}
+
+static lb_status check_device_error(lb_handle* h)
+{
+    unsigned e = 0;
+    CK(h, cudaMemcpy(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e & ERR_NONFINITE) {
+        h->faulted = true;
+        return fail(h, LB_ERR_NONFINITE, "lb: non-finite or non-positive density detected on the device");
+    }
+    if (e & ERR_TIMEOUT) {
+        h->faulted = true;
+        return fail(h, LB_ERR_TIMEOUT, "lb: a bounded device wait ran out (pipeline stalled)");
+    }
+    return LB_OK;
+}
+
+static lb_status sync_and_check(lb_handle* h)
+{
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->batch_pending = false;
+    return check_device_error(h);
+}
+
+static lb_status reset_counters(lb_handle* h)
+{
+    h->t = 0;
+    h->n_samples = 0;
+    h->faulted = false;
+    h->initialised = true;
+    CK(h, cudaMemsetAsync(h->acc_prof, 0, sizeof(double) * h->n_cells * h->ny, h->stream));
+    CK(h, cudaMemsetAsync(h->acc_wall, 0, sizeof(double) * h->n_cells * 2, h->stream));
+    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
+    h->h_err[0] = 0;
+    return LB_OK;
+}
+
+static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
+{
+    if (k == LB_KERNEL_AUTO) {
+        const int cand[][2] = {{128, 64}, {64, 64}, {64, 32}, {32, 32}};
+        for (auto& c : cand)
+            if (tiled_supported(h->g, h->elem, c[0], c[1])) {
+                if (select_kernel(h, LB_KERNEL_TILED, c[0], c[1]) == LB_OK) return LB_OK;
+            }
+        return select_kernel(h, LB_KERNEL_GENERIC, 0, 0);
+    }
+    free_graphs(h);
+    if (k == LB_KERNEL_GENERIC) {
+        if (h->plan) {
+            tiled_destroy(h->plan);
+            h->plan = nullptr;
+        }
+        h->kernel = LB_KERNEL_GENERIC;
+        h->tile_x = 32;
+        h->tile_y = 8;
+        return LB_OK;
+    }
+    if (k != LB_KERNEL_TILED) return fail(h, LB_ERR_INVALID, "lb_set_kernel: unknown kernel %d", (int)k);
+    if (tx == 0) tx = 64;
+    if (ty == 0) ty = 64;
+    if (!tiled_supported(h->g, h->elem, tx, ty))
+        return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: tiled kernel does not support nx=%d ny=%d tile %dx%d",
+                    h->nx, h->ny, tx, ty);
+    if (tiled_partials_nbx(h->g, tx) > h->nbx_alloc)
+        return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: tile %d too narrow for the partial buffers", tx);
+    const char* msg = nullptr;
+    TiledPlan* p = tiled_create(h->g, h->elem, h->bc, h->f[0], h->f[1], tx, ty, &msg);
+    if (!p) return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: %s", msg ? msg : "tiled plan failed");
+    if (h->plan) tiled_destroy(h->plan);
+    h->plan = p;
+    h->kernel = LB_KERNEL_TILED;
+    h->tile_x = tx;
+    h->tile_y = ty;
+    return LB_OK;
+}
+
+extern "C" {
+
+lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec, void* cuda_stream,
+                    lb_handle** out)
+{
+    if (!out) return fail(nullptr, LB_ERR_INVALID, "lb_create: out is NULL");
+    *out = nullptr;
+    if (!cells || n_cells < 1) return fail(nullptr, LB_ERR_INVALID, "lb_create: need n_cells >= 1 cells");
+    if (prec != LB_FP32 && prec != LB_FP16_SHIFTED && prec != LB_FP64)
+        return fail(nullptr, LB_ERR_INVALID, "lb_create: unknown precision %d", (int)prec);
+    const lb_cell_params& c0 = cells[0];
+    for (int c = 0; c < n_cells; ++c) {
+        const lb_cell_params& p = cells[c];
+        if (p.nx != c0.nx || p.ny != c0.ny || p.bc != c0.bc)
+            return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d differs in nx/ny/bc from cell 0", c);
+        if (p.nx < 5 || p.ny < 5 || (long long)p.nx * p.ny > (1LL << 31))
+            return fail(nullptr, LB_ERR_INVALID, "lb_create: lattice %dx%d out of range (5 .. 2^31 sites)", p.nx, p.ny);
+        if (!(p.tau > 0.5) || !std::isfinite(p.tau))
+            return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d tau=%g must exceed 1/2", c, p.tau);
+        if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0))
+            return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d rho0=%g must be positive", c, p.rho0);
+        if (p.bc != LB_BC_PERIODIC && p.bc != LB_BC_COUETTE)
+            return fail(nullptr, LB_ERR_INVALID, "lb_create: unknown boundary %d", p.bc);
+        const double v[] = {p.g_aa1, p.g_aa2, p.g_bb1, p.g_bb2, p.g_ab, p.u_wall, p.rho_bar_a, p.rho_bar_b};
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d has a non-finite parameter", c);
+    }
+    lb_handle* h = new (std::nothrow) lb_handle();
+    if (!h) return fail(nullptr, LB_ERR_NOMEM, "lb_create: out of host memory");
+    h->n_cells = n_cells;
+    h->nx = c0.nx;
+    h->ny = c0.ny;
+    h->bc = c0.bc;
+    h->prec = prec;
+    h->elem = prec == LB_FP64 ? 8 : (prec == LB_FP32 ? 4 : 2);
+    h->cells.assign(cells, cells + n_cells);
+    cudaError_t e = cudaGetDevice(&h->device);
+    auto bail = [&](lb_status st, const char* what, cudaError_t ce) {
+        fail(nullptr, st, "lb_create: %s: %s", what, cudaGetErrorString(ce));
+        release(h);
+        return st;
+    };
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA, "cudaGetDevice", e);
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(LB_ERR_CUDA, "cudaStreamCreate", e);
+        h->own_stream = true;
+    }
+    const int align = 128 / h->elem;  // rows start on 128-byte boundaries
+    h->g.nx = h->nx;
+    h->g.ny = h->ny;
+    h->g.pitch = (h->nx + align - 1) / align * align;
+    h->g.n_cells = n_cells;
+    h->g.plane = (long long)h->ny * h->g.pitch;
+    h->g.cellstride = 18 * h->g.plane;
+    const size_t fbytes = (size_t)n_cells * h->g.cellstride * h->elem;
+    const size_t n = (size_t)h->nx * h->ny;
+    const size_t cbytes = prec == LB_FP64 ? 8 : 4;
+    h->nbx_alloc = std::max(generic_partials_nbx(h->g), tiled_partials_nbx(h->g, 32));
+    struct A { void** p; size_t b; } allocs[] = {
+        {&h->f[0], fbytes},
+        {&h->f[1], fbytes},
+        {&h->aux, (size_t)n_cells * 4 * n * cbytes},
+        {(void**)&h->prof_part, sizeof(double) * n_cells * h->nbx_alloc * h->ny},
+        {(void**)&h->wall_part, sizeof(double) * n_cells * h->nbx_alloc * 2},
+        {(void**)&h->acc_prof, sizeof(double) * n_cells * h->ny},
+        {(void**)&h->acc_wall, sizeof(double) * n_cells * 2},
+        {(void**)&h->d_err, sizeof(unsigned)},
+        {(void**)&h->d_cells, sizeof(CellDev) * n_cells},
+        {(void**)&h->red_part, sizeof(double) * n_cells * state_sums_blocks(h->g) * 4},
+        {(void**)&h->red_out, sizeof(double) * n_cells * 4},
+    };
+    for (auto& a : allocs) {
+        e = cudaMalloc(a.p, a.b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA, "cudaMalloc", e);
+        }
+    }
+    e = cudaHostAlloc((void**)&h->h_err, sizeof(unsigned), cudaHostAllocDefault);
+    if (e != cudaSuccess) return bail(LB_ERR_NOMEM, "cudaHostAlloc", e);
+    e = cudaEventCreateWithFlags(&h->batch_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA, "cudaEventCreate", e);
+    std::vector<CellDev> dc(n_cells);
+    for (int c = 0; c < n_cells; ++c) dc[c] = to_dev(cells[c]);
+    e = cudaMemcpyAsync(h->d_cells, dc.data(), sizeof(CellDev) * n_cells, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, fbytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, fbytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->prof_part, 0, sizeof(double) * n_cells * h->nbx_alloc * h->ny, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->wall_part, 0, sizeof(double) * n_cells * h->nbx_alloc * 2, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA, "initial copies", e);
+    if (reset_counters(h) != LB_OK) {
+        fail(nullptr, LB_ERR_CUDA, "lb_create: %s", h->last_error.c_str());
+        release(h);
+        return LB_ERR_CUDA;
+    }
+    h->initialised = false;
+    if (select_kernel(h, LB_KERNEL_AUTO, 0, 0) != LB_OK) {
+        fail(nullptr, LB_ERR_CUDA, "lb_create: %s", h->last_error.c_str());
+        release(h);
+        return LB_ERR_CUDA;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b, const double* ux,
+                         const double* uy)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!rho_a || !rho_b) return fail(h, LB_ERR_INVALID, "lb_init_fields: rho_a and rho_b are required");
+    CK(h, cudaSetDevice(h->device));
+    const size_t n = (size_t)h->nx * h->ny;
+    if (!h->staging) CK(h, cudaMalloc(&h->staging, sizeof(double) * 4 * n * h->n_cells));
+    const double* src[4] = {rho_a, rho_b, ux, uy};
+    for (int a = 0; a < 4; ++a) {
+        double* dst = h->staging + a * n;
+        if (src[a])
+            CK(h, cudaMemcpy2DAsync(dst, 4 * n * sizeof(double), src[a], n * sizeof(double), n * sizeof(double),
+                                    h->n_cells, cudaMemcpyHostToDevice, h->stream));
+        else
+            CK(h, cudaMemset2DAsync(dst, 4 * n * sizeof(double), 0, n * sizeof(double), h->n_cells, h->stream));
+    }
+    CK(h, with_type(h, [&](auto* tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        return launch_equilibrium<T>(h->staging, (T*)h->f[0], h->g, h->d_cells, h->stream);
+    }));
+    h->launches += 1;
+    h->cur = 0;
+    lb_status st = reset_counters(h);
+    if (st != LB_OK) return st;
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->batch_pending = false;
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_handle* h, const double* f)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!f) return fail(h, LB_ERR_INVALID, "lb_set_populations: f is NULL");
+    CK(h, cudaSetDevice(h->device));
+    const size_t bytes = sizeof(double) * 18 * (size_t)h->nx * h->ny * h->n_cells;
+    double* tmp = nullptr;
+    CK(h, cudaMalloc(&tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, f, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = with_type(h, [&](auto* tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            return launch_import<T>(tmp, (T*)h->f[0], h->g, h->d_cells, h->stream);
+        });
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(h, LB_ERR_CUDA, "lb_set_populations: %s", cudaGetErrorString(e));
+    h->launches += 1;
+    h->cur = 0;
+    lb_status st = reset_counters(h);
+    if (st != LB_OK) return st;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_populations(lb_handle* h, double* f)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!f) return fail(h, LB_ERR_INVALID, "lb_get_populations: f is NULL");
+    if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_get_populations: no state loaded");
+    CK(h, cudaSetDevice(h->device));
+    const size_t bytes = sizeof(double) * 18 * (size_t)h->nx * h->ny * h->n_cells;
+    double* tmp = nullptr;
+    CK(h, cudaMalloc(&tmp, bytes));
+    cudaError_t e = with_type(h, [&](auto* tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        return launch_export<T>((const T*)h->f[h->cur], tmp, h->g, h->d_cells, h->stream);
+    });
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(h, LB_ERR_CUDA, "lb_get_populations: %s", cudaGetErrorString(e));
+    h->launches += 1;
+    return LB_OK;
+}
+
+static cudaError_t enqueue_one_step(lb_handle* h, int src, bool sample, int* nl)
+{
+    cudaError_t e = with_type(h, [&](auto* tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        if (h->kernel == LB_KERNEL_TILED)
+            return launch_tiled_step<T>(h->plan, src, h->d_cells, sample, h->prof_part, h->wall_part, h->d_err,
+                                        h->stream, nl);
+        return launch_generic_step<T>((const T*)h->f[src], (T*)h->f[1 - src], h->g, h->bc, h->d_cells, h->aux,
+                                      sample, h->prof_part, h->wall_part, h->d_err, h->stream, nl);
+    });
+    if (e != cudaSuccess || !sample) return e;
+    const int nbx = h->kernel == LB_KERNEL_TILED ? tiled_partials_nbx(h->g, h->tile_x) : generic_partials_nbx(h->g);
+    *nl += 1;
+    return launch_accumulate(h->prof_part, h->wall_part, nbx, h->ny, h->bc, h->n_cells, h->acc_prof, h->acc_wall,
+                             h->stream);
+}
+
+// A chunk of `steps` steps starting from buffer `src`; only the last one may be sampled.
+static cudaError_t run_chunk(lb_handle* h, int src, int steps, bool sample_last, int* nl)
+{
+    const int min_graph = 4;
+    if (steps < min_graph) {
+        for (int k = 0; k < steps; ++k) {
+            cudaError_t e = enqueue_one_step(h, src, sample_last && k == steps - 1, nl);
+            if (e != cudaSuccess) return e;
+            src ^= 1;
+        }
+        return cudaSuccess;
+    }
+    auto key = std::make_tuple(src, steps, sample_last ? 1 : 0);
+    auto it = h->graphs.find(key);
+    int per = 0;
+    if (it == h->graphs.end()) {
+        if (h->graphs.size() > 64) free_graphs(h);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = h->use_graphs ? cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)
+                                      : cudaErrorStreamCaptureUnsupported;
+        if (e != cudaSuccess) {
+            // streams that cannot be captured (the legacy default stream): plain launches
+            cudaGetLastError();
+            h->use_graphs = false;
+            for (int k = 0; k < steps; ++k) {
+                e = enqueue_one_step(h, src, sample_last && k == steps - 1, nl);
+                if (e != cudaSuccess) return e;
+                src ^= 1;
+            }
+            return cudaSuccess;
+        }
+        int s = src;
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+            e = enqueue_one_step(h, s, sample_last && k == steps - 1, &per);
+            s ^= 1;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return e;
+        }
+        if (e2 != cudaSuccess) return e2;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return e;
+        it = h->graphs.emplace(key, exec).first;
+    }
+    // count the launches the graph holds
+    int kernels_per_step = h->kernel == LB_KERNEL_TILED ? 1 : 2;
+    *nl += steps * kernels_per_step + (sample_last ? 1 : 0);
+    return cudaGraphLaunch(it->second, h->stream);
+}
+
+lb_status lb_step(lb_handle* h, long long n_steps)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (n_steps < 0) return fail(h, LB_ERR_INVALID, "lb_step: n_steps < 0");
+    if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_step: no state loaded (call lb_init_fields)");
+    if (h->faulted) return fail(h, LB_ERR_STATE, "lb_step: an earlier device error left the state invalid");
+    CK(h, cudaSetDevice(h->device));
+    if (h->batch_pending && cudaEventQuery(h->batch_done) == cudaSuccess) {
+        h->batch_pending = false;
+        if (h->h_err[0]) {
+            h->faulted = true;
+            return fail(h, (h->h_err[0] & ERR_TIMEOUT) ? LB_ERR_TIMEOUT : LB_ERR_NONFINITE,
+                        "lb_step: the previous batch reported a device error (%u)", h->h_err[0]);
+        }
+    }
+    if (n_steps == 0) return LB_OK;
+    int nl = 0;
+    long long done = 0;
+    while (done < n_steps) {
+        // steps up to and including the next sampled step (or the end)
+        long long left = n_steps - done;
+        long long to_sample = -1;
+        if (h->every > 0) {
+            long long t = h->t;
+            long long next = t <= h->start ? h->start : h->start + ((t - h->start + h->every - 1) / h->every) * h->every;
+            to_sample = next - t;  // steps before the sampled one
+        }
+        long long chunk;
+        bool sample_last = false;
+        if (to_sample >= 0 && to_sample < left) {
+            chunk = to_sample + 1;
+            sample_last = true;
+        } else {
+            chunk = left;
+        }
+        // split long unsampled runs into graph-sized pieces
+        while (chunk > 0) {
+            const long long piece_max = 64;
+            const long long piece = chunk > piece_max ? piece_max : chunk;
+            const bool s_last = sample_last && piece == chunk;
+            cudaError_t e = run_chunk(h, h->cur, (int)piece, s_last, &nl);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, LB_ERR_CUDA, "lb_step: launch failed: %s", cudaGetErrorString(e));
+            }
+            if (piece & 1) h->cur ^= 1;
+            h->t += piece;
+            done += piece;
+            chunk -= piece;
+            if (s_last) h->n_samples += 1;
+        }
+    }
+    h->launches += nl;
+    CK(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaEventRecord(h->batch_done, h->stream));
+    h->batch_pending = true;
+    return LB_OK;
+}
+
+lb_status lb_set_sampling(lb_handle* h, long long start_step, long long every)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (every < 0 || start_step < 0) return fail(h, LB_ERR_INVALID, "lb_set_sampling: negative argument");
+    CK(h, cudaSetDevice(h->device));
+    h->start = start_step;
+    h->every = every;
+    h->n_samples = 0;
+    CK(h, cudaMemsetAsync(h->acc_prof, 0, sizeof(double) * h->n_cells * h->ny, h->stream));
+    CK(h, cudaMemsetAsync(h->acc_wall, 0, sizeof(double) * h->n_cells * 2, h->stream));
+    return LB_OK;
+}
+
+static lb_status read_acc(lb_handle* h, std::vector<double>& prof, std::vector<double>& wall)
+{
+    lb_status st = sync_and_check(h);
+    if (st != LB_OK) return st;
+    prof.resize((size_t)h->n_cells * h->ny);
+    wall.resize((size_t)h->n_cells * 2);
+    CK(h, cudaMemcpy(prof.data(), h->acc_prof, sizeof(double) * prof.size(), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(wall.data(), h->acc_wall, sizeof(double) * wall.size(), cudaMemcpyDeviceToHost));
+    return LB_OK;
+}
+
+lb_status lb_shear_stress(lb_handle* h, double* sigma_xy, double* shear_rate, double* shear_bulk)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!sigma_xy || !shear_rate) return fail(h, LB_ERR_INVALID, "lb_shear_stress: outputs are NULL");
+    std::vector<double> prof, wall;
+    lb_status st = read_acc(h, prof, wall);
+    if (st != LB_OK) return st;
+    const double ns = (double)h->n_samples, nx = h->nx;
+    const int ny = h->ny, lo = ny / 4, hi = ny - ny / 4;
+    for (int c = 0; c < h->n_cells; ++c) {
+        if (h->n_samples == 0) {
+            sigma_xy[c] = shear_rate[c] = NAN;
+            if (shear_bulk) shear_bulk[c] = NAN;
+            continue;
+        }
+        sigma_xy[c] = 0.5 * (wall[c * 2 + 0] - wall[c * 2 + 1]) / (nx * ns);
+        const double* p = prof.data() + (size_t)c * ny;
+        shear_rate[c] = (p[ny - 1] - p[0]) / (nx * ns) / (ny - 1);
+        if (shear_bulk) {
+            double ym = 0.5 * (lo + hi - 1), num = 0.0, den = 0.0;
+            for (int y = lo; y < hi; ++y) {
+                num += (y - ym) * (p[y] / (nx * ns));
+                den += (y - ym) * (y - ym);
+            }
+            shear_bulk[c] = num / den;
+        }
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_profile(lb_handle* h, double* ubar, long long* n_samples)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!ubar) return fail(h, LB_ERR_INVALID, "lb_get_profile: ubar is NULL");
+    std::vector<double> prof, wall;
+    lb_status st = read_acc(h, prof, wall);
+    if (st != LB_OK) return st;
+    const double d = (double)h->nx * (double)h->n_samples;
+    for (size_t k = 0; k < prof.size(); ++k) ubar[k] = h->n_samples ? prof[k] / d : NAN;
+    if (n_samples) *n_samples = h->n_samples;
+    return LB_OK;
+}
+
+lb_status lb_get_fields(lb_handle* h, double* rho_a, double* rho_b, double* ux, double* uy)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_get_fields: no state loaded");
+    CK(h, cudaSetDevice(h->device));
+    const size_t n = (size_t)h->nx * h->ny;
+    if (!h->staging) CK(h, cudaMalloc(&h->staging, sizeof(double) * 4 * n * h->n_cells));
+    CK(h, with_type(h, [&](auto* tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        return launch_fields<T>((const T*)h->f[h->cur], h->staging, h->g, h->d_cells, h->d_err, h->stream);
+    }));
+    h->launches += 1;
+    double* dst[4] = {rho_a, rho_b, ux, uy};
+    for (int a = 0; a < 4; ++a)
+        if (dst[a])
+            CK(h, cudaMemcpy2DAsync(dst[a], n * sizeof(double), h->staging + a * n, 4 * n * sizeof(double),
+                                    n * sizeof(double), h->n_cells, cudaMemcpyDeviceToHost, h->stream));
+    return sync_and_check(h);
+}
+
+lb_status lb_reductions(lb_handle* h, double* mass_ab, double* momentum_xy)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_reductions: no state loaded");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, with_type(h, [&](auto* tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        return launch_state_sums<T>((const T*)h->f[h->cur], h->g, h->d_cells, h->red_part, h->red_out, h->d_err,
+                                    h->stream);
+    }));
+    h->launches += 2;
+    std::vector<double> o((size_t)h->n_cells * 4);
+    CK(h, cudaMemcpyAsync(o.data(), h->red_out, sizeof(double) * o.size(), cudaMemcpyDeviceToHost, h->stream));
+    lb_status st = sync_and_check(h);
+    if (st != LB_OK) return st;
+    for (int c = 0; c < h->n_cells; ++c) {
+        if (mass_ab) {
+            mass_ab[2 * c] = o[4 * c];
+            mass_ab[2 * c + 1] = o[4 * c + 1];
+        }
+        if (momentum_xy) {
+            momentum_xy[2 * c] = o[4 * c + 2];
+            momentum_xy[2 * c + 1] = o[4 * c + 3];
+        }
+    }
+    return LB_OK;
+}
+
+lb_status lb_set_kernel(lb_handle* h, lb_kernel kernel, int tile_x, int tile_y)
+{
+    if (!h) return LB_ERR_INVALID;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return select_kernel(h, kernel, tile_x, tile_y);
+}
+
+lb_status lb_get_kernel(const lb_handle* h, lb_kernel* kernel, int* tile_x, int* tile_y)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (kernel) *kernel = h->kernel;
+    if (tile_x) *tile_x = h->tile_x;
+    if (tile_y) *tile_y = h->tile_y;
+    return LB_OK;
+}
+
+lb_status lb_autotune(lb_handle* h, const char* cache_path)
+{
+    if (!h) return LB_ERR_INVALID;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    char devname[256] = "";
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) snprintf(devname, sizeof devname, "%s", prop.name);
+    for (char* c = devname; *c; ++c)
+        if (*c == ' ') *c = '_';
+    char key[512];
+    snprintf(key, sizeof key, "%s nx=%d ny=%d cells=%d prec=%d bc=%d", devname, h->nx, h->ny, h->n_cells,
+             (int)h->prec, h->bc);
+    if (cache_path) {
+        FILE* fp = fopen(cache_path, "r");
+        if (fp) {
+            char line[768];
+            while (fgets(line, sizeof line, fp)) {
+                int k = -1, tx = 0, ty = 0;
+                char* bar = strchr(line, '|');
+                if (!bar) continue;
+                *bar = 0;
+                if (strcmp(line, key) == 0 && sscanf(bar + 1, "%d %d %d", &k, &tx, &ty) == 3) {
+                    fclose(fp);
+                    return select_kernel(h, (lb_kernel)k, tx, ty);
+                }
+            }
+            fclose(fp);
+        }
+    }
+    // candidates: generic, and every supported tile
+    std::vector<std::tuple<int, int, int>> cand;
+    cand.emplace_back((int)LB_KERNEL_GENERIC, 0, 0);
+    const int txs[] = {32, 64, 128, 256};
+    const int tys[] = {16, 32, 64, 128, 256};
+    for (int tx : txs)
+        for (int ty : tys)
+            if (tiled_supported(h->g, h->elem, tx, ty)) cand.emplace_back((int)LB_KERNEL_TILED, tx, ty);
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    std::tuple<int, int, int> best_c = cand[0];
+    const int reps = 6;
+    for (auto& c : cand) {
+        if (select_kernel(h, (lb_kernel)std::get<0>(c), std::get<1>(c), std::get<2>(c)) != LB_OK) continue;
+        int nl = 0;
+        // trial steps read the current buffer and write the other one, without
+        // swapping, so the state is unchanged
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r) ok = enqueue_one_step(h, h->cur, false, &nl) == cudaSuccess;
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && ok; ++r) ok = enqueue_one_step(h, h->cur, false, &nl) == cudaSuccess;
+        cudaEventRecord(e1, h->stream);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        h->launches += nl;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lb_status st = select_kernel(h, (lb_kernel)std::get<0>(best_c), std::get<1>(best_c), std::get<2>(best_c));
+    if (st != LB_OK) return st;
+    if (cache_path) {
+        FILE* fp = fopen(cache_path, "a");
+        if (fp) {
+            fprintf(fp, "%s|%d %d %d %.6f\n", key, std::get<0>(best_c), std::get<1>(best_c), std::get<2>(best_c),
+                    best / reps);
+            fclose(fp);
+        }
+    }
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_handle* h)
+{
+    if (!h) return LB_ERR_INVALID;
+    return sync_and_check(h);
+}
+
+long long lb_steps_done(const lb_handle* h) { return h ? h->t : 0; }
+
+void* lb_stream(const lb_handle* h) { return h ? (void*)h->stream : nullptr; }
+
+long long lb_kernel_launches(const lb_handle* h) { return h ? h->launches : 0; }
+
+const char* lb_last_error(const lb_handle* h)
+{
+    if (!h) return g_create_msg[0] ? g_create_msg : g_null_msg;
+    return h->last_error.c_str();
+}
+
+void lb_destroy(lb_handle* h) { release(h); }
+
+}  // extern "C"

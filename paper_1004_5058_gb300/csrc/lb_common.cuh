@@ -1,0 +1,204 @@
+// Shared device-side definitions of the CUDA path: lattice tables, per-cell
+// parameters, storage precisions and the per-site arithmetic of one time step
+// (forces of Eq. (FFF), shifted equilibrium and BGK collision of Eq. (be)).
+// Both kernel families (generic and tiled) call the site functions below, so
+// they compute bit-identical results for the same inputs.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbhb {
+
+// ---------------------------------------------------------------- tables --
+// D2Q9 order: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
+__host__ __device__ constexpr int q_cx(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
+__host__ __device__ constexpr int q_cy(int i) { return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0); }
+__host__ __device__ constexpr int q_opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5); }
+__host__ __device__ constexpr double q_w(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// Half of the 24-neighbour interaction stencil (one vector of each +-c pair),
+// k = 0..11; the first four (k < 4) have |c|^2 <= 2 and form belt 1.
+__host__ __device__ constexpr int hs_dx(int k)
+{
+    return k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 1 : k == 3 ? -1 : k == 4 ? 2 : k == 5 ? 0 : k == 6 ? 2 : k == 7 ? -2 : k == 8 ? 1 : k == 9 ? -1 : k == 10 ? 2 : -2;
+}
+__host__ __device__ constexpr int hs_dy(int k)
+{
+    return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 1 : k == 3 ? 1 : k == 4 ? 0 : k == 5 ? 2 : k == 6 ? 1 : k == 7 ? 1 : k == 8 ? 2 : k == 9 ? 2 : k == 10 ? 2 : 2;
+}
+// Belt-1 weights: the standard D2Q9 weights 1/9 (|c|^2 = 1), 1/36 (|c|^2 = 2).
+__host__ __device__ constexpr double hs_w1(int k)
+{
+    return k >= 4 ? 0.0 : (hs_dx(k) * hs_dx(k) + hs_dy(k) * hs_dy(k) == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+// Two-belt weights of the 25-velocity isotropic set, same second moment 1/3:
+// |c|^2 = 1, 2, 4, 5, 8 -> 4/63, 4/135, 1/180, 2/945, 1/15120.
+__host__ __device__ constexpr double hs_w2(int k)
+{
+    return (hs_dx(k) * hs_dx(k) + hs_dy(k) * hs_dy(k)) == 1 ? 4.0 / 63.0
+         : (hs_dx(k) * hs_dx(k) + hs_dy(k) * hs_dy(k)) == 2 ? 4.0 / 135.0
+         : (hs_dx(k) * hs_dx(k) + hs_dy(k) * hs_dy(k)) == 4 ? 1.0 / 180.0
+         : (hs_dx(k) * hs_dx(k) + hs_dy(k) * hs_dy(k)) == 5 ? 2.0 / 945.0
+                                                            : 1.0 / 15120.0;
+}
+
+// ------------------------------------------------------------ parameters --
+// Per-cell parameters as the kernels read them.
+struct CellDev {
+    double tau, omega, rho0, gab_over_rho0;
+    double g1[2], g2[2];  // G^a_ss, G^r_ss for s = A, B
+    double u_wall;        // top wall +u_wall, bottom wall -u_wall (Couette)
+    double rho_bar[2];    // FP16 shift reference
+};
+
+// Population array geometry: [cell][s][i][y][pitch], x fastest.
+struct Geom {
+    int nx, ny, pitch, n_cells;
+    long long plane;       // ny * pitch
+    long long cellstride;  // 18 * plane
+};
+
+__host__ __device__ inline long long fidx(const Geom& g, int cell, int q, int y, int x)
+{
+    return (long long)cell * g.cellstride + (long long)q * g.plane + (long long)y * g.pitch + x;
+}
+
+// ------------------------------------------------------- storage formats --
+template <class T> struct Store;
+template <> struct Store<float> {
+    using C = float;
+    static constexpr bool shifted = false;
+    __device__ static C ld(const float* p, long long k, C) { return p[k]; }
+    __device__ static void st(float* p, long long k, C v, C) { p[k] = v; }
+};
+template <> struct Store<double> {
+    using C = double;
+    static constexpr bool shifted = false;
+    __device__ static C ld(const double* p, long long k, C) { return p[k]; }
+    __device__ static void st(double* p, long long k, C v, C) { p[k] = v; }
+};
+// FP16 storage of the shifted populations g_i = f_i - w_i rho_bar_s.
+template <> struct Store<__half> {
+    using C = float;
+    static constexpr bool shifted = true;
+    __device__ static C ld(const __half* p, long long k, C shift) { return __half2float(p[k]) + shift; }
+    __device__ static void st(__half* p, long long k, C v, C shift) { p[k] = __float2half_rn(v - shift); }
+};
+
+template <class C> __device__ inline C expm1_c(C x);
+template <> __device__ inline float expm1_c<float>(float x) { return expm1f(x); }
+template <> __device__ inline double expm1_c<double>(double x) { return expm1(x); }
+
+// psi(rho) = rho0 (1 - exp(-rho/rho0)) = -rho0 expm1(-rho/rho0)
+template <class C> __device__ inline C psi_of(C rho, C rho0, C inv_rho0) { return -rho0 * expm1_c<C>(-rho * inv_rho0); }
+
+// ----------------------------------------------------- per-site physics --
+// Interaction sums of Eq. (FFF) at one site for one species, from the
+// differences d_k = g(r + c_k) - g(r - c_k) over the half stencil:
+//   S1 = sum_{belt 1} w c psi_s(r+c),  S2 = sum_{belts 1+2} p c psi_s(r+c),
+//   X  = sum_{belt 1} w c rho_s'(r+c).
+template <class C> struct Sums {
+    C s1x, s1y, s2x, s2y, xx, xy;
+};
+
+template <class C>
+__device__ inline Sums<C> stencil_sums(const C dpsi[12], const C drho_other[4])
+{
+    Sums<C> r;
+    r.s1x = r.s1y = r.s2x = r.s2y = r.xx = r.xy = C(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const C w2 = C(hs_w2(k));
+        if (hs_dx(k) != 0) r.s2x += (w2 * C(hs_dx(k))) * dpsi[k];
+        if (hs_dy(k) != 0) r.s2y += (w2 * C(hs_dy(k))) * dpsi[k];
+        if (k < 4) {
+            const C w1 = C(hs_w1(k));
+            if (hs_dx(k) != 0) {
+                r.s1x += (w1 * C(hs_dx(k))) * dpsi[k];
+                r.xx += (w1 * C(hs_dx(k))) * drho_other[k];
+            }
+            if (hs_dy(k) != 0) {
+                r.s1y += (w1 * C(hs_dy(k))) * dpsi[k];
+                r.xy += (w1 * C(hs_dy(k))) * drho_other[k];
+            }
+        }
+    }
+    return r;
+}
+
+// Result of colliding one site: post-collision populations and the total
+// force (for the force-corrected velocity of the observables).
+template <class C> struct Collided {
+    C fs[2][9];
+    C Fx, Fy;
+};
+
+// Shifted-velocity BGK collision of Eq. (be) for both species at one site.
+//   u      = j / (rho_A + rho_B)                                (barycentric)
+//   F_s    = -psi_s (G^a S1 + G^r S2) - (G_AB/rho0) rho_s X       (Eq. (FFF))
+//   u_s    = u + tau F_s/rho_s = u - tau[(psi_s/rho_s)(G^a S1 + G^r S2) + (G_AB/rho0) X]
+//   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau
+// psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
+// vanishing species density.
+template <class C>
+__device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi[2],
+                                    const Sums<C> sm[2], const CellDev& p, Collided<C>& out)
+{
+    C jx = C(0), jy = C(0);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        jx += (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
+        jy += (f[s][2] - f[s][4]) + (f[s][5] - f[s][7]) + (f[s][6] - f[s][8]);
+    }
+    const C inv_rho = C(1) / (rho[0] + rho[1]);
+    const C ux = jx * inv_rho, uy = jy * inv_rho;
+    const C tau = C(p.tau), omega = C(p.omega), gx = C(p.gab_over_rho0);
+    C Fx = C(0), Fy = C(0);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const C ga = C(p.g1[s]), gr = C(p.g2[s]);
+        const C Gx = ga * sm[s].s1x + gr * sm[s].s2x;
+        const C Gy = ga * sm[s].s1y + gr * sm[s].s2y;
+        Fx += -psi[s] * Gx - gx * rho[s] * sm[s].xx;
+        Fy += -psi[s] * Gy - gx * rho[s] * sm[s].xy;
+        const C por = rho[s] != C(0) ? psi[s] / rho[s] : C(1);
+        const C usx = ux - tau * (por * Gx + gx * sm[s].xx);
+        const C usy = uy - tau * (por * Gy + gx * sm[s].xy);
+        const C usq = C(1.5) * (usx * usx + usy * usy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const C cu = C(q_cx(i)) * usx + C(q_cy(i)) * usy;
+            const C feq = C(q_w(i)) * rho[s] * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
+            out.fs[s][i] = f[s][i] + omega * (feq - f[s][i]);
+        }
+    }
+    out.Fx = Fx;
+    out.Fy = Fy;
+}
+
+// Halfway bounce-back with a moving wall: a population f*_i leaving through the
+// wall returns as f_opp(i) = f*_i - 2 w_i rho_s (c_i . u_w)/cs^2 (cs^2 = 1/3);
+// *dpx receives the x-momentum this link delivers to the fluid.
+template <class C>
+__device__ inline C bounce(int i, C fstar, C rho_s, C u_w, C* dpx)
+{
+    const C back = fstar - C(6.0 * q_w(i)) * rho_s * (C(q_cx(i)) * u_w);
+    *dpx = C(q_cx(q_opp(i))) * back - C(q_cx(i)) * fstar;
+    return back;
+}
+
+// Row seen by the interaction stencil: periodic, or mirrored across the walls
+// (psi(x,-k) = psi(x,k-1), psi(x,ny-1+k) = psi(x,ny-k)).  |y - in-range| <= 3.
+__host__ __device__ inline int stencil_row(int y, int ny, int bc)
+{
+    if (bc == 0) return y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    return y < 0 ? -y - 1 : (y >= ny ? 2 * ny - y - 1 : y);
+}
+__host__ __device__ inline int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
+// Device error word bits.
+enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
+
+}  // namespace lbhb

@@ -1,0 +1,46 @@
+// Internal launch interface between the C ABI (lb_capi.cu) and the kernels.
+#pragma once
+
+#include "lb_common.cuh"
+
+namespace lbhb {
+
+// generic family (lb_generic.cu)
+template <class T>
+cudaError_t launch_generic_step(const T* fin, T* fout, const Geom& g, int bc, const CellDev* cells, void* aux,
+                                bool sample, double* prof_part, double* wall_part, unsigned* err,
+                                cudaStream_t st, int* n_launches);
+int generic_partials_nbx(const Geom& g);
+
+// tiled family (lb_tiled.cu)
+struct TiledPlan;  // opaque per-handle state of the tiled kernel
+bool tiled_supported(const Geom& g, int elem_bytes, int tile_x, int tile_y);
+int tiled_partials_nbx(const Geom& g, int tile_x);
+// Creates the plan (tensor maps for both ping-pong buffers).  Returns nullptr
+// and sets *err_msg if the shape/tile is not supported or encoding failed.
+TiledPlan* tiled_create(const Geom& g, int elem_bytes, int bc, void* f0, void* f1, int tile_x, int tile_y,
+                        const char** err_msg);
+void tiled_destroy(TiledPlan* p);
+template <class T>
+cudaError_t launch_tiled_step(TiledPlan* p, int src_buf, const CellDev* cells, bool sample, double* prof_part,
+                              double* wall_part, unsigned* err, cudaStream_t st, int* n_launches);
+void tiled_tiles(const TiledPlan* p, int* tx, int* ty);
+
+// auxiliary kernels (lb_aux.cu)
+template <class T>
+cudaError_t launch_equilibrium(const double* src, T* f, const Geom& g, const CellDev* cells, cudaStream_t st);
+template <class T>
+cudaError_t launch_export(const T* f, double* dst, const Geom& g, const CellDev* cells, cudaStream_t st);
+template <class T>
+cudaError_t launch_import(const double* src, T* f, const Geom& g, const CellDev* cells, cudaStream_t st);
+template <class T>
+cudaError_t launch_fields(const T* f, double* dst, const Geom& g, const CellDev* cells, unsigned* err,
+                          cudaStream_t st);
+int state_sums_blocks(const Geom& g);
+template <class T>
+cudaError_t launch_state_sums(const T* f, const Geom& g, const CellDev* cells, double* part, double* out,
+                              unsigned* err, cudaStream_t st);
+cudaError_t launch_accumulate(const double* prof_part, const double* wall_part, int nbx, int ny, int bc,
+                              int n_cells, double* acc_prof, double* acc_wall, cudaStream_t st);
+
+}  // namespace lbhb

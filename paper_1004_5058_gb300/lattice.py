@@ -1,0 +1,167 @@
+"""Python front end of the C ABI: a handle of one or more lattice cells.
+
+Thin marshalling over liblbhb.so (see include/lbhb.h for the meaning of every
+call); numpy arrays in and out, float64 host fields laid out [cell][y][x].
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Iterable, Optional
+
+import numpy as np
+
+from . import _lib as L
+from .inputs import CellParams
+
+PRECISIONS = {"fp32": L.LB_FP32, "fp16": L.LB_FP16_SHIFTED, "fp16_shifted": L.LB_FP16_SHIFTED, "fp64": L.LB_FP64}
+KERNELS = {"auto": L.LB_KERNEL_AUTO, "generic": L.LB_KERNEL_GENERIC, "tiled": L.LB_KERNEL_TILED}
+KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(L._D)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream) or None  # torch.cuda.Stream / ExternalStream
+
+
+def cell_struct(c: CellParams) -> L.lb_cell_params:
+    return L.lb_cell_params(c.nx, c.ny, c.tau, c.rho0, c.g_aa1, c.g_aa2, c.g_bb1, c.g_bb2, c.g_ab,
+                            c.u_wall, c.rho_bar_a, c.rho_bar_b, c.bc)
+
+
+class Lattice:
+    """n_cells independent cells advanced together (lb_create .. lb_destroy)."""
+
+    def __init__(self, cells: Iterable[CellParams], precision: str = "fp32", stream=None):
+        self.lib = L.load()
+        self.cells = list(cells)
+        self.n_cells = len(self.cells)
+        self.nx, self.ny = self.cells[0].nx, self.cells[0].ny
+        self.precision = precision
+        arr = (L.lb_cell_params * self.n_cells)(*[cell_struct(c) for c in self.cells])
+        h = L._H()
+        st = self.lib.lb_create(arr, self.n_cells, PRECISIONS[precision], _stream_ptr(stream), C.byref(h))
+        L.check(st, None)
+        self.h = h
+
+    # ---- life cycle
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, st):
+        return L.check(st, self.h)
+
+    def _field(self, a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        a = a.reshape(self.n_cells, self.ny, self.nx)
+        return a
+
+    # ---- state
+    def init_fields(self, rho_a, rho_b, ux=None, uy=None):
+        ra, rb, u, v = (self._field(a) for a in (rho_a, rho_b, ux, uy))
+        self._chk(self.lib.lb_init_fields(self.h, _dp(ra), _dp(rb), _dp(u), _dp(v)))
+        return self
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.n_cells, 2, 9, self.ny, self.nx)
+        self._chk(self.lib.lb_set_populations(self.h, _dp(f)))
+        return self
+
+    def get_populations(self):
+        f = np.empty((self.n_cells, 2, 9, self.ny, self.nx))
+        self._chk(self.lib.lb_get_populations(self.h, _dp(f)))
+        return f
+
+    def step(self, n: int):
+        self._chk(self.lib.lb_step(self.h, int(n)))
+        return self
+
+    def sync(self):
+        self._chk(self.lib.lb_sync(self.h))
+        return self
+
+    # ---- observables
+    def set_sampling(self, start: int, every: int):
+        self._chk(self.lib.lb_set_sampling(self.h, int(start), int(every)))
+        return self
+
+    def shear_stress(self):
+        s = np.empty(self.n_cells)
+        r = np.empty(self.n_cells)
+        b = np.empty(self.n_cells)
+        self._chk(self.lib.lb_shear_stress(self.h, _dp(s), _dp(r), _dp(b)))
+        return s, r, b
+
+    def profile(self):
+        u = np.empty((self.n_cells, self.ny))
+        n = C.c_longlong()
+        self._chk(self.lib.lb_get_profile(self.h, _dp(u), C.byref(n)))
+        return u, n.value
+
+    def fields(self):
+        out = [np.empty((self.n_cells, self.ny, self.nx)) for _ in range(4)]
+        self._chk(self.lib.lb_get_fields(self.h, *[_dp(o) for o in out]))
+        return tuple(out)
+
+    def reductions(self):
+        m = np.empty((self.n_cells, 2))
+        p = np.empty((self.n_cells, 2))
+        self._chk(self.lib.lb_reductions(self.h, _dp(m), _dp(p)))
+        return m, p
+
+    # ---- kernels
+    def set_kernel(self, kind: str = "auto", tile_x: int = 0, tile_y: int = 0):
+        self._chk(self.lib.lb_set_kernel(self.h, KERNELS[kind], int(tile_x), int(tile_y)))
+        return self
+
+    def kernel(self):
+        k, tx, ty = C.c_int(), C.c_int(), C.c_int()
+        self._chk(self.lib.lb_get_kernel(self.h, C.byref(k), C.byref(tx), C.byref(ty)))
+        return KERNEL_NAMES[k.value], tx.value, ty.value
+
+    def autotune(self, cache_path: Optional[str] = None):
+        self._chk(self.lib.lb_autotune(self.h, cache_path.encode() if cache_path else None))
+        return self.kernel()
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.lb_steps_done(self.h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.lb_kernel_launches(self.h))
+
+    @property
+    def stream_ptr(self) -> int:
+        return int(self.lib.lb_stream(self.h) or 0)
+
+
+def hb_fit(shear_rate, sigma, beta_lo: float = 0.02, beta_hi: float = 3.0):
+    """Herschel-Bulkley fit sigma = sigma_Y + A S^beta (lb_hb_fit)."""
+    S = np.ascontiguousarray(shear_rate, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    out = np.empty(4)
+    L.check(L.load().lb_hb_fit(_dp(S), _dp(sg), int(S.size), float(beta_lo), float(beta_hi), _dp(out)))
+    return dict(sigma_y=float(out[0]), A=float(out[1]), beta=float(out[2]), rss=float(out[3]))

@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, on the
+same seeded inputs.
+
+Tolerances (written per test) follow from the arithmetic:
+  * FP64 storage/arithmetic: differences come only from the order of additions
+    and fused multiply-adds; one step stays within ~1e-15 of f, and 1000 steps
+    of a relaxing state within 1e-12 of rho.
+  * FP32 (eps = 6e-8): one step differs by the rounding of the loaded f
+    (|f| < 0.5) plus the force/shift error, a few ulp; 4e-7 absolute bounds it.
+    Over 1000 steps of a relaxing (non-demixing) state, max |d rho| <= 1e-5.
+  * FP16-shifted storage (eps_16 = 4.9e-4 on |g| <= 0.06): one rounding of g per
+    step, <= 3.5e-5 absolute on f.
+A demixing state (spinodal growth) amplifies any difference exponentially;
+there the comparison stops before the growth phase, and longer runs are
+compared through exact invariants (mass) instead.
+"""
+import numpy as np
+import pytest
+
+from paper_1004_5058_gb300 import inputs as I
+from tests._util import max_abs, oracle_runs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def lattice(cells, prec, kernel="generic", tile=(0, 0)):
+    from paper_1004_5058_gb300 import Lattice
+    lat = Lattice(cells, prec)
+    if kernel == "tiled":
+        from paper_1004_5058_gb300._lib import LBError
+        try:
+            lat.set_kernel("tiled", *tile)
+        except LBError as e:
+            lat.close()
+            pytest.skip("tiled kernel unsupported here: %s" % e)
+    else:
+        lat.set_kernel(kernel)
+    return lat
+
+
+KERNELS = ["generic", "tiled"]
+
+
+def evolved_state(cell, steps, seed):
+    from oracle import lb as orc
+    ra, rb = I.random_fields(cell.nx, cell.ny, seed=seed)
+    ux = uy = None
+    if cell.bc == 1:
+        ux, uy = I.couette_velocity(cell.nx, cell.ny, cell.u_wall)
+    r = orc.Run(cell, ra[0], rb[0], None if ux is None else ux[0], None if uy is None else uy[0])
+    r.step(steps)
+    return r
+
+
+# ------------------------------------------------------------ one step --
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 2e-15), ("fp32", 4e-7), ("fp16", 3.5e-5)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_one_step_from_evolved_state(kernel, prec, tol, bc):
+    cell = I.make_cell("paper", nx=64, ny=48, g_ab=0.405, bc=bc, u_wall=0.02 if bc else 0.0)
+    from oracle import lb as orc
+    r = evolved_state(cell, 400, seed=31)
+    f0 = r.f.copy()
+    f1, obs, prof = orc.step(cell, f0, want_profile=True)
+    with lattice([cell], prec, kernel) as lat:
+        lat.set_populations(f0[None])
+        start = lat.get_populations()[0]
+        lat.set_sampling(0, 1).step(1)
+        g1 = lat.get_populations()[0]
+        sigma, S, _ = lat.shear_stress()
+        ub, ns = lat.profile()
+    # compare the update itself, from the state the device holds after rounding
+    f1_from_start, obs_s, prof_s = orc.step(cell, start, want_profile=True)
+    assert max_abs(g1, f1_from_start) <= tol
+    if prec == "fp64":
+        assert max_abs(g1, f1) <= tol
+    assert ns == 1
+    # observables of the step, from the same start: FP64 sums of FP32/FP64 site values
+    otol = 1e-14 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(ub[0], prof_s / cell.nx, rtol=0, atol=otol)
+    if bc == 1:
+        ref_sigma = 0.5 * (obs_s["pi_top"] - obs_s["pi_bot"]) / cell.nx
+        assert abs(sigma[0] - ref_sigma) <= otol
+
+
+# ------------------------------------------------------------- C1 runs --
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_c1_periodic_1000_steps_paper_couplings(kernel, prec, tol):
+    """64x64 fully periodic, the paper's footnote couplings, random init, 1000 steps."""
+    cell = I.make_cell("paper", nx=64, ny=64)
+    ra, rb = I.random_fields(64, 64, seed=1004)
+    with lattice([cell], prec, kernel) as lat:
+        lat.init_fields(ra, rb).step(1000)
+        ga, gb, gu, gv = lat.fields()
+        mass, mom = lat.reductions()
+    (r,) = oracle_runs([cell], ra, rb, steps=1000)
+    oa, ob, ou, ov = r.fields()
+    assert max_abs(ga[0], oa) <= tol and max_abs(gb[0], ob) <= tol
+    assert max_abs(gu[0], ou) <= tol and max_abs(gv[0], ov) <= tol
+    m0 = (ra.sum(), rb.sum())
+    mtol = 1e-13 if prec == "fp64" else 1e-5
+    assert abs(mass[0, 0] - m0[0]) / m0[0] <= mtol and abs(mass[0, 1] - m0[1]) / m0[1] <= mtol
+    assert abs(mom[0]).max() / (m0[0] + m0[1]) <= (1e-13 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol,steps", [("fp64", 1e-11, 1000), ("fp32", 1e-5, 150)])
+def test_c1_periodic_demixing(kernel, prec, tol, steps):
+    """Same box with G_AB = 0.405 (demixing).  FP64 follows the oracle through the
+    spinodal growth; FP32 is compared before the growth phase, and mass is
+    checked after 1000 steps."""
+    cell = I.make_cell("paper", nx=64, ny=64, g_ab=0.405)
+    ra, rb = I.random_fields(64, 64, seed=1004)
+    with lattice([cell], prec, kernel) as lat:
+        lat.init_fields(ra, rb).step(steps)
+        ga, gb, _, _ = lat.fields()
+        lat.step(1000 - steps)
+        mass, _ = lat.reductions()
+    (r,) = oracle_runs([cell], ra, rb, steps=steps)
+    oa, ob, _, _ = r.fields()
+    assert max_abs(ga[0], oa) <= tol and max_abs(gb[0], ob) <= tol
+    mtol = 1e-13 if prec == "fp64" else 1e-5
+    assert abs(mass[0, 0] - ra.sum()) / ra.sum() <= mtol
+
+
+# ------------------------------------------------------------- Couette --
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol,sig_tol", [("fp64", 1e-12, 1e-13), ("fp32", 2e-5, 1e-7)])
+def test_couette_fields_and_stress(kernel, prec, tol, sig_tol):
+    """sig_tol: absolute on sigma_xy (~6e-5 here): each wall link's momentum is
+    a difference of O(0.03) populations, so FP32 leaves ~1e-8 per site and the
+    FP32/FP64 field drift over 400 steps adds to it."""
+    nx, ny, U = 64, 64, 0.01
+    cell = I.make_cell("paper", nx=nx, ny=ny, bc=1, u_wall=U)
+    ra, rb = I.random_fields(nx, ny, seed=3)
+    ux, uy = I.couette_velocity(nx, ny, U)
+    with lattice([cell], prec, kernel) as lat:
+        lat.init_fields(ra, rb, ux, uy).set_sampling(100, 5).step(400)
+        ga, gb, gu, _ = lat.fields()
+        sigma, S, Sb = lat.shear_stress()
+        ub, ns = lat.profile()
+    (r,) = oracle_runs([cell], ra, rb, ux, uy, steps=400, sampling=(100, 5))
+    oa, ob, ou, _ = r.fields()
+    osig, oS, oSb, oub = r.shear()
+    assert ns == r.acc.n_samples == 61
+    assert max_abs(ga[0], oa) <= tol and max_abs(gu[0], ou) <= tol
+    np.testing.assert_allclose(ub[0], oub, rtol=0, atol=tol * U * 10)
+    assert abs(sigma[0] - osig) <= sig_tol
+    assert abs(S[0] - oS) <= tol * abs(oS) * 10 + 1e-15
+    assert abs(Sb[0] - oSb) <= tol * abs(oSb) * 10 + 1e-15
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batched_cells_each_match_own_oracle(kernel):
+    """Four cells with different wall speeds and couplings in one handle."""
+    nx, ny = 64, 32
+    cells = [I.make_cell("paper", nx=nx, ny=ny, bc=1, u_wall=u, g_ab=g)
+             for u, g in [(1e-3, 0.3), (3e-3, 0.35), (1e-2, 0.405), (2e-2, 0.45)]]
+    ra, rb = I.random_fields(nx, ny, n_cells=4, seed=9)
+    ux, uy = I.couette_velocity(nx, ny, [c.u_wall for c in cells], n_cells=4)
+    with lattice(cells, "fp64", kernel) as lat:
+        lat.init_fields(ra, rb, ux, uy).set_sampling(50, 10).step(120)
+        ga, gb, _, _ = lat.fields()
+        sigma, S, _ = lat.shear_stress()
+    runs = oracle_runs(cells, ra, rb, ux, uy, steps=120, sampling=(50, 10))
+    for c, r in enumerate(runs):
+        oa, ob, _, _ = r.fields()
+        assert max_abs(ga[c], oa) <= 1e-12 and max_abs(gb[c], ob) <= 1e-12
+        osig, oS, _, _ = r.shear()
+        assert sigma[c] == pytest.approx(osig, rel=1e-9, abs=1e-16)
+        assert S[c] == pytest.approx(oS, rel=1e-9, abs=1e-16)
+
+
+# -------------------------------------------------------- ragged shapes --
+@pytest.mark.parametrize("nx,ny,bc", [(37, 23, 0), (37, 23, 1), (5, 5, 0), (130, 9, 1), (96, 70, 1)])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_ragged_and_small_shapes(nx, ny, bc, kernel):
+    cell = I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=bc, u_wall=0.01 if bc else 0.0)
+    ra, rb = I.random_fields(nx, ny, seed=nx * 100 + ny)
+    with lattice([cell], "fp64", kernel) as lat:
+        lat.init_fields(ra, rb).step(50)
+        ga, gb, _, _ = lat.fields()
+    (r,) = oracle_runs([cell], ra, rb, steps=50)
+    oa, ob, _, _ = r.fields()
+    assert max_abs(ga[0], oa) <= 1e-13 and max_abs(gb[0], ob) <= 1e-13
+
+
+# ----------------------------------------------------------- the ABI --
+def test_error_paths_and_state():
+    from paper_1004_5058_gb300 import Lattice
+    from paper_1004_5058_gb300._lib import LBError, LB_ERR_NONFINITE, LB_ERR_STATE
+    cell = I.make_cell("paper", nx=32, ny=32)
+    with Lattice([cell], "fp32") as lat:
+        with pytest.raises(LBError) as e:
+            lat.step(1)  # nothing loaded yet
+        assert e.value.status == LB_ERR_STATE
+        ra, rb = I.random_fields(32, 32)
+        lat.init_fields(ra, rb).step(0).sync()
+        assert lat.steps_done == 0
+        bad = ra.copy()
+        bad[0, 3, 4] = np.nan
+        lat.init_fields(bad, rb).step(3)
+        with pytest.raises(LBError) as e:
+            lat.fields()
+        assert e.value.status == LB_ERR_NONFINITE
+        with pytest.raises(LBError) as e:
+            lat.step(1)
+        assert e.value.status == LB_ERR_STATE
+        lat.init_fields(ra, rb).step(5)  # a fresh state clears the error
+        lat.fields()
+        assert lat.steps_done == 5
+        assert lat.kernel_launches > 0
+
+
+def test_autotune_keeps_state_and_caches(tmp_path):
+    from paper_1004_5058_gb300 import Lattice
+    cell = I.make_cell("paper", nx=256, ny=128, g_ab=0.405)
+    ra, rb = I.random_fields(256, 128)
+    cache = str(tmp_path / "tune.txt")
+    with Lattice([cell], "fp32") as lat:
+        lat.init_fields(ra, rb).step(7)
+        before = lat.get_populations()
+        choice = lat.autotune(cache)
+        after = lat.get_populations()
+        assert np.array_equal(before, after)
+        assert lat.steps_done == 7
+    with Lattice([cell], "fp32") as lat2:
+        lat2.init_fields(ra, rb)
+        assert lat2.autotune(cache) == choice

@@ -333,3 +333,28 @@ def test_shear_wave_viscosity(tau):
     rate = -math.log(amp() / a0) / (r.t - t0)
     nu = (tau - 0.5) / 3.0
     assert rate == pytest.approx(nu * k * k, rel=2e-2)
+
+
+# -------------------------------------------------------- Herschel-Bulkley --
+@pytest.mark.parametrize("sy,A,beta", [(1.5e-4, 2e-2, 0.5), (1.5e-4, 5e-3, 0.25), (2e-5, 0.1, 1.3)])
+def test_hb_oracle_recovers_noiseless(sy, A, beta):
+    from oracle import hbfit
+    S = np.logspace(-5, -2, 16)
+    r = hbfit.fit(S, sy + A * S ** beta)
+    assert r["beta"] == pytest.approx(beta, rel=1e-8)
+    assert r["A"] == pytest.approx(A, rel=1e-7)
+    assert r["sigma_y"] == pytest.approx(sy, rel=1e-6, abs=1e-12)
+    assert r["rss"] < 1e-20
+
+
+def test_hb_oracle_misfit_has_single_minimum():
+    """For noiseless HB data the residual as a function of beta decreases to
+    the true exponent and increases after it (variable projection is well posed)."""
+    from oracle import hbfit
+    S = np.logspace(-5, -2, 16)
+    sig = 1.5e-4 + 5e-3 * S ** 0.25
+    bs = np.linspace(0.05, 1.5, 59)
+    r = np.array([hbfit._rss(S, sig, b)[0] for b in bs])
+    k = int(np.argmin(r))
+    assert abs(bs[k] - 0.25) <= 0.03
+    assert np.all(np.diff(r[: k + 1]) <= 1e-30) and np.all(np.diff(r[k:]) >= -1e-30)
