@@ -1,0 +1,385 @@
+"""Benchmark of the fused two-species multirange LB step on GB300.
+
+Workload (default): a batch of 8 Couette cells of 1024 x 1024 sites, FP32, the
+paper's footnote couplings with G_AB = 0.405, walls at U = 1e-4 .. 1e-2 (8
+log-spaced speeds), seeded random densities and the linear Couette start.  One
+benchmark step = 100 lattice time steps of every cell (CUDA-graph chunks),
+with the FP64 shear-stress/profile reductions every 10 steps.
+
+value    MLUPS = (cells * nx * ny) * 100 * K / device time of K steps, summed over ranks
+e2e      same metric through the C ABI with host buffers: per step, lb_init_fields
+         from pinned host arrays (H2D), 100 time steps, lb_shear_stress and
+         lb_get_profile (D2H), and the Herschel-Bulkley fit of the 8 points
+roofline fused-kernel HBM roofline: algorithmic bytes (18 populations read + 18
+         written per site update) / mean kernel duration from CUDA events on
+         the library's stream, against the measured copy bandwidth
+cpu_baseline the FP64 oracle on this host's cores, on a bounded sample
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own 8-cell batch (weak scaling, no data
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (2-species site updates/s) and % of HBM roofline at 1 GB300; flow-curve points/s"
+UNIT = "MLUPS"
+BYTES_PER_SITE = {"fp32": 144, "fp16": 72, "fp64": 288}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--cells", type=int, default=8)
+    ap.add_argument("--chunk", type=int, default=100, help="lattice time steps per benchmark step")
+    ap.add_argument("--every", type=int, default=10, help="sampling interval of the FP64 reductions")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "tiled"])
+    ap.add_argument("--tile", default="", help="TXxTY for the tiled kernel (default: autotune)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_cells(nx, ny, n_cells, rank):
+    from paper_1004_5058_gb300 import inputs as I
+    speeds = I.log_spaced(1e-4, 1e-2, n_cells) if n_cells > 1 else [1e-3]
+    return [I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=u) for u in speeds]
+
+
+def workload_fields(nx, ny, cells, seed):
+    from paper_1004_5058_gb300 import inputs as I
+    ra, rb = I.random_fields(nx, ny, n_cells=len(cells), seed=seed)
+    ux, uy = I.couette_velocity(nx, ny, [c.u_wall for c in cells], n_cells=len(cells))
+    return ra, rb, ux, uy
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    for f in ("lb_tiled.cu", "lb_common.cuh", "tma.cuh"):
+        with open(os.path.join(ROOT, "paper_1004_5058_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(precision, nx, ny, n_cells):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    scaled to this workload's sites, if it was taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "fused_step_dram.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(precision)
+    if not e or d.get("source_digest") != source_digest():
+        return None
+    per_site = float(e["dram_bytes_per_launch"]) / float(e["sites_per_launch"])
+    return per_site * nx * ny * n_cells
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(args, seconds):
+    """The FP64 oracle, as it stands, on this host's cores: one cell of the
+    workload, as many time steps as fit in about `seconds`."""
+    from oracle import lb as orc
+    cells = workload_cells(args.nx, args.ny, args.cells, 0)
+    cell = cells[len(cells) // 2]
+    ra, rb, ux, uy = workload_fields(args.nx, args.ny, [cell], seed=1004)
+    run = orc.Run(cell, ra[0], rb[0], ux[0], uy[0])
+    run.set_sampling(0, args.every)
+    cores = orc.max_threads()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        run.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 100000:
+            break
+    mlups = args.nx * args.ny * steps / el / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "1 cell of %dx%d (Couette U=%.3g), %d FP64 time steps in %.1f s" %
+                      (args.nx, args.ny, cell.u_wall, steps, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    K, W = args.steps, args.warmup
+    per_step = max(1.0, min(args.cpu_seconds, 60.0 / max(1, K + W)))
+    from oracle import lb as orc
+    cells = workload_cells(args.nx, args.ny, args.cells, 0)
+    cell = cells[len(cells) // 2]
+    ra, rb, ux, uy = workload_fields(args.nx, args.ny, [cell], seed=1004)
+    run = orc.Run(cell, ra[0], rb[0], ux[0], uy[0])
+    run.set_sampling(0, args.every)
+
+    def one_step():
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < per_step:
+            run.step(1)
+            n += 1
+        return n, time.perf_counter() - t0
+
+    for _ in range(W):
+        one_step()
+    tot_n, tot_t = 0, 0.0
+    for _ in range(K):
+        n, t = one_step()
+        tot_n += n
+        tot_t += t
+    mlups = args.nx * args.ny * tot_n / tot_t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+        "warmup": W, "ms_per_step": 1e3 * tot_t / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "couette %dx%d x %d cells, FP64 oracle on host cores (1 cell sampled)" %
+                               (args.nx, args.ny, args.cells), "nx": args.nx, "ny": args.ny, "cells": args.cells},
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
+                         "sample": "1 cell of %dx%d, %d FP64 time steps in %.1f s over %d timed steps" %
+                                   (args.nx, args.ny, tot_n, tot_t, K)},
+        "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    import __graft_entry__ as g
+    g.build()
+    from paper_1004_5058_gb300 import Lattice, hb_fit
+
+    nx, ny, n_cells, chunk = args.nx, args.ny, args.cells, args.chunk
+    cells = workload_cells(nx, ny, n_cells, rank)
+    ra, rb, ux, uy = workload_fields(nx, ny, cells, seed=1004 + rank)
+    lat = Lattice(cells, args.precision)
+    lat.init_fields(ra, rb, ux, uy)
+    if args.kernel != "auto" or args.tile:
+        tx, ty = (int(v) for v in args.tile.split("x")) if args.tile else (0, 0)
+        lat.set_kernel(args.kernel if args.kernel != "auto" else "tiled", tx, ty)
+    else:
+        lat.autotune(os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
+                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    kernel, tx, ty = lat.kernel()
+    stream = torch.cuda.ExternalStream(lat.stream_ptr)
+    lat.set_sampling(0, args.every)
+
+    def barrier():
+        if pg:
+            pg.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        lat.step(chunk)
+    lat.sync()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = lat.kernel_launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lat.step(chunk)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    launches = lat.kernel_launches - launches0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    sites = nx * ny * n_cells
+    value = sites * chunk * args.steps * world / (ms * 1e-3) / 1e6
+    sigma, S, Sb = lat.shear_stress()
+
+    # roofline: fused kernel alone (sampling off), CUDA events on the same stream
+    lat.set_sampling(0, 0)
+    n_roof = max(50, min(400, int(2e9 / (sites * BYTES_PER_SITE[args.precision]) * 20)))
+    lat.step(20)
+    lat.sync()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    l0 = lat.kernel_launches
+    r0.record(stream)
+    lat.step(n_roof)
+    r1.record(stream)
+    r1.synchronize()
+    kernels_per_step = (lat.kernel_launches - l0) / n_roof
+    t_launch = r0.elapsed_time(r1) * 1e-3 / n_roof / kernels_per_step
+    alg_bytes = BYTES_PER_SITE[args.precision] * sites
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (t_launch if kernels_per_step == 1 else t_launch * kernels_per_step) / 1e9
+    traffic = committed_traffic(args.precision, nx, ny, n_cells) if kernel == "tiled" else None
+
+    # end to end through the C ABI with host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_ra, h_rb, h_ux, h_uy = pin(ra), pin(rb), pin(ux), pin(uy)
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        lat.init_fields(h_ra, h_rb, h_ux, h_uy)
+        lat.set_sampling(chunk // 2, args.every)
+        lat.step(chunk)
+        s, r, _ = lat.shear_stress()
+        lat.profile()
+        ok = np.isfinite(r) & (r > 0)
+        if ok.sum() >= 3:
+            hb_fit(r[ok], s[ok])
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = sites * chunk * e2e_steps * world / e2e_s / 1e6
+    h2d = 4 * sites * 8
+    d2h = n_cells * 8 * 2 + n_cells * 8 * 2 + n_cells * ny * 8 + n_cells * 8 * 2
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "couette batch: %d cells of %dx%d, FP32, %d time steps per step, FP64 "
+                               "reductions every %d" % (n_cells, nx, ny, chunk, args.every),
+                   "cells": n_cells, "nx": nx, "ny": ny, "lattice_steps_per_step": chunk,
+                   "sampling_every": args.every, "precision": args.precision, "kernel": kernel,
+                   "tile": [tx, ty], "couplings": "paper footnote, G_AB=0.405", "u_wall": "1e-4..1e-2 log",
+                   "l2": "inputs larger than L2 (%.2f GB populations, ping-pong)" %
+                         (2 * sites * BYTES_PER_SITE[args.precision] / 2 / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "%s copy bandwidth" % peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": t_launch * 1e3,
+                     "bytes_per_site_update": BYTES_PER_SITE[args.precision]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "lattice_steps_per_step": chunk},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "flow_curve": {"sigma_xy": [float(v) for v in sigma], "shear_rate": [float(v) for v in S]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -87,6 +87,11 @@ template <> struct Store<__half> {
     __device__ static void st(__half* p, long long k, C v, C shift) { p[k] = __float2half_rn(v - shift); }
 };
 
+// Stored element -> compute type (shift not included).
+__device__ inline float to_c(float v) { return v; }
+__device__ inline double to_c(double v) { return v; }
+__device__ inline float to_c(__half v) { return __half2float(v); }
+
 template <class C> __device__ inline C expm1_c(C x);
 template <> __device__ inline float expm1_c<float>(float x) { return expm1f(x); }
 template <> __device__ inline double expm1_c<double>(double x) { return expm1(x); }
@@ -139,7 +144,8 @@ template <class C> struct Collided {
 //   u      = j / (rho_A + rho_B)                                (barycentric)
 //   F_s    = -psi_s (G^a S1 + G^r S2) - (G_AB/rho0) rho_s X       (Eq. (FFF))
 //   u_s    = u + tau F_s/rho_s = u - tau[(psi_s/rho_s)(G^a S1 + G^r S2) + (G_AB/rho0) X]
-//   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau
+//   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau, i = 1..8
+//   f*_0s  = rho_s - sum_{i>=1} f*_is   (the same value in exact arithmetic)
 // psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
 // vanishing species density.
 template <class C>
@@ -167,12 +173,17 @@ __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi
         const C usx = ux - tau * (por * Gx + gx * sm[s].xx);
         const C usy = uy - tau * (por * Gy + gx * sm[s].xy);
         const C usq = C(1.5) * (usx * usx + usy * usy);
+        C moving = C(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
+        for (int i = 1; i < 9; ++i) {
             const C cu = C(q_cx(i)) * usx + C(q_cy(i)) * usy;
             const C feq = C(q_w(i)) * rho[s] * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
             out.fs[s][i] = f[s][i] + omega * (feq - f[s][i]);
+            moving += out.fs[s][i];
         }
+        // BGK conserves rho_s; closing the rest population on it keeps the rounded
+        // weights (sum of float(w_i) = 1 + 7.5e-9) from biasing the mass each step.
+        out.fs[s][0] = rho[s] - moving;
     }
     out.Fx = Fx;
     out.Fy = Fy;

@@ -1,30 +1,452 @@
-// Tiled single-pass kernel family (placeholder until the TMA kernel lands).
+// Tiled single-pass kernel family: the whole time step (moments, pseudopotential,
+// 25-point forces of Eq. (FFF), shifted BGK collision of Eq. (be), streaming)
+// in one pass over the populations.
+//
+// Work item = one column strip of TX sites x one segment of TY rows of one cell.
+// A CTA of TX threads (one column each) walks its segment row by row:
+//   * TMA (cp.async.bulk.tensor, 4-D map [cell][q][y][x]) brings whole rows of all
+//     18 populations into a ring of D shared-memory slots, several rows ahead,
+//     each slot completing on its own mbarrier; a row is TX main columns plus
+//     16-byte halo boxes on both sides (periodic wrap in x by coordinates);
+//   * when row y+2 lands, its rho_s and psi_s (for the TX columns and 2 halo
+//     columns per side) go into a 6-row ring, so rows y-2..y+2 of psi/rho are
+//     on chip when row y is collided: the 25-point stencil reads shared memory;
+//   * row y is collided from its populations still in the slot ring and pushed
+//     to the other ping-pong buffer with plain coalesced stores (x-shifted by
+//     -1/0/+1 element), bounce-back rows handled in place.
+// HBM traffic per site update is one read and one write of the 18 populations;
+// halo rows/columns are re-read by neighbouring work items (mostly from L2).
+// The grid is persistent (CTAs loop over work items).  Every mbarrier wait is
+// bounded: on timeout the CTA records ERR_TIMEOUT, drains its copies in flight
+// (also bounded) and leaves.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "lb_internal.h"
+#include "tma.cuh"
 
 namespace lbhb {
 
-struct TiledPlan {
-    int dummy;
+constexpr int RING = 6;  // psi/rho rows on chip: 5 read by a collision + 1 being written
+
+template <class C> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+__host__ __device__ constexpr int al128(int b) { return (b + 127) / 128 * 128; }
+
+struct SlotGeom {
+    int main_b, halo_b, main_al, halo_al, slot_b, tx_bytes, halo;
 };
 
-bool tiled_supported(const Geom&, int, int, int) { return false; }
-int tiled_partials_nbx(const Geom& g, int tile_x) { return (g.nx + tile_x - 1) / tile_x; }
-TiledPlan* tiled_create(const Geom&, int, int, void*, void*, int, int, const char** err_msg)
+__host__ __device__ inline SlotGeom slot_geom(int tx, int elem)
 {
-    if (err_msg) *err_msg = "tiled kernel not built";
-    return nullptr;
+    SlotGeom s;
+    s.halo = 16 / elem;
+    s.main_b = 18 * tx * elem;
+    s.halo_b = 18 * s.halo * elem;
+    s.main_al = al128(s.main_b);
+    s.halo_al = al128(s.halo_b);
+    s.slot_b = s.main_al + 2 * s.halo_al;
+    s.tx_bytes = s.main_b + 2 * s.halo_b;
+    return s;
 }
-void tiled_destroy(TiledPlan* p) { delete p; }
-void tiled_tiles(const TiledPlan*, int* tx, int* ty) { *tx = *ty = 0; }
+
+struct TiledPlan {
+    Geom g;
+    int elem, bc, tx, ty, depth;
+    int n_strips, n_seg, grid;
+    size_t smem;
+    CUtensorMap tm_main[2], tm_halo[2];
+    void* f[2];
+};
+
+template <class T, int TX, bool SAMPLE>
+__global__ void __launch_bounds__(TX) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
+                                                        const __grid_constant__ CUtensorMap tm_halo,
+                                                        T* __restrict__ fout, Geom g, int bc, int ty, int depth,
+                                                        int n_strips, int n_seg,
+                                                        const CellDev* __restrict__ cells,
+                                                        double* __restrict__ prof_part,
+                                                        double* __restrict__ wall_part, unsigned* __restrict__ err)
+{
+    using C = typename Store<T>::C;
+    using C2 = typename V2<C>::t;
+    constexpr int E = (int)sizeof(T);
+    constexpr int H = 16 / E;
+    constexpr int W = TX + 4;  // psi/rho ring row: columns -2 .. TX+1
+    const SlotGeom sg = slot_geom(TX, E);
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* fring = smem;
+    C2* psi_ring = reinterpret_cast<C2*>(smem + (size_t)depth * sg.slot_b);
+    C2* rho_ring = psi_ring + RING * W;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(rho_ring + RING * W);
+
+    const int t = threadIdx.x;
+    if (t == 0) {
+        for (int d = 0; d < depth; ++d) mbar_init(&bars[d], 1);
+        fence_mbar_init();
+        prefetch_tensormap(&tm_main);
+        prefetch_tensormap(&tm_halo);
+    }
+    __syncthreads();
+
+    const long long per_cell = (long long)n_strips * n_seg;
+    const long long items = per_cell * g.n_cells;
+    uint32_t nrow = 0;     // rows this CTA has issued and consumed in earlier items
+    uint32_t issued = 0;   // thread 0: rows issued in the current item
+    bool aborted = false;
+
+    for (long long w = blockIdx.x; w < items && !aborted; w += gridDim.x) {
+        const int cell = (int)(w / per_cell);
+        const int rem = (int)(w % per_cell);
+        const int seg = rem / n_strips, strip = rem % n_strips;
+        const int x0 = strip * TX, y0 = seg * ty;
+        const int rows = min(ty, g.ny - y0);
+        const int R = rows + 4;  // logical rows y0-2 .. y0+rows+1
+        const CellDev& p = cells[cell];
+        C shift[2][9];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) shift[s][i] = Store<T>::shifted ? C(q_w(i) * p.rho_bar[s]) : C(0);
+        const int xl = x0 >= H ? x0 - H : g.nx - H;
+        const int xr = x0 + TX < g.nx ? x0 + TX : 0;
+
+        __syncthreads();  // rings of the previous item are no longer read
+
+        auto issue = [&](int k) {
+            const uint32_t n = nrow + (uint32_t)k;
+            const int slot = (int)(n % (uint32_t)depth);
+            unsigned char* dst = fring + (size_t)slot * sg.slot_b;
+            const int yp = stencil_row(y0 - 2 + k, g.ny, bc);
+            mbar_arrive_expect_tx(&bars[slot], (uint32_t)sg.tx_bytes);
+            tma_load_4d(dst, &tm_main, x0, yp, 0, cell, &bars[slot]);
+            tma_load_4d(dst + sg.main_al, &tm_halo, xl, yp, 0, cell, &bars[slot]);
+            tma_load_4d(dst + sg.main_al + sg.halo_al, &tm_halo, xr, yp, 0, cell, &bars[slot]);
+        };
+        if (t == 0) {
+            issued = 0;
+            for (int k = 0; k < depth && k < R; ++k) issue(k), ++issued;
+        }
+        auto wait_row = [&](int k) -> bool {
+            const uint32_t n = nrow + (uint32_t)k;
+            return mbar_wait_bounded(&bars[n % (uint32_t)depth], (n / (uint32_t)depth) & 1u);
+        };
+        // rho_s, psi_s of logical row k into ring row k % RING
+        auto psi_stage = [&](int k) {
+            const unsigned char* base = fring + (size_t)((nrow + (uint32_t)k) % (uint32_t)depth) * sg.slot_b;
+            const int ring = (k % RING) * W;
+            auto site = [&](const T* src, int stride, int col, int pos) {
+                C r[2];
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    C acc = C(0);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const T v = src[(s * 9 + i) * stride + col];
+                        acc += Store<T>::shifted ? to_c(v) + shift[s][i] : to_c(v);
+                    }
+                    r[s] = acc;
+                }
+                const C rho0 = C(p.rho0), ir0 = C(1.0 / p.rho0);
+                C2 ps, rh;
+                ps.x = psi_of<C>(r[0], rho0, ir0);
+                ps.y = psi_of<C>(r[1], rho0, ir0);
+                rh.x = r[0];
+                rh.y = r[1];
+                psi_ring[ring + pos] = ps;
+                rho_ring[ring + pos] = rh;
+            };
+            site(reinterpret_cast<const T*>(base), TX, t, t + 2);
+            if (t < 4) {
+                if (t < 2)
+                    site(reinterpret_cast<const T*>(base + sg.main_al), H, H - 2 + t, t);
+                else
+                    site(reinterpret_cast<const T*>(base + sg.main_al + sg.halo_al), H, t - 2, TX + t);
+            }
+        };
+
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) {
+            ok = wait_row(k) && ok;
+            psi_stage(k);
+        }
+        for (int j = 0; j < rows; ++j) {
+            ok = wait_row(j + 4) && ok;
+            psi_stage(j + 4);
+            // barrier: psi/rho of row j+4 visible, collision of row j+1 finished
+            // everywhere; it also tells every thread whether any wait ran out
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                aborted = true;
+                break;
+            }
+            if (t == 0) {
+                if (j == 0) {
+                    if (depth < R) issue(depth), ++issued;
+                    if (depth + 1 < R) issue(depth + 1), ++issued;
+                } else if (j + 1 + depth < R) {
+                    issue(j + 1 + depth);
+                    ++issued;
+                }
+            }
+            // ---- collide logical row k = j + 2 (lattice row y)
+            const int k = j + 2, y = y0 + j, x = x0 + t;
+            const T* fm = reinterpret_cast<const T*>(fring + (size_t)((nrow + (uint32_t)k) % (uint32_t)depth) * sg.slot_b);
+            C f[2][9];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const T v = fm[(s * 9 + i) * TX + t];
+                    f[s][i] = Store<T>::shifted ? to_c(v) + shift[s][i] : to_c(v);
+                }
+            int rb[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) rb[d] = ((k - 2 + d) % RING) * W + t + 2;
+            const C2 ps0 = psi_ring[rb[2]], rh0 = rho_ring[rb[2]];
+            C dpa[12], dpb[12], dra[4], drb[4];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                const int dx = hs_dx(q), dy = hs_dy(q);
+                const C2 pp = psi_ring[rb[2 + dy] + dx], pm = psi_ring[rb[2 - dy] - dx];
+                dpa[q] = pp.x - pm.x;
+                dpb[q] = pp.y - pm.y;
+                if (q < 4) {
+                    const C2 rp = rho_ring[rb[2 + dy] + dx], rm = rho_ring[rb[2 - dy] - dx];
+                    dra[q] = rp.x - rm.x;
+                    drb[q] = rp.y - rm.y;
+                }
+            }
+            Sums<C> sm[2];
+            sm[0] = stencil_sums<C>(dpa, drb);
+            sm[1] = stencil_sums<C>(dpb, dra);
+            const C rho[2] = {rh0.x, rh0.y}, psi[2] = {ps0.x, ps0.y};
+            Collided<C> c;
+            collide_site<C>(f, rho, psi, sm, p, c);
+
+            double dpx_site = 0.0;
+            const C u_top = C(p.u_wall), u_bot = C(-p.u_wall);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int yd = y + q_cy(i);
+                    if (bc == 1 && (yd < 0 || yd >= g.ny)) {
+                        C dpx;
+                        const C back = bounce<C>(i, c.fs[s][i], rho[s], yd < 0 ? u_bot : u_top, &dpx);
+                        Store<T>::st(fout, fidx(g, cell, s * 9 + q_opp(i), y, x), back, shift[s][q_opp(i)]);
+                        dpx_site += (double)dpx;
+                    } else {
+                        const int xd = wrap_x(x + q_cx(i), g.nx);
+                        const int ydd = yd < 0 ? yd + g.ny : (yd >= g.ny ? yd - g.ny : yd);
+                        Store<T>::st(fout, fidx(g, cell, s * 9 + i, ydd, xd), c.fs[s][i], shift[s][i]);
+                    }
+                }
+            if (SAMPLE) {
+                const C rt = rho[0] + rho[1];
+                C jx = C(0);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) jx += (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
+                double uphys = (double)((jx + C(0.5) * c.Fx) / rt);
+                if (!(rt > C(0)) || !isfinite((double)rho[0]) || !isfinite((double)rho[1])) atomicOr(err, ERR_NONFINITE);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    uphys += __shfl_down_sync(0xffffffffu, uphys, o);
+                    dpx_site += __shfl_down_sync(0xffffffffu, dpx_site, o);
+                }
+                if ((t & 31) == 0) {
+                    const int nbx = g.nx / 32, wg = x / 32;
+                    prof_part[((long long)cell * nbx + wg) * g.ny + y] = uphys;
+                    if (bc == 1 && (y == 0 || y == g.ny - 1))
+                        wall_part[((long long)cell * nbx + wg) * 2 + (y == 0 ? 1 : 0)] = dpx_site;
+                }
+            }
+        }
+        if (aborted) {
+            if (t == 0) {
+                atomicOr(err, ERR_TIMEOUT);
+                // drain the copies still in flight before shared memory is released
+                for (uint32_t k = 0; k < issued; ++k) {
+                    const uint32_t n = nrow + k;
+                    mbar_wait_bounded(&bars[n % (uint32_t)depth], (n / (uint32_t)depth) & 1u, 1u << 20);
+                }
+            }
+            __syncthreads();
+            break;
+        }
+        nrow += (uint32_t)R;
+    }
+}
+
+// ------------------------------------------------------------- host side --
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+static int depth_for(int tx, int elem)
+{
+    const SlotGeom sg = slot_geom(tx, elem);
+    // about 3 rows in flight, at most 96 KB of row slots
+    int d = 6;
+    while (d > 5 && (size_t)d * sg.slot_b > 96 * 1024) --d;
+    return d;
+}
+
+static size_t smem_bytes(int tx, int elem, int depth)
+{
+    const SlotGeom sg = slot_geom(tx, elem);
+    const int c2 = elem == 8 ? 16 : 8;
+    return (size_t)depth * sg.slot_b + (size_t)2 * RING * (tx + 4) * c2 + (size_t)depth * 8;
+}
+
+bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
+{
+    if (tile_x != 32 && tile_x != 64 && tile_x != 128 && tile_x != 256) return false;
+    if (tile_y < 1 || g.nx % tile_x != 0 || g.ny < 5) return false;
+    if (g.nx < tile_x || (g.nx * elem) % 16 != 0) return false;
+    if (smem_bytes(tile_x, elem, depth_for(tile_x, elem)) > 227 * 1024) return false;
+    return encode_fn() != nullptr;
+}
+
+int tiled_partials_nbx(const Geom& g, int) { return (g.nx + 31) / 32; }
+
+template <class T, int TX, bool S>
+static const void* kernel_ptr()
+{
+    return reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, S>);
+}
+
 template <class T>
-cudaError_t launch_tiled_step(TiledPlan*, int, const CellDev*, bool, double*, double*, unsigned*, cudaStream_t, int*)
+static const void* pick(int tx, bool sample)
 {
-    return cudaErrorNotSupported;
+    switch (tx) {
+    case 32: return sample ? kernel_ptr<T, 32, true>() : kernel_ptr<T, 32, false>();
+    case 64: return sample ? kernel_ptr<T, 64, true>() : kernel_ptr<T, 64, false>();
+    case 128: return sample ? kernel_ptr<T, 128, true>() : kernel_ptr<T, 128, false>();
+    default: return sample ? kernel_ptr<T, 256, true>() : kernel_ptr<T, 256, false>();
+    }
 }
+
+static const void* pick_any(int elem, int tx, bool sample)
+{
+    if (elem == 4) return pick<float>(tx, sample);
+    if (elem == 8) return pick<double>(tx, sample);
+    return pick<__half>(tx, sample);
+}
+
+static bool encode(CUtensorMap* m, void* base, const Geom& g, int elem, int box_x)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = elem == 4   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 18, (cuuint64_t)g.n_cells};
+    cuuint64_t strides[3] = {(cuuint64_t)g.pitch * elem, (cuuint64_t)g.plane * elem,
+                             (cuuint64_t)g.cellstride * elem};
+    cuuint32_t box[4] = {(cuuint32_t)box_x, 1, 18, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+TiledPlan* tiled_create(const Geom& g, int elem, int bc, void* f0, void* f1, int tile_x, int tile_y,
+                        const char** err_msg)
+{
+    if (!tiled_supported(g, elem, tile_x, tile_y)) {
+        if (err_msg) *err_msg = "shape/tile not supported by the tiled kernel";
+        return nullptr;
+    }
+    TiledPlan* p = new TiledPlan();
+    p->g = g;
+    p->elem = elem;
+    p->bc = bc;
+    p->tx = tile_x;
+    p->ty = tile_y;
+    p->depth = depth_for(tile_x, elem);
+    p->n_strips = g.nx / tile_x;
+    p->n_seg = (g.ny + tile_y - 1) / tile_y;
+    p->smem = smem_bytes(tile_x, elem, p->depth);
+    p->f[0] = f0;
+    p->f[1] = f1;
+    const int halo = 16 / elem;
+    for (int b = 0; b < 2; ++b)
+        if (!encode(&p->tm_main[b], b ? f1 : f0, g, elem, tile_x) || !encode(&p->tm_halo[b], b ? f1 : f0, g, elem, halo)) {
+            if (err_msg) *err_msg = "cuTensorMapEncodeTiled failed";
+            delete p;
+            return nullptr;
+        }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int occ = 1;
+    for (int s = 0; s < 2; ++s) {
+        const void* k = pick_any(elem, tile_x, s == 1);
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess) {
+            cudaGetLastError();
+            if (err_msg) *err_msg = "cudaFuncSetAttribute(max dynamic smem) failed";
+            delete p;
+            return nullptr;
+        }
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, tile_x, p->smem) != cudaSuccess || o < 1) {
+            cudaGetLastError();
+            if (err_msg) *err_msg = "tiled kernel does not fit on an SM";
+            delete p;
+            return nullptr;
+        }
+        occ = s == 0 ? o : std::min(occ, o);
+    }
+    const long long items = (long long)p->n_strips * p->n_seg * g.n_cells;
+    const long long slots = (long long)sms * occ;
+    p->grid = (int)std::min(items, slots);
+    return p;
+}
+
+void tiled_destroy(TiledPlan* p) { delete p; }
+
+void tiled_tiles(const TiledPlan* p, int* tx, int* ty)
+{
+    *tx = p->tx;
+    *ty = p->ty;
+}
+
+template <class T>
+cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool sample, double* prof_part,
+                              double* wall_part, unsigned* err, cudaStream_t st, int* n_launches)
+{
+    T* dst = reinterpret_cast<T*>(p->f[1 - src]);
+    const void* k = pick<T>(p->tx, sample);
+    Geom g = p->g;
+    int bc = p->bc, ty = p->ty, depth = p->depth, ns = p->n_strips, nseg = p->n_seg;
+    void* args[] = {(void*)&p->tm_main[src], (void*)&p->tm_halo[src], (void*)&dst, (void*)&g, (void*)&bc,
+                    (void*)&ty, (void*)&depth, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
+                    (void*)&wall_part, (void*)&err};
+    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid), dim3(p->tx), args, p->smem, st);
+    *n_launches += 1;
+    return e;
+}
+
 template cudaError_t launch_tiled_step<float>(TiledPlan*, int, const CellDev*, bool, double*, double*, unsigned*,
                                               cudaStream_t, int*);
 template cudaError_t launch_tiled_step<double>(TiledPlan*, int, const CellDev*, bool, double*, double*, unsigned*,
                                                cudaStream_t, int*);
 template cudaError_t launch_tiled_step<__half>(TiledPlan*, int, const CellDev*, bool, double*, double*, unsigned*,
                                                cudaStream_t, int*);
+
 }  // namespace lbhb
