@@ -198,7 +198,14 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
         return LB_OK;
     }
     if (k != LB_KERNEL_TILED) return fail(h, LB_ERR_INVALID, "lb_set_kernel: unknown kernel %d", (int)k);
-    if (tx == 0) tx = 64;
+    if (tx == 0) {
+        tx = 32;
+        for (int c : {128, 64})
+            if (h->nx % c == 0) {
+                tx = c;
+                break;
+            }
+    }
     if (ty == 0) ty = 64;
     if (!tiled_supported(h->g, h->elem, tx, ty))
         return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: tiled kernel does not support nx=%d ny=%d tile %dx%d",
