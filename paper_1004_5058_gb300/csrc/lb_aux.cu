@@ -21,7 +21,7 @@ __global__ void equilibrium_kernel(const double* __restrict__ src, T* __restrict
         for (int i = 0; i < 9; ++i) {
             const double cu = q_cx(i) * ux + q_cy(i) * uy;
             const double feq = q_w(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-            const C sh = Store<T>::shifted ? C(q_w(i) * cells[cell].rho_bar[s]) : C(0);
+            const C sh = Store<T>::shifted ? pop_shift<C>(i, params<C>(cells[cell]), s) : C(0);
             Store<T>::st(f, fidx(g, cell, s * 9 + i, y, x), C(feq), sh);
         }
     }
@@ -36,7 +36,7 @@ __global__ void export_kernel(const T* __restrict__ f, double* __restrict__ dst,
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, cq = blockIdx.z;
     if (x >= g.nx) return;
     const int cell = cq / 18, q = cq % 18, s = q / 9, i = q % 9;
-    const C sh = Store<T>::shifted ? C(q_w(i) * cells[cell].rho_bar[s]) : C(0);
+    const C sh = Store<T>::shifted ? pop_shift<C>(i, params<C>(cells[cell]), s) : C(0);
     dst[(((long long)cell * 18 + q) * g.ny + y) * g.nx + x] = (double)Store<T>::ld(f, fidx(g, cell, q, y, x), sh);
 }
 
@@ -48,7 +48,7 @@ __global__ void import_kernel(const double* __restrict__ src, T* __restrict__ f,
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, cq = blockIdx.z;
     if (x >= g.nx) return;
     const int cell = cq / 18, q = cq % 18, s = q / 9, i = q % 9;
-    const C sh = Store<T>::shifted ? C(q_w(i) * cells[cell].rho_bar[s]) : C(0);
+    const C sh = Store<T>::shifted ? pop_shift<C>(i, params<C>(cells[cell]), s) : C(0);
     Store<T>::st(f, fidx(g, cell, q, y, x), C(src[(((long long)cell * 18 + q) * g.ny + y) * g.nx + x]), sh);
 }
 
@@ -66,7 +66,7 @@ __global__ void fields_kernel(const T* __restrict__ f, double* __restrict__ dst,
         C v[9];
         C r = C(0);
         for (int i = 0; i < 9; ++i) {
-            const C sh = Store<T>::shifted ? C(q_w(i) * cells[cell].rho_bar[s]) : C(0);
+            const C sh = Store<T>::shifted ? pop_shift<C>(i, params<C>(cells[cell]), s) : C(0);
             v[i] = Store<T>::ld(f, fidx(g, cell, s * 9 + i, y, x), sh);
             r += v[i];
         }
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(RED_THREADS) state_sums_kernel(const T* __rest
             C v[9];
             C r = C(0);
             for (int i = 0; i < 9; ++i) {
-                const C sh = Store<T>::shifted ? C(q_w(i) * cells[cell].rho_bar[s]) : C(0);
+                const C sh = Store<T>::shifted ? pop_shift<C>(i, params<C>(cells[cell]), s) : C(0);
                 v[i] = Store<T>::ld(f, fidx(g, cell, s * 9 + i, y, x), sh);
                 r += v[i];
             }

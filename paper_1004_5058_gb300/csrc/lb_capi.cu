@@ -112,20 +112,28 @@ static void release(lb_handle* h)
     delete h;
 }
 
+template <class C>
+static void fill(ParamSet<C>& d, const lb_cell_params& c)
+{
+    d.tau = C(c.tau);
+    d.omega = C(1.0 / c.tau);
+    d.rho0 = C(c.rho0);
+    d.inv_rho0 = C(1.0 / c.rho0);
+    d.gab_over_rho0 = C(c.g_ab / c.rho0);
+    d.g1[0] = C(c.g_aa1);
+    d.g1[1] = C(c.g_bb1);
+    d.g2[0] = C(c.g_aa2);
+    d.g2[1] = C(c.g_bb2);
+    d.u_wall = C(c.u_wall);
+    d.rho_bar[0] = C(c.rho_bar_a);
+    d.rho_bar[1] = C(c.rho_bar_b);
+}
+
 static CellDev to_dev(const lb_cell_params& c)
 {
     CellDev d{};
-    d.tau = c.tau;
-    d.omega = 1.0 / c.tau;
-    d.rho0 = c.rho0;
-    d.gab_over_rho0 = c.g_ab / c.rho0;
-    d.g1[0] = c.g_aa1;
-    d.g1[1] = c.g_bb1;
-    d.g2[0] = c.g_aa2;
-    d.g2[1] = c.g_bb2;
-    d.u_wall = c.u_wall;
-    d.rho_bar[0] = c.rho_bar_a;
-    d.rho_bar[1] = c.rho_bar_b;
+    fill(d.d, c);
+    fill(d.f, c);
     return d;
 }
 

@@ -45,13 +45,25 @@ __host__ __device__ constexpr double hs_w2(int k)
 }
 
 // ------------------------------------------------------------ parameters --
-// Per-cell parameters as the kernels read them.
-struct CellDev {
-    double tau, omega, rho0, gab_over_rho0;
-    double g1[2], g2[2];  // G^a_ss, G^r_ss for s = A, B
-    double u_wall;        // top wall +u_wall, bottom wall -u_wall (Couette)
-    double rho_bar[2];    // FP16 shift reference
+// Per-cell parameters as stored on the device, in both compute precisions so
+// that FP32 kernels never touch the (slow) FP64 pipe for them.
+template <class C> struct ParamSet {
+    C tau, omega, rho0, inv_rho0, gab_over_rho0;
+    C g1[2], g2[2];  // G^a_ss, G^r_ss for s = A, B
+    C u_wall;        // top wall +u_wall, bottom wall -u_wall (Couette)
+    C rho_bar[2];    // FP16 shift reference
 };
+struct CellDev {
+    ParamSet<double> d;
+    ParamSet<float> f;
+};
+template <class C> __host__ __device__ inline const ParamSet<C>& params(const CellDev& c);
+template <> __host__ __device__ inline const ParamSet<double>& params<double>(const CellDev& c) { return c.d; }
+template <> __host__ __device__ inline const ParamSet<float>& params<float>(const CellDev& c) { return c.f; }
+
+// Shift of the FP16 storage, g_i = f_i - w_i rho_bar_s, in the compute type;
+// the same expression everywhere a population is stored or loaded.
+template <class C> __device__ inline C pop_shift(int i, const ParamSet<C>& p, int s) { return C(q_w(i)) * p.rho_bar[s]; }
 
 // Population array geometry: [cell][s][i][y][pitch], x fastest.
 struct Geom {
@@ -133,6 +145,45 @@ __device__ inline Sums<C> stencil_sums(const C dpsi[12], const C drho_other[4])
     return r;
 }
 
+// Shifted-velocity BGK collision of Eq. (be) for one species s at one site.
+//   F_s    = -psi_s (G^a S1 + G^r S2) - (G_AB/rho0) rho_s X       (Eq. (FFF))
+//   u_s    = u + tau F_s/rho_s = u - tau[(psi_s/rho_s)(G^a S1 + G^r S2) + (G_AB/rho0) X]
+//   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau, i = 1..8
+//   f*_0s  = rho_s - sum_{i>=1} f*_is   (the same value in exact arithmetic)
+// u is the barycentric velocity j / (rho_A + rho_B) of both species.
+// psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
+// vanishing species density.  Closing the rest population on rho_s keeps the
+// rounded weights (sum of float(w_i) = 1 + 7.5e-9) from biasing the mass.
+// *Fx, *Fy receive F_s (for the force-corrected velocity of the observables).
+template <class C>
+__device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C uy, const Sums<C>& sm, C ga, C gr,
+                                       const ParamSet<C>& p, C fs[9], C* Fx, C* Fy)
+{
+    const C tau = p.tau, omega = p.omega, gx = p.gab_over_rho0;
+    const C Gx = ga * sm.s1x + gr * sm.s2x;
+    const C Gy = ga * sm.s1y + gr * sm.s2y;
+    *Fx = -psi_s * Gx - gx * rho_s * sm.xx;
+    *Fy = -psi_s * Gy - gx * rho_s * sm.xy;
+    const C por = rho_s != C(0) ? psi_s / rho_s : C(1);
+    const C usx = ux - tau * (por * Gx + gx * sm.xx);
+    const C usy = uy - tau * (por * Gy + gx * sm.xy);
+    const C usq = C(1.5) * (usx * usx + usy * usy);
+    C moving = C(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const C cu = C(q_cx(i)) * usx + C(q_cy(i)) * usy;
+        const C feq = C(q_w(i)) * rho_s * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
+        fs[i] = f[i] + omega * (feq - f[i]);
+        moving += fs[i];
+    }
+    fs[0] = rho_s - moving;
+}
+
+// Momentum of one species' populations, as differences of opposite directions
+// (a state at rest gives exactly zero).
+template <class C> __device__ inline C mom_x(const C f[9]) { return (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]); }
+template <class C> __device__ inline C mom_y(const C f[9]) { return (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]); }
+
 // Result of colliding one site: post-collision populations and the total
 // force (for the force-corrected velocity of the observables).
 template <class C> struct Collided {
@@ -140,53 +191,21 @@ template <class C> struct Collided {
     C Fx, Fy;
 };
 
-// Shifted-velocity BGK collision of Eq. (be) for both species at one site.
-//   u      = j / (rho_A + rho_B)                                (barycentric)
-//   F_s    = -psi_s (G^a S1 + G^r S2) - (G_AB/rho0) rho_s X       (Eq. (FFF))
-//   u_s    = u + tau F_s/rho_s = u - tau[(psi_s/rho_s)(G^a S1 + G^r S2) + (G_AB/rho0) X]
-//   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau, i = 1..8
-//   f*_0s  = rho_s - sum_{i>=1} f*_is   (the same value in exact arithmetic)
-// psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
-// vanishing species density.
+// Both species at one site: u = j / (rho_A + rho_B), then collide_species each.
 template <class C>
 __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi[2],
-                                    const Sums<C> sm[2], const CellDev& p, Collided<C>& out)
+                                    const Sums<C> sm[2], const ParamSet<C>& p, Collided<C>& out)
 {
-    C jx = C(0), jy = C(0);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        jx += (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
-        jy += (f[s][2] - f[s][4]) + (f[s][5] - f[s][7]) + (f[s][6] - f[s][8]);
-    }
+    const C jx = mom_x<C>(f[0]) + mom_x<C>(f[1]);
+    const C jy = mom_y<C>(f[0]) + mom_y<C>(f[1]);
     const C inv_rho = C(1) / (rho[0] + rho[1]);
     const C ux = jx * inv_rho, uy = jy * inv_rho;
-    const C tau = C(p.tau), omega = C(p.omega), gx = C(p.gab_over_rho0);
-    C Fx = C(0), Fy = C(0);
+    C Fx[2], Fy[2];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const C ga = C(p.g1[s]), gr = C(p.g2[s]);
-        const C Gx = ga * sm[s].s1x + gr * sm[s].s2x;
-        const C Gy = ga * sm[s].s1y + gr * sm[s].s2y;
-        Fx += -psi[s] * Gx - gx * rho[s] * sm[s].xx;
-        Fy += -psi[s] * Gy - gx * rho[s] * sm[s].xy;
-        const C por = rho[s] != C(0) ? psi[s] / rho[s] : C(1);
-        const C usx = ux - tau * (por * Gx + gx * sm[s].xx);
-        const C usy = uy - tau * (por * Gy + gx * sm[s].xy);
-        const C usq = C(1.5) * (usx * usx + usy * usy);
-        C moving = C(0);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const C cu = C(q_cx(i)) * usx + C(q_cy(i)) * usy;
-            const C feq = C(q_w(i)) * rho[s] * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
-            out.fs[s][i] = f[s][i] + omega * (feq - f[s][i]);
-            moving += out.fs[s][i];
-        }
-        // BGK conserves rho_s; closing the rest population on it keeps the rounded
-        // weights (sum of float(w_i) = 1 + 7.5e-9) from biasing the mass each step.
-        out.fs[s][0] = rho[s] - moving;
-    }
-    out.Fx = Fx;
-    out.Fy = Fy;
+    for (int s = 0; s < 2; ++s)
+        collide_species<C>(f[s], rho[s], psi[s], ux, uy, sm[s], p.g1[s], p.g2[s], p, out.fs[s], &Fx[s], &Fy[s]);
+    out.Fx = Fx[0] + Fx[1];
+    out.Fy = Fy[0] + Fy[1];
 }
 
 // Halfway bounce-back with a moving wall: a population f*_i leaving through the

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) moments_psi_kernel(const T* __restrict__ 
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int cell = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const CellDev& p = cells[cell];
+    const ParamSet<C>& p = params<C>(cells[cell]);
     const long long n = (long long)g.nx * g.ny;
     C* a = aux + (long long)cell * 4 * n + (long long)y * g.nx + x;
 #pragma unroll
@@ -28,11 +28,11 @@ __global__ void __launch_bounds__(256) moments_psi_kernel(const T* __restrict__ 
         C r = C(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const C sh = Store<T>::shifted ? C(q_w(i) * p.rho_bar[s]) : C(0);
+            const C sh = Store<T>::shifted ? pop_shift<C>(i, p, s) : C(0);
             r += Store<T>::ld(f, fidx(g, cell, s * 9 + i, y, x), sh);
         }
         a[s * n] = r;
-        a[(2 + s) * n] = psi_of<C>(r, C(p.rho0), C(1.0 / p.rho0));
+        a[(2 + s) * n] = psi_of<C>(r, p.rho0, p.inv_rho0);
     }
 }
 
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int cell = blockIdx.z;
     const bool active = x < g.nx && y < g.ny;
-    const CellDev& p = cells[cell];
+    const ParamSet<C>& p = params<C>(cells[cell]);
     const long long n = (long long)g.nx * g.ny;
     const C* rho_f = aux + (long long)cell * 4 * n;
     double uphys = 0.0, dpx_site = 0.0;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const C sh = Store<T>::shifted ? C(q_w(i) * p.rho_bar[s]) : C(0);
+                const C sh = Store<T>::shifted ? pop_shift<C>(i, p, s) : C(0);
                 f[s][i] = Store<T>::ld(fin, fidx(g, cell, s * 9 + i, y, x), sh);
             }
         const long long k0 = (long long)y * g.nx + x;
@@ -83,17 +83,17 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
         Collided<C> c;
         collide_site<C>(f, rho, psi, sm, p, c);
 
-        const C u_top = C(p.u_wall), u_bot = C(-p.u_wall);
+        const C u_top = p.u_wall, u_bot = -p.u_wall;
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int yd = y + q_cy(i);
-                const C sh = Store<T>::shifted ? C(q_w(i) * p.rho_bar[s]) : C(0);
+                const C sh = Store<T>::shifted ? pop_shift<C>(i, p, s) : C(0);
                 if (bc == 1 && (yd < 0 || yd >= g.ny)) {
                     C dpx;
                     const C back = bounce<C>(i, c.fs[s][i], rho[s], yd < 0 ? u_bot : u_top, &dpx);
-                    const C sho = Store<T>::shifted ? C(q_w(q_opp(i)) * p.rho_bar[s]) : C(0);
+                    const C sho = Store<T>::shifted ? pop_shift<C>(q_opp(i), p, s) : C(0);
                     Store<T>::st(fout, fidx(g, cell, s * 9 + q_opp(i), y, x), back, sho);
                     dpx_site += (double)dpx;
                 } else {
@@ -105,9 +105,7 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
         if (SAMPLE) {
             const C rt = rho[0] + rho[1];
             // force-corrected velocity (j + F/2)/rho
-            C jx = C(0);
-#pragma unroll
-            for (int s = 0; s < 2; ++s) jx += (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
+            const C jx = mom_x<C>(f[0]) + mom_x<C>(f[1]);
             uphys = (double)((jx + C(0.5) * c.Fx) / rt);
             if (!(rt > C(0)) || !isfinite((double)rho[0]) || !isfinite((double)rho[1])) atomicOr(err, ERR_NONFINITE);
         }

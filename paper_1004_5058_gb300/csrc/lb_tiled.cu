@@ -62,31 +62,51 @@ struct TiledPlan {
     void* f[2];
 };
 
+// Row-slot ring depth: about three rows in flight beyond the three in use.
+__host__ __device__ constexpr int ring_depth(int tx, int elem)
+{
+    return (6 * al128(18 * tx * elem) + 12 * al128(18 * (16 / elem) * elem) <= 96 * 1024) ? 6 : 5;
+}
+// Words between the species-A and species-B psi/rho rings, chosen so that a
+// half-warp reading A and the other half reading B hit disjoint banks.
+__host__ __device__ constexpr int ring_species_stride(int tx)
+{
+    return RING * (tx + 4) + ((16 - (RING * (tx + 4)) % 32) + 32) % 32;
+}
+
 template <class T, int TX, bool SAMPLE>
-__global__ void __launch_bounds__(TX) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
-                                                        const __grid_constant__ CUtensorMap tm_halo,
-                                                        T* __restrict__ fout, Geom g, int bc, int ty, int depth,
-                                                        int n_strips, int n_seg,
-                                                        const CellDev* __restrict__ cells,
-                                                        double* __restrict__ prof_part,
-                                                        double* __restrict__ wall_part, unsigned* __restrict__ err)
+__global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
+                                                            const __grid_constant__ CUtensorMap tm_halo,
+                                                            T* __restrict__ fout, Geom g, int bc, int ty,
+                                                            int n_strips, int n_seg,
+                                                            const CellDev* __restrict__ cells,
+                                                            double* __restrict__ prof_part,
+                                                            double* __restrict__ wall_part,
+                                                            unsigned* __restrict__ err)
 {
     using C = typename Store<T>::C;
-    using C2 = typename V2<C>::t;
     constexpr int E = (int)sizeof(T);
-    constexpr int H = 16 / E;
-    constexpr int W = TX + 4;  // psi/rho ring row: columns -2 .. TX+1
-    const SlotGeom sg = slot_geom(TX, E);
+    constexpr int H = 16 / E;            // halo columns per side brought by TMA
+    constexpr int W = TX + 4;            // ring row: columns -2 .. TX+1
+    constexpr int D = ring_depth(TX, E);
+    constexpr int SS = ring_species_stride(TX);
+    constexpr int MAIN_AL = al128(18 * TX * E);
+    constexpr int HALO_AL = al128(18 * H * E);
+    constexpr int SLOT = MAIN_AL + 2 * HALO_AL;
+    constexpr uint32_t TX_BYTES = 18 * TX * E + 2 * 18 * H * E;
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* fring = smem;
-    C2* psi_ring = reinterpret_cast<C2*>(smem + (size_t)depth * sg.slot_b);
-    C2* rho_ring = psi_ring + RING * W;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(rho_ring + RING * W);
+    C* psi_ring = reinterpret_cast<C*>(smem + D * SLOT);  // [species][RING][W] (stride SS per species)
+    C* rho_ring = psi_ring + 2 * SS;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(rho_ring + 2 * SS);
 
     const int t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    const int sp = lane >> 4;                 // species of this thread
+    const int c = warp * 16 + (lane & 15);    // column of this thread in the strip
     if (t == 0) {
-        for (int d = 0; d < depth; ++d) mbar_init(&bars[d], 1);
+        for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
         fence_mbar_init();
         prefetch_tensormap(&tm_main);
         prefetch_tensormap(&tm_halo);
@@ -95,8 +115,8 @@ __global__ void __launch_bounds__(TX) tiled_step_kernel(const __grid_constant__ 
 
     const long long per_cell = (long long)n_strips * n_seg;
     const long long items = per_cell * g.n_cells;
-    uint32_t nrow = 0;     // rows this CTA has issued and consumed in earlier items
-    uint32_t issued = 0;   // thread 0: rows issued in the current item
+    uint32_t nrow = 0;    // rows consumed by this CTA in earlier items
+    uint32_t issued = 0;  // thread 0: rows issued in the current item
     bool aborted = false;
 
     for (long long w = blockIdx.x; w < items && !aborted; w += gridDim.x) {
@@ -106,66 +126,69 @@ __global__ void __launch_bounds__(TX) tiled_step_kernel(const __grid_constant__ 
         const int x0 = strip * TX, y0 = seg * ty;
         const int rows = min(ty, g.ny - y0);
         const int R = rows + 4;  // logical rows y0-2 .. y0+rows+1
-        const CellDev& p = cells[cell];
-        C shift[2][9];
+        // per-cell parameters as scalars (no runtime-indexed arrays: they would
+        // live in local memory)
+        const ParamSet<C>& pg = params<C>(cells[cell]);
+        ParamSet<C> p;
+        p.tau = pg.tau;
+        p.omega = pg.omega;
+        p.rho0 = pg.rho0;
+        p.inv_rho0 = pg.inv_rho0;
+        p.gab_over_rho0 = pg.gab_over_rho0;
+        p.u_wall = pg.u_wall;
+        const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
+        const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
+        C shift[9];
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) shift[s][i] = Store<T>::shifted ? C(q_w(i) * p.rho_bar[s]) : C(0);
+        for (int i = 0; i < 9; ++i) shift[i] = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
         const int xl = x0 >= H ? x0 - H : g.nx - H;
         const int xr = x0 + TX < g.nx ? x0 + TX : 0;
+        // destination columns x-1, x, x+1 (periodic)
+        const int x = x0 + c;
+        const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p = x == g.nx - 1 ? 0 : x + 1;
+        T* const dst_s = fout + (long long)cell * g.cellstride + (long long)sp * 9 * g.plane;
 
         __syncthreads();  // rings of the previous item are no longer read
 
         auto issue = [&](int k) {
             const uint32_t n = nrow + (uint32_t)k;
-            const int slot = (int)(n % (uint32_t)depth);
-            unsigned char* dst = fring + (size_t)slot * sg.slot_b;
+            const int slot = (int)(n % D);
+            unsigned char* dst = fring + slot * SLOT;
             const int yp = stencil_row(y0 - 2 + k, g.ny, bc);
-            mbar_arrive_expect_tx(&bars[slot], (uint32_t)sg.tx_bytes);
+            mbar_arrive_expect_tx(&bars[slot], TX_BYTES);
             tma_load_4d(dst, &tm_main, x0, yp, 0, cell, &bars[slot]);
-            tma_load_4d(dst + sg.main_al, &tm_halo, xl, yp, 0, cell, &bars[slot]);
-            tma_load_4d(dst + sg.main_al + sg.halo_al, &tm_halo, xr, yp, 0, cell, &bars[slot]);
+            tma_load_4d(dst + MAIN_AL, &tm_halo, xl, yp, 0, cell, &bars[slot]);
+            tma_load_4d(dst + MAIN_AL + HALO_AL, &tm_halo, xr, yp, 0, cell, &bars[slot]);
         };
         if (t == 0) {
             issued = 0;
-            for (int k = 0; k < depth && k < R; ++k) issue(k), ++issued;
+            for (int k = 0; k < D && k < R; ++k) issue(k), ++issued;
         }
         auto wait_row = [&](int k) -> bool {
             const uint32_t n = nrow + (uint32_t)k;
-            return mbar_wait_bounded(&bars[n % (uint32_t)depth], (n / (uint32_t)depth) & 1u);
+            return mbar_wait_bounded(&bars[n % D], (n / D) & 1u);
         };
-        // rho_s, psi_s of logical row k into ring row k % RING
+        // rho_s, psi_s of logical row k (own species, own column; lanes 0 and 16
+        // of warps 0..3 also take the four halo columns)
         auto psi_stage = [&](int k) {
-            const unsigned char* base = fring + (size_t)((nrow + (uint32_t)k) % (uint32_t)depth) * sg.slot_b;
-            const int ring = (k % RING) * W;
+            const unsigned char* base = fring + ((nrow + (uint32_t)k) % D) * SLOT;
+            const int ring = sp * SS + (k % RING) * W;
             auto site = [&](const T* src, int stride, int col, int pos) {
-                C r[2];
+                C acc = C(0);
 #pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    C acc = C(0);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const T v = src[(s * 9 + i) * stride + col];
-                        acc += Store<T>::shifted ? to_c(v) + shift[s][i] : to_c(v);
-                    }
-                    r[s] = acc;
+                for (int i = 0; i < 9; ++i) {
+                    const T v = src[(sp * 9 + i) * stride + col];
+                    acc += Store<T>::shifted ? to_c(v) + shift[i] : to_c(v);
                 }
-                const C rho0 = C(p.rho0), ir0 = C(1.0 / p.rho0);
-                C2 ps, rh;
-                ps.x = psi_of<C>(r[0], rho0, ir0);
-                ps.y = psi_of<C>(r[1], rho0, ir0);
-                rh.x = r[0];
-                rh.y = r[1];
-                psi_ring[ring + pos] = ps;
-                rho_ring[ring + pos] = rh;
+                psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
+                rho_ring[ring + pos] = acc;
             };
-            site(reinterpret_cast<const T*>(base), TX, t, t + 2);
-            if (t < 4) {
-                if (t < 2)
-                    site(reinterpret_cast<const T*>(base + sg.main_al), H, H - 2 + t, t);
+            site(reinterpret_cast<const T*>(base), TX, c, c + 2);
+            if ((lane & 15) == 0 && warp < 4) {
+                if (warp < 2)
+                    site(reinterpret_cast<const T*>(base + MAIN_AL), H, H - 2 + warp, warp);
                 else
-                    site(reinterpret_cast<const T*>(base + sg.main_al + sg.halo_al), H, t - 2, TX + t);
+                    site(reinterpret_cast<const T*>(base + MAIN_AL + HALO_AL), H, warp - 2, TX + warp);
             }
         };
 
@@ -185,83 +208,82 @@ __global__ void __launch_bounds__(TX) tiled_step_kernel(const __grid_constant__ 
             }
             if (t == 0) {
                 if (j == 0) {
-                    if (depth < R) issue(depth), ++issued;
-                    if (depth + 1 < R) issue(depth + 1), ++issued;
-                } else if (j + 1 + depth < R) {
-                    issue(j + 1 + depth);
+                    if (D < R) issue(D), ++issued;
+                    if (D + 1 < R) issue(D + 1), ++issued;
+                } else if (j + 1 + D < R) {
+                    issue(j + 1 + D);
                     ++issued;
                 }
             }
             // ---- collide logical row k = j + 2 (lattice row y)
-            const int k = j + 2, y = y0 + j, x = x0 + t;
-            const T* fm = reinterpret_cast<const T*>(fring + (size_t)((nrow + (uint32_t)k) % (uint32_t)depth) * sg.slot_b);
-            C f[2][9];
+            const int k = j + 2, y = y0 + j;
+            const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT);
+            C f[9];
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const T v = fm[(s * 9 + i) * TX + t];
-                    f[s][i] = Store<T>::shifted ? to_c(v) + shift[s][i] : to_c(v);
-                }
+            for (int i = 0; i < 9; ++i) {
+                const T v = fm[(sp * 9 + i) * TX + c];
+                f[i] = Store<T>::shifted ? to_c(v) + shift[i] : to_c(v);
+            }
+            const C* ps = psi_ring + sp * SS + c + 2;
+            const C* ro = rho_ring + (1 - sp) * SS + c + 2;
             int rb[5];
 #pragma unroll
-            for (int d = 0; d < 5; ++d) rb[d] = ((k - 2 + d) % RING) * W + t + 2;
-            const C2 ps0 = psi_ring[rb[2]], rh0 = rho_ring[rb[2]];
-            C dpa[12], dpb[12], dra[4], drb[4];
+            for (int d = 0; d < 5; ++d) rb[d] = ((k - 2 + d) % RING) * W;
+            const C psi_s = ps[rb[2]];
+            const C rho_s = rho_ring[sp * SS + c + 2 + rb[2]];
+            const C rho_o = ro[rb[2]];
+            C dps[12], dro[4];
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
                 const int dx = hs_dx(q), dy = hs_dy(q);
-                const C2 pp = psi_ring[rb[2 + dy] + dx], pm = psi_ring[rb[2 - dy] - dx];
-                dpa[q] = pp.x - pm.x;
-                dpb[q] = pp.y - pm.y;
-                if (q < 4) {
-                    const C2 rp = rho_ring[rb[2 + dy] + dx], rm = rho_ring[rb[2 - dy] - dx];
-                    dra[q] = rp.x - rm.x;
-                    drb[q] = rp.y - rm.y;
+                dps[q] = ps[rb[2 + dy] + dx] - ps[rb[2 - dy] - dx];
+                if (q < 4) dro[q] = ro[rb[2 + dy] + dx] - ro[rb[2 - dy] - dx];
+            }
+            const Sums<C> sm = stencil_sums<C>(dps, dro);
+            // barycentric velocity: own species' momentum + the partner lane's
+            const C jx_s = mom_x<C>(f), jy_s = mom_y<C>(f);
+            const C jx = jx_s + __shfl_xor_sync(0xffffffffu, jx_s, 16);
+            const C jy = jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16);
+            const C rho_t = rho_s + rho_o;
+            const C inv_rho = C(1) / rho_t;
+            C fs[9], Fx, Fy;
+            collide_species<C>(f, rho_s, psi_s, jx * inv_rho, jy * inv_rho, sm, ga, gr, p, fs, &Fx, &Fy);
+
+            // push streaming; rows next to a Couette wall bounce back in place
+            const bool wall_lo = bc == 1 && y == 0, wall_hi = bc == 1 && y == g.ny - 1;
+            const int row_m = (y == 0 ? g.ny - 1 : y - 1) * g.pitch;
+            const int row_0 = y * g.pitch;
+            const int row_p = (y == g.ny - 1 ? 0 : y + 1) * g.pitch;
+            const int pl = (int)g.plane;  // < 2^31 / 18, checked on the host
+            const int col3[3] = {col_m, x, col_p};
+            const int row3[3] = {row_m, row_0, row_p};
+            double dpx_site = 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int cy = q_cy(i);
+                const bool into_wall = (cy < 0 && wall_lo) || (cy > 0 && wall_hi);
+                if (into_wall) {
+                    C dpx;
+                    const C back = bounce<C>(i, fs[i], rho_s, cy < 0 ? -p.u_wall : p.u_wall, &dpx);
+                    Store<T>::st(dst_s, q_opp(i) * pl + row_0 + x, back, shift[q_opp(i)]);
+                    dpx_site += (double)dpx;
+                } else {
+                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + col3[q_cx(i) + 1], fs[i], shift[i]);
                 }
             }
-            Sums<C> sm[2];
-            sm[0] = stencil_sums<C>(dpa, drb);
-            sm[1] = stencil_sums<C>(dpb, dra);
-            const C rho[2] = {rh0.x, rh0.y}, psi[2] = {ps0.x, ps0.y};
-            Collided<C> c;
-            collide_site<C>(f, rho, psi, sm, p, c);
-
-            double dpx_site = 0.0;
-            const C u_top = C(p.u_wall), u_bot = C(-p.u_wall);
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int yd = y + q_cy(i);
-                    if (bc == 1 && (yd < 0 || yd >= g.ny)) {
-                        C dpx;
-                        const C back = bounce<C>(i, c.fs[s][i], rho[s], yd < 0 ? u_bot : u_top, &dpx);
-                        Store<T>::st(fout, fidx(g, cell, s * 9 + q_opp(i), y, x), back, shift[s][q_opp(i)]);
-                        dpx_site += (double)dpx;
-                    } else {
-                        const int xd = wrap_x(x + q_cx(i), g.nx);
-                        const int ydd = yd < 0 ? yd + g.ny : (yd >= g.ny ? yd - g.ny : yd);
-                        Store<T>::st(fout, fidx(g, cell, s * 9 + i, ydd, xd), c.fs[s][i], shift[s][i]);
-                    }
-                }
             if (SAMPLE) {
-                const C rt = rho[0] + rho[1];
-                C jx = C(0);
-#pragma unroll
-                for (int s = 0; s < 2; ++s) jx += (f[s][1] - f[s][3]) + (f[s][5] - f[s][7]) + (f[s][8] - f[s][6]);
-                double uphys = (double)((jx + C(0.5) * c.Fx) / rt);
-                if (!(rt > C(0)) || !isfinite((double)rho[0]) || !isfinite((double)rho[1])) atomicOr(err, ERR_NONFINITE);
+                const C Fx_t = Fx + __shfl_xor_sync(0xffffffffu, Fx, 16);
+                double uphys = sp == 0 ? (double)((jx + C(0.5) * Fx_t) / rho_t) : 0.0;
+                if (!(rho_t > C(0)) || !isfinite((double)rho_s)) atomicOr(err, ERR_NONFINITE);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     uphys += __shfl_down_sync(0xffffffffu, uphys, o);
                     dpx_site += __shfl_down_sync(0xffffffffu, dpx_site, o);
                 }
-                if ((t & 31) == 0) {
-                    const int nbx = g.nx / 32, wg = x / 32;
+                if (lane == 0) {
+                    const int nbx = g.nx / 16, wg = (x0 >> 4) + warp;
                     prof_part[((long long)cell * nbx + wg) * g.ny + y] = uphys;
-                    if (bc == 1 && (y == 0 || y == g.ny - 1))
-                        wall_part[((long long)cell * nbx + wg) * 2 + (y == 0 ? 1 : 0)] = dpx_site;
+                    if (wall_lo || wall_hi) wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = dpx_site;
                 }
             }
         }
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(TX) tiled_step_kernel(const __grid_constant__ 
                 // drain the copies still in flight before shared memory is released
                 for (uint32_t k = 0; k < issued; ++k) {
                     const uint32_t n = nrow + k;
-                    mbar_wait_bounded(&bars[n % (uint32_t)depth], (n / (uint32_t)depth) & 1u, 1u << 20);
+                    mbar_wait_bounded(&bars[n % D], (n / D) & 1u, 1u << 20);
                 }
             }
             __syncthreads();
@@ -296,20 +318,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-static int depth_for(int tx, int elem)
-{
-    const SlotGeom sg = slot_geom(tx, elem);
-    // about 3 rows in flight, at most 96 KB of row slots
-    int d = 6;
-    while (d > 5 && (size_t)d * sg.slot_b > 96 * 1024) --d;
-    return d;
-}
+static int depth_for(int tx, int elem) { return ring_depth(tx, elem); }
 
 static size_t smem_bytes(int tx, int elem, int depth)
 {
     const SlotGeom sg = slot_geom(tx, elem);
-    const int c2 = elem == 8 ? 16 : 8;
-    return (size_t)depth * sg.slot_b + (size_t)2 * RING * (tx + 4) * c2 + (size_t)depth * 8;
+    const int cb = elem == 8 ? 8 : 4;
+    return (size_t)depth * sg.slot_b + (size_t)4 * ring_species_stride(tx) * cb + (size_t)depth * 8;
 }
 
 bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
@@ -317,11 +332,12 @@ bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
     if (tile_x != 32 && tile_x != 64 && tile_x != 128 && tile_x != 256) return false;
     if (tile_y < 1 || g.nx % tile_x != 0 || g.ny < 5) return false;
     if (g.nx < tile_x || (g.nx * elem) % 16 != 0) return false;
+    if (18 * g.plane >= (1LL << 31)) return false;  // 32-bit element offsets inside a cell
     if (smem_bytes(tile_x, elem, depth_for(tile_x, elem)) > 227 * 1024) return false;
     return encode_fn() != nullptr;
 }
 
-int tiled_partials_nbx(const Geom& g, int) { return (g.nx + 31) / 32; }
+int tiled_partials_nbx(const Geom& g, int) { return (g.nx + 15) / 16; }
 
 template <class T, int TX, bool S>
 static const void* kernel_ptr()
@@ -404,7 +420,7 @@ TiledPlan* tiled_create(const Geom& g, int elem, int bc, void* f0, void* f1, int
             return nullptr;
         }
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, tile_x, p->smem) != cudaSuccess || o < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 2 * tile_x, p->smem) != cudaSuccess || o < 1) {
             cudaGetLastError();
             if (err_msg) *err_msg = "tiled kernel does not fit on an SM";
             delete p;
@@ -433,11 +449,11 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
     T* dst = reinterpret_cast<T*>(p->f[1 - src]);
     const void* k = pick<T>(p->tx, sample);
     Geom g = p->g;
-    int bc = p->bc, ty = p->ty, depth = p->depth, ns = p->n_strips, nseg = p->n_seg;
+    int bc = p->bc, ty = p->ty, ns = p->n_strips, nseg = p->n_seg;
     void* args[] = {(void*)&p->tm_main[src], (void*)&p->tm_halo[src], (void*)&dst, (void*)&g, (void*)&bc,
-                    (void*)&ty, (void*)&depth, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
+                    (void*)&ty, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
                     (void*)&wall_part, (void*)&err};
-    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid), dim3(p->tx), args, p->smem, st);
+    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid), dim3(2 * p->tx), args, p->smem, st);
     *n_launches += 1;
     return e;
 }
