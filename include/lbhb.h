@@ -141,8 +141,11 @@ lb_status lb_get_fields(lb_handle* h, double* rho_a, double* rho_b, double* ux, 
  * j_x, j_y.  Either may be NULL.  Synchronous; reports LB_ERR_NONFINITE. */
 lb_status lb_reductions(lb_handle* h, double* mass_ab, double* momentum_xy);
 
-/* Chooses the kernel family and tile (tile_x, tile_y; 0 = default) for
- * subsequent steps.  LB_ERR_UNSUPPORTED if the shape does not allow it. */
+/* Chooses the kernel family and tile for subsequent steps.  Tiled family:
+ * tile_x = columns per work item (32, 64, 128 or 256, dividing nx; 0 = the
+ * widest that divides nx), tile_y = rows per work item (0 = chosen from a
+ * model of how evenly the work items fill the GPU).  The generic family
+ * ignores both.  LB_ERR_UNSUPPORTED if the shape does not allow the request. */
 lb_status lb_set_kernel(lb_handle* h, lb_kernel kernel, int tile_x, int tile_y);
 
 /* Times the supported tiles on this handle's buffers (the state is left

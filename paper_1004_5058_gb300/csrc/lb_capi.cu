@@ -187,7 +187,7 @@ static lb_status reset_counters(lb_handle* h)
 static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
 {
     if (k == LB_KERNEL_AUTO) {
-        const int cand[][2] = {{128, 64}, {64, 64}, {64, 32}, {32, 32}};
+        const int cand[][2] = {{128, 0}, {64, 0}, {32, 0}};
         for (auto& c : cand)
             if (tiled_supported(h->g, h->elem, c[0], c[1])) {
                 if (select_kernel(h, LB_KERNEL_TILED, c[0], c[1]) == LB_OK) return LB_OK;
@@ -214,7 +214,6 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
                 break;
             }
     }
-    if (ty == 0) ty = 64;
     if (!tiled_supported(h->g, h->elem, tx, ty))
         return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: tiled kernel does not support nx=%d ny=%d tile %dx%d",
                     h->nx, h->ny, tx, ty);
@@ -226,8 +225,7 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
     if (h->plan) tiled_destroy(h->plan);
     h->plan = p;
     h->kernel = LB_KERNEL_TILED;
-    h->tile_x = tx;
-    h->tile_y = ty;
+    tiled_tiles(p, &h->tile_x, &h->tile_y);
     return LB_OK;
 }
 
@@ -712,7 +710,7 @@ lb_status lb_autotune(lb_handle* h, const char* cache_path)
     std::vector<std::tuple<int, int, int>> cand;
     cand.emplace_back((int)LB_KERNEL_GENERIC, 0, 0);
     const int txs[] = {32, 64, 128, 256};
-    const int tys[] = {16, 32, 64, 128, 256};
+    const int tys[] = {0, 16, 32, 64};  // 0: segment height from the fill model
     for (int tx : txs)
         for (int ty : tys)
             if (tiled_supported(h->g, h->elem, tx, ty)) cand.emplace_back((int)LB_KERNEL_TILED, tx, ty);

@@ -115,9 +115,37 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
 
     const long long per_cell = (long long)n_strips * n_seg;
     const long long items = per_cell * g.n_cells;
-    uint32_t nrow = 0;    // rows consumed by this CTA in earlier items
-    uint32_t issued = 0;  // thread 0: rows issued in the current item
+    uint32_t nrow = 0;  // global index of row 0 of the current item (rows consumed before it)
     bool aborted = false;
+
+    // Issue cursor (thread 0): the next row to load may belong to a later item
+    // of this CTA, so the row pipeline does not drain between items.  Global
+    // row n always lives in slot n % D with mbarrier phase (n / D) & 1.
+    long long iw = blockIdx.x;
+    int ik = 0;
+    uint32_t n_issued = 0;
+    auto issue_upto = [&](uint32_t limit) {
+        while (n_issued < limit && iw < items) {
+            const int icell = (int)(iw / per_cell);
+            const int irem = (int)(iw % per_cell);
+            const int ix0 = (irem % n_strips) * TX, iy0 = (irem / n_strips) * ty;
+            const int irows = min(ty, g.ny - iy0);
+            const int slot = (int)(n_issued % D);
+            unsigned char* dst = fring + slot * SLOT;
+            const int yp = stencil_row(iy0 - 2 + ik, g.ny, bc);
+            const int ixl = ix0 >= H ? ix0 - H : g.nx - H;
+            const int ixr = ix0 + TX < g.nx ? ix0 + TX : 0;
+            mbar_arrive_expect_tx(&bars[slot], TX_BYTES);
+            tma_load_4d(dst, &tm_main, ix0, yp, 0, icell, &bars[slot]);
+            tma_load_4d(dst + MAIN_AL, &tm_halo, ixl, yp, 0, icell, &bars[slot]);
+            tma_load_4d(dst + MAIN_AL + HALO_AL, &tm_halo, ixr, yp, 0, icell, &bars[slot]);
+            ++n_issued;
+            if (++ik == irows + 4) {
+                ik = 0;
+                iw += gridDim.x;
+            }
+        }
+    };
 
     for (long long w = blockIdx.x; w < items && !aborted; w += gridDim.x) {
         const int cell = (int)(w / per_cell);
@@ -141,8 +169,6 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
         C shift[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) shift[i] = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
-        const int xl = x0 >= H ? x0 - H : g.nx - H;
-        const int xr = x0 + TX < g.nx ? x0 + TX : 0;
         // destination columns x-1, x, x+1 (periodic)
         const int x = x0 + c;
         const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p = x == g.nx - 1 ? 0 : x + 1;
@@ -150,20 +176,7 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
 
         __syncthreads();  // rings of the previous item are no longer read
 
-        auto issue = [&](int k) {
-            const uint32_t n = nrow + (uint32_t)k;
-            const int slot = (int)(n % D);
-            unsigned char* dst = fring + slot * SLOT;
-            const int yp = stencil_row(y0 - 2 + k, g.ny, bc);
-            mbar_arrive_expect_tx(&bars[slot], TX_BYTES);
-            tma_load_4d(dst, &tm_main, x0, yp, 0, cell, &bars[slot]);
-            tma_load_4d(dst + MAIN_AL, &tm_halo, xl, yp, 0, cell, &bars[slot]);
-            tma_load_4d(dst + MAIN_AL + HALO_AL, &tm_halo, xr, yp, 0, cell, &bars[slot]);
-        };
-        if (t == 0) {
-            issued = 0;
-            for (int k = 0; k < D && k < R; ++k) issue(k), ++issued;
-        }
+        if (t == 0) issue_upto(nrow + D);  // rows of earlier items are all done
         auto wait_row = [&](int k) -> bool {
             const uint32_t n = nrow + (uint32_t)k;
             return mbar_wait_bounded(&bars[n % D], (n / D) & 1u);
@@ -184,11 +197,16 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
                 rho_ring[ring + pos] = acc;
             };
             site(reinterpret_cast<const T*>(base), TX, c, c + 2);
-            if ((lane & 15) == 0 && warp < 4) {
-                if (warp < 2)
-                    site(reinterpret_cast<const T*>(base + MAIN_AL), H, H - 2 + warp, warp);
-                else
-                    site(reinterpret_cast<const T*>(base + MAIN_AL + HALO_AL), H, warp - 2, TX + warp);
+            // halo column h (0,1: columns -2,-1; 2,3: columns TX, TX+1) of this
+            // thread's species goes to warp h % NW, lane h / NW of the half-warp
+            constexpr int NW = 2 * TX / 32;
+            const int hl = lane & 15;
+            if (hl < (4 + NW - 1) / NW) {
+                const int h = hl * NW + warp;
+                if (h < 2)
+                    site(reinterpret_cast<const T*>(base + MAIN_AL), H, H - 2 + h, h);
+                else if (h < 4)
+                    site(reinterpret_cast<const T*>(base + MAIN_AL + HALO_AL), H, h - 2, TX + h);
             }
         };
 
@@ -206,15 +224,8 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
                 aborted = true;
                 break;
             }
-            if (t == 0) {
-                if (j == 0) {
-                    if (D < R) issue(D), ++issued;
-                    if (D + 1 < R) issue(D + 1), ++issued;
-                } else if (j + 1 + D < R) {
-                    issue(j + 1 + D);
-                    ++issued;
-                }
-            }
+            // rows 0 .. j+1 of this item are done with their slots
+            if (t == 0) issue_upto(nrow + (uint32_t)(j + 2 + D));
             // ---- collide logical row k = j + 2 (lattice row y)
             const int k = j + 2, y = y0 + j;
             const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT);
@@ -291,10 +302,7 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
             if (t == 0) {
                 atomicOr(err, ERR_TIMEOUT);
                 // drain the copies still in flight before shared memory is released
-                for (uint32_t k = 0; k < issued; ++k) {
-                    const uint32_t n = nrow + k;
-                    mbar_wait_bounded(&bars[n % D], (n / D) & 1u, 1u << 20);
-                }
+                for (uint32_t n = nrow; n < n_issued; ++n) mbar_wait_bounded(&bars[n % D], (n / D) & 1u, 1u << 20);
             }
             __syncthreads();
             break;
@@ -327,10 +335,32 @@ static size_t smem_bytes(int tx, int elem, int depth)
     return (size_t)depth * sg.slot_b + (size_t)4 * ring_species_stride(tx) * cb + (size_t)depth * 8;
 }
 
+// Segment height from a fill model: work items = strips x segments x cells run
+// on `slots` persistent CTAs, each item costing about (rows + 6) row-times
+// (4 halo rows plus pipeline effects); pick the height with the least
+// rounds x cost, so the last round of items is not mostly empty.
+static int pick_segment_rows(const Geom& g, int tile_x, long long slots)
+{
+    const long long strips = g.nx / tile_x;
+    int best = 32;
+    double best_cost = 1e300;
+    for (int ty = 8; ty <= 256 && ty <= g.ny; ++ty) {
+        const long long items = strips * g.n_cells * ((g.ny + ty - 1) / ty);
+        const long long rounds = (items + slots - 1) / slots;
+        const int rows = std::min(ty, g.ny);
+        const double cost = (double)rounds * (rows + 6);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = ty;
+        }
+    }
+    return best;
+}
+
 bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
 {
     if (tile_x != 32 && tile_x != 64 && tile_x != 128 && tile_x != 256) return false;
-    if (tile_y < 1 || g.nx % tile_x != 0 || g.ny < 5) return false;
+    if (tile_y < 0 || g.nx % tile_x != 0 || g.ny < 5) return false;  // tile_y 0: chosen by the fill model
     if (g.nx < tile_x || (g.nx * elem) % 16 != 0) return false;
     if (18 * g.plane >= (1LL << 31)) return false;  // 32-bit element offsets inside a cell
     if (smem_bytes(tile_x, elem, depth_for(tile_x, elem)) > 227 * 1024) return false;
@@ -396,7 +426,6 @@ TiledPlan* tiled_create(const Geom& g, int elem, int bc, void* f0, void* f1, int
     p->ty = tile_y;
     p->depth = depth_for(tile_x, elem);
     p->n_strips = g.nx / tile_x;
-    p->n_seg = (g.ny + tile_y - 1) / tile_y;
     p->smem = smem_bytes(tile_x, elem, p->depth);
     p->f[0] = f0;
     p->f[1] = f1;
@@ -428,8 +457,10 @@ TiledPlan* tiled_create(const Geom& g, int elem, int bc, void* f0, void* f1, int
         }
         occ = s == 0 ? o : std::min(occ, o);
     }
-    const long long items = (long long)p->n_strips * p->n_seg * g.n_cells;
     const long long slots = (long long)sms * occ;
+    if (p->ty <= 0) p->ty = pick_segment_rows(g, tile_x, slots);
+    p->n_seg = (g.ny + p->ty - 1) / p->ty;
+    const long long items = (long long)p->n_strips * p->n_seg * g.n_cells;
     p->grid = (int)std::min(items, slots);
     return p;
 }
