@@ -121,27 +121,24 @@ template <class C> struct Sums {
 };
 
 template <class C>
-__device__ inline Sums<C> stencil_sums(const C dpsi[12], const C drho_other[4])
+__device__ inline Sums<C> stencil_sums(const C d[12], const C e[4])
 {
+    // Terms grouped by weight (the half stencil is symmetric under x -> -x):
+    //   belt 1: (1,0),(0,1) weight 1/9; (1,1),(-1,1) weight 1/36
+    //   belts 1+2: |c|^2 = 1: 4/63, 2: 4/135, 4: 1/180, 5: 2/945, 8: 1/15120
+    const C p1 = C(hs_w2(0)), p2 = C(hs_w2(2)), p4 = C(hs_w2(4)), p5 = C(hs_w2(6)), p8 = C(hs_w2(10));
+    const C w1 = C(hs_w1(0)), w2 = C(hs_w1(2));
+    const C dm23 = d[2] - d[3], dp23 = d[2] + d[3];                           // (1,1), (-1,1)
+    const C dm67 = d[6] - d[7], dp67 = d[6] + d[7];                           // (2,1), (-2,1)
+    const C dm89 = d[8] - d[9], dp89 = d[8] + d[9];                           // (1,2), (-1,2)
+    const C dm1011 = d[10] - d[11], dp1011 = d[10] + d[11];                   // (2,2), (-2,2)
     Sums<C> r;
-    r.s1x = r.s1y = r.s2x = r.s2y = r.xx = r.xy = C(0);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const C w2 = C(hs_w2(k));
-        if (hs_dx(k) != 0) r.s2x += (w2 * C(hs_dx(k))) * dpsi[k];
-        if (hs_dy(k) != 0) r.s2y += (w2 * C(hs_dy(k))) * dpsi[k];
-        if (k < 4) {
-            const C w1 = C(hs_w1(k));
-            if (hs_dx(k) != 0) {
-                r.s1x += (w1 * C(hs_dx(k))) * dpsi[k];
-                r.xx += (w1 * C(hs_dx(k))) * drho_other[k];
-            }
-            if (hs_dy(k) != 0) {
-                r.s1y += (w1 * C(hs_dy(k))) * dpsi[k];
-                r.xy += (w1 * C(hs_dy(k))) * drho_other[k];
-            }
-        }
-    }
+    r.s1x = w1 * d[0] + w2 * dm23;
+    r.s1y = w1 * d[1] + w2 * dp23;
+    r.s2x = p1 * d[0] + p2 * dm23 + (C(2) * p4) * d[4] + p5 * (C(2) * dm67 + dm89) + (C(2) * p8) * dm1011;
+    r.s2y = p1 * d[1] + p2 * dp23 + (C(2) * p4) * d[5] + p5 * (dp67 + C(2) * dp89) + (C(2) * p8) * dp1011;
+    r.xx = w1 * e[0] + w2 * (e[2] - e[3]);
+    r.xy = w1 * e[1] + w2 * (e[2] + e[3]);
     return r;
 }
 
@@ -150,6 +147,8 @@ __device__ inline Sums<C> stencil_sums(const C dpsi[12], const C drho_other[4])
 //   u_s    = u + tau F_s/rho_s = u - tau[(psi_s/rho_s)(G^a S1 + G^r S2) + (G_AB/rho0) X]
 //   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau, i = 1..8
 //   f*_0s  = rho_s - sum_{i>=1} f*_is   (the same value in exact arithmetic)
+// f^eq_i = w_i rho_s (1 + 3 c_i.u_s + 4.5 (c_i.u_s)^2 - 1.5 u_s^2) is evaluated for
+// the pairs +-c_i together (even part + odd part).
 // u is the barycentric velocity j / (rho_A + rho_B) of both species.
 // psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
 // vanishing species density.  Closing the rest population on rho_s keeps the
@@ -167,14 +166,21 @@ __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C u
     const C por = rho_s != C(0) ? psi_s / rho_s : C(1);
     const C usx = ux - tau * (por * Gx + gx * sm.xx);
     const C usy = uy - tau * (por * Gy + gx * sm.xy);
-    const C usq = C(1.5) * (usx * usx + usy * usy);
+    // f^eq of a pair +-c: w rho (1 - 1.5 u^2 + 4.5 (c.u)^2) +- 3 w rho (c.u)
+    const C base = C(1) - C(1.5) * (usx * usx + usy * usy);
+    const C wr1 = C(q_w(1)) * rho_s, wr5 = C(q_w(5)) * rho_s;
+    const C cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
+    const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
     C moving = C(0);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const C cu = C(q_cx(i)) * usx + C(q_cy(i)) * usy;
-        const C feq = C(q_w(i)) * rho_s * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
-        fs[i] = f[i] + omega * (feq - f[i]);
-        moving += fs[i];
+    for (int k = 0; k < 4; ++k) {
+        const C wr = k < 2 ? wr1 : wr5;
+        const C a = wr * (base + C(4.5) * cu[k] * cu[k]);
+        const C b = (C(3) * wr) * cu[k];
+        const int i = lo[k], j = hi[k];
+        fs[i] = f[i] + omega * ((a + b) - f[i]);
+        fs[j] = f[j] + omega * ((a - b) - f[j]);
+        moving += fs[i] + fs[j];
     }
     fs[0] = rho_s - moving;
 }
@@ -227,6 +233,32 @@ __host__ __device__ inline int stencil_row(int y, int ny, int bc)
     return y < 0 ? -y - 1 : (y >= ny ? 2 * ny - y - 1 : y);
 }
 __host__ __device__ inline int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
+// Sum over the 32 lanes of a warp (result valid in lane 0).  FP32 values are
+// added as an unevaluated (hi, lo) pair with the error-free two-sum, so the
+// result carries ~2^-48 relative error without using the FP64 pipe; FP64
+// values are added in FP64.
+__device__ inline double warp_sum_compensated(float v)
+{
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const float sum = __fadd_rn(hi, h2);
+        const float bp = __fsub_rn(sum, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bp)), __fsub_rn(h2, bp));
+        hi = sum;
+        lo = __fadd_rn(__fadd_rn(lo, l2), err);
+    }
+    return (double)hi + (double)lo;
+}
+__device__ inline double warp_sum_compensated(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Device error word bits.
 enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };

@@ -120,29 +120,37 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
 
     // Issue cursor (thread 0): the next row to load may belong to a later item
     // of this CTA, so the row pipeline does not drain between items.  Global
-    // row n always lives in slot n % D with mbarrier phase (n / D) & 1.
+    // row n always lives in slot n % D with mbarrier phase (n / D) & 1.  The
+    // geometry of the item being issued is cached (one division per item).
     long long iw = blockIdx.x;
-    int ik = 0;
+    int ik = 0, icell = 0, ix0 = 0, iy0 = 0, iR = 0, ixl = 0, ixr = 0;
     uint32_t n_issued = 0;
+    auto load_item = [&]() {
+        if (iw >= items) return;
+        icell = (int)(iw / per_cell);
+        const int irem = (int)(iw - (long long)icell * per_cell);
+        const int iseg = irem / n_strips;
+        ix0 = (irem - iseg * n_strips) * TX;
+        iy0 = iseg * ty;
+        iR = min(ty, g.ny - iy0) + 4;
+        ixl = ix0 >= H ? ix0 - H : g.nx - H;
+        ixr = ix0 + TX < g.nx ? ix0 + TX : 0;
+    };
+    if (t == 0) load_item();
     auto issue_upto = [&](uint32_t limit) {
         while (n_issued < limit && iw < items) {
-            const int icell = (int)(iw / per_cell);
-            const int irem = (int)(iw % per_cell);
-            const int ix0 = (irem % n_strips) * TX, iy0 = (irem / n_strips) * ty;
-            const int irows = min(ty, g.ny - iy0);
             const int slot = (int)(n_issued % D);
             unsigned char* dst = fring + slot * SLOT;
             const int yp = stencil_row(iy0 - 2 + ik, g.ny, bc);
-            const int ixl = ix0 >= H ? ix0 - H : g.nx - H;
-            const int ixr = ix0 + TX < g.nx ? ix0 + TX : 0;
             mbar_arrive_expect_tx(&bars[slot], TX_BYTES);
             tma_load_4d(dst, &tm_main, ix0, yp, 0, icell, &bars[slot]);
             tma_load_4d(dst + MAIN_AL, &tm_halo, ixl, yp, 0, icell, &bars[slot]);
             tma_load_4d(dst + MAIN_AL + HALO_AL, &tm_halo, ixr, yp, 0, icell, &bars[slot]);
             ++n_issued;
-            if (++ik == irows + 4) {
+            if (++ik == iR) {
                 ik = 0;
                 iw += gridDim.x;
+                load_item();
             }
         }
     };
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
             const int pl = (int)g.plane;  // < 2^31 / 18, checked on the host
             const int col3[3] = {col_m, x, col_p};
             const int row3[3] = {row_m, row_0, row_p};
-            double dpx_site = 0.0;
+            C dpx_site = C(0);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int cy = q_cy(i);
@@ -277,24 +285,24 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
                     C dpx;
                     const C back = bounce<C>(i, fs[i], rho_s, cy < 0 ? -p.u_wall : p.u_wall, &dpx);
                     Store<T>::st(dst_s, q_opp(i) * pl + row_0 + x, back, shift[q_opp(i)]);
-                    dpx_site += (double)dpx;
+                    dpx_site += dpx;
                 } else {
                     Store<T>::st(dst_s, i * pl + row3[cy + 1] + col3[q_cx(i) + 1], fs[i], shift[i]);
                 }
             }
             if (SAMPLE) {
                 const C Fx_t = Fx + __shfl_xor_sync(0xffffffffu, Fx, 16);
-                double uphys = sp == 0 ? (double)((jx + C(0.5) * Fx_t) / rho_t) : 0.0;
-                if (!(rho_t > C(0)) || !isfinite((double)rho_s)) atomicOr(err, ERR_NONFINITE);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    uphys += __shfl_down_sync(0xffffffffu, uphys, o);
-                    dpx_site += __shfl_down_sync(0xffffffffu, dpx_site, o);
-                }
+                const C up = sp == 0 ? (jx + C(0.5) * Fx_t) / rho_t : C(0);
+                if (!(rho_t > C(0)) || !isfinite(rho_s)) atomicOr(err, ERR_NONFINITE);
+                // lane sums carried as an unevaluated pair (error-free two-sum),
+                // then added in FP64: ~2^-48 relative, no FP64 pipe in the tree
+                const double usum = warp_sum_compensated(up);
+                double wsum = 0.0;
+                if (wall_lo || wall_hi) wsum = warp_sum_compensated((C)dpx_site);
                 if (lane == 0) {
                     const int nbx = g.nx / 16, wg = (x0 >> 4) + warp;
-                    prof_part[((long long)cell * nbx + wg) * g.ny + y] = uphys;
-                    if (wall_lo || wall_hi) wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = dpx_site;
+                    prof_part[((long long)cell * nbx + wg) * g.ny + y] = usum;
+                    if (wall_lo || wall_hi) wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = wsum;
                 }
             }
         }
