@@ -105,9 +105,11 @@ def test_c1_periodic_1000_steps_paper_couplings(kernel, prec, tol):
     assert max_abs(ga[0], oa) <= tol and max_abs(gb[0], ob) <= tol
     assert max_abs(gu[0], ou) <= tol and max_abs(gv[0], ov) <= tol
     m0 = (ra.sum(), rb.sum())
-    # mass: FP64 to round-off; FP32 drifts by unbiased roundings of rho - sum f*
-    # (~1e-8 relative per site and step, averaging over sites), so 2e-6 bounds 1000 steps
-    mtol = 1e-13 if prec == "fp64" else 2e-6
+    # mass: FP64 to round-off.  FP32: each site and step rounds rho = sum f (8
+    # additions) and the rest population rho - sum f* (9 more), at most ~3.5e-7
+    # of rho together, so 1000 steps are bounded by 3.5e-4; the observed drift is
+    # a small systematic bias (~4e-6 per 1000 steps), and 1e-5 is asserted
+    mtol = 1e-13 if prec == "fp64" else 1e-5
     assert abs(mass[0, 0] - m0[0]) / m0[0] <= mtol and abs(mass[0, 1] - m0[1]) / m0[1] <= mtol
     assert abs(mom[0]).max() / (m0[0] + m0[1]) <= (1e-13 if prec == "fp64" else 1e-6)
 
@@ -128,7 +130,7 @@ def test_c1_periodic_demixing(kernel, prec, tol, steps):
     (r,) = oracle_runs([cell], ra, rb, steps=steps)
     oa, ob, _, _ = r.fields()
     assert max_abs(ga[0], oa) <= tol and max_abs(gb[0], ob) <= tol
-    mtol = 1e-13 if prec == "fp64" else 2e-6
+    mtol = 1e-13 if prec == "fp64" else 1e-5
     assert abs(mass[0, 0] - ra.sum()) / ra.sum() <= mtol
 
 
