@@ -171,6 +171,36 @@ void* lb_stream(const lb_handle* h);
  * (kernels launched as nodes of a CUDA graph count one each). */
 long long lb_kernel_launches(const lb_handle* h);
 
+/* FP64 state sums without any allocation, for callers that cannot allocate
+ * device memory (their memory belongs to another allocator or a fixed budget,
+ * or they cannot accept the device-wide synchronisation cudaMalloc/cudaFree
+ * may cause).  The paper has no counterpart: it is an interface variant of
+ * lb_reductions that needs no handle.
+ *   populations  caller's device buffer, layout [n_cells][18][ny][pitch]
+ *                (species A then B, D2Q9 order as in lb_set_populations), in
+ *                LB_FP32 or LB_FP64 storage; LB_FP16_SHIFTED is rejected
+ *                (LB_ERR_UNSUPPORTED)
+ *   sums         caller's device buffer [n_cells][4] float64, receives
+ *                (sum rho_A, sum rho_B, sum j_x, sum j_y) per cell; a
+ *                non-finite density makes its cell's sums non-finite
+ *   cuda_stream  stream of the current device (NULL: the legacy default stream)
+ * Work is enqueued and the call returns; read sums after the stream is done.
+ * The partial sums live in one scratch array compiled into the library
+ * (65536 doubles + an error word, 512 KiB on every GPU that loads the library,
+ * held until exit): inputs needing more partial sums than that (4 per block of
+ * up to 8192 sites, per cell) are rejected with LB_ERR_INVALID and a message,
+ * e.g. more than 16 cells of 4096x4096.  The array is shared by all calls on a
+ * device and keeps the last call's contents; calls that overlap on the GPU
+ * (different streams or host threads) race on it and must be serialised by the
+ * caller.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine).  Errors: LB_ERR_INVALID (null or misaligned
+ * pointer, bad size), LB_ERR_UNSUPPORTED, LB_ERR_CUDA; message in
+ * lb_last_error(NULL). */
+lb_status lb_reductions_noalloc(const void* populations, lb_precision prec, int nx, int ny, int pitch,
+                                int n_cells, double* sums, void* cuda_stream);
+
 /* Message for the last failing call on h; a static string when h is NULL. */
 const char* lb_last_error(const lb_handle* h);
 

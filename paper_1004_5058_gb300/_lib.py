@@ -52,6 +52,8 @@ SIGNATURES = {
     "lb_last_error": (C.c_char_p, [_H]),
     "lb_destroy": (None, [_H]),
     "lb_hb_fit": (C.c_int, [_D, _D, C.c_int, C.c_double, C.c_double, _D]),
+    "lb_reductions_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                        C.c_void_p]),
 }
 
 _lib = None

@@ -60,6 +60,8 @@ struct lb_handle {
 static const char* g_null_msg = "lb: handle is NULL";
 static thread_local char g_create_msg[512] = "";
 
+void lbhb::set_handleless_error(const char* msg) { snprintf(g_create_msg, sizeof g_create_msg, "%s", msg); }
+
 static lb_status fail(lb_handle* h, lb_status st, const char* fmt, ...)
 {
     char buf[512];

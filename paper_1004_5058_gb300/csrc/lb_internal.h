@@ -43,4 +43,7 @@ cudaError_t launch_state_sums(const T* f, const Geom& g, const CellDev* cells, d
 cudaError_t launch_accumulate(const double* prof_part, const double* wall_part, int nbx, int ny, int bc,
                               int n_cells, double* acc_prof, double* acc_wall, cudaStream_t st);
 
+// Message returned by lb_last_error(NULL) (lb_capi.cu).
+void set_handleless_error(const char* msg);
+
 }  // namespace lbhb
