@@ -31,6 +31,14 @@ class lb_cell_params(C.Structure):
                 ("rho_bar_a", C.c_double), ("rho_bar_b", C.c_double), ("bc", C.c_int)]
 
 
+class mlp_config(C.Structure):
+    _fields_ = [("max_batch", C.c_int), ("lam", C.c_double), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("center", C.c_double * 5),
+                ("half_range", C.c_double * 5), ("sigma_scale", C.c_double), ("logit_margin", C.c_double)]
+
+
+_F = C.POINTER(C.c_float)
+
 SIGNATURES = {
     "lb_create": (C.c_int, [C.POINTER(lb_cell_params), C.c_int, C.c_int, C.c_void_p, C.POINTER(_H)]),
     "lb_init_fields": (C.c_int, [_H, _D, _D, _D, _D]),
@@ -54,6 +62,17 @@ SIGNATURES = {
     "lb_hb_fit": (C.c_int, [_D, _D, C.c_int, C.c_double, C.c_double, _D]),
     "lb_reductions_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                         C.c_void_p]),
+    # include/lbhb_mlp.h
+    "mlp_param_count": (C.c_longlong, []),
+    "mlp_create": (C.c_int, [C.POINTER(mlp_config), C.c_void_p, C.POINTER(_H)]),
+    "mlp_set_params": (C.c_int, [_H, _F, C.c_longlong]),
+    "mlp_get_params": (C.c_int, [_H, _F, C.c_longlong]),
+    "mlp_forward": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_void_p]),
+    "mlp_gradients": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, _F, C.POINTER(C.c_double)]),
+    "mlp_train_step": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "mlp_serve": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mlp_kernel_launches": (C.c_longlong, [_H]),
+    "mlp_destroy": (None, [_H]),
 }
 
 _lib = None

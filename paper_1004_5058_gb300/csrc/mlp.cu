@@ -1,0 +1,625 @@
+// Flow-curve surrogate kernels (include/lbhb_mlp.h): BF16 tensor-core GEMMs
+// with FP32 accumulation (mma.sync m16n8k16) and fused epilogues for the
+// forward pass, the backward pass and Adam on FP32 master weights.
+//
+// Every product is written as C[m][n] = sum_k A[m][k] B[n][k] with both operands
+// K-contiguous ("NT"): the forward pass multiplies activations [batch][in] by
+// weights [out][in]; the backward pass by a transposed weight copy [in][out];
+// the weight gradients multiply transposed activation and gradient copies
+// [features][batch], which the epilogues write alongside the normal layout.
+// Batch rows beyond the live batch are written as zeros, so padded rows and
+// columns never contribute.  Weight gradients use split-K partial sums reduced
+// in a fixed order, so results are reproducible.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbhb_mlp.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int NIN = 5, KIN = 16, HID = 128, NOUT = 2, NOUTP = 16;
+constexpr long long OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * NIN, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID * HID,
+                    OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID * HID, OFF_W4 = OFF_B3 + HID,
+                    OFF_B4 = OFF_W4 + NOUT * HID, NPARAM = OFF_B4 + NOUT;
+
+struct LayerDef {
+    int in, in_p, out, out_p;
+    long long offW, offB;
+};
+__host__ __device__ constexpr LayerDef layer_def(int l)
+{
+    return l == 0   ? LayerDef{NIN, KIN, HID, HID, OFF_W1, OFF_B1}
+           : l == 1 ? LayerDef{HID, HID, HID, HID, OFF_W2, OFF_B2}
+           : l == 2 ? LayerDef{HID, HID, HID, HID, OFF_W3, OFF_B3}
+                    : LayerDef{HID, HID, NOUT, NOUTP, OFF_W4, OFF_B4};
+}
+constexpr int KSPLIT = 512;  // batch rows per split-K partial of a weight gradient
+
+enum { EPI_TANH = 0, EPI_OUT = 1, EPI_DTANH = 2, EPI_PARTIAL = 3 };
+
+struct Epi {
+    const float* bias;  // EPI_TANH, EPI_OUT: [N]
+    bf16* out_b;        // EPI_TANH, EPI_DTANH: [rows][ld_out]
+    bf16* out_t;        // EPI_TANH, EPI_DTANH: [N][ld_t] (transposed copy)
+    float* out_f;       // EPI_OUT: [rows][ld_out]; EPI_PARTIAL: [split][M][N]
+    const bf16* hprev;  // EPI_DTANH: activation whose tanh derivative is applied, [rows][ld_out]
+    int ld_out, ld_t;
+    int rows_live;      // batch rows that hold data; later rows are written as zero
+    int rows_buf;       // rows the buffers have
+};
+
+__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// C[m][n] = sum_{k in split} A[m][k] B[n][k]; 64x64 tile per CTA, 4 warps of
+// 32x32, BK = 32.  K, the split chunk and both leading dimensions are multiples
+// of 8 (16-byte vector loads).
+template <int EPI>
+__global__ void __launch_bounds__(128) gemm_nt(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
+                                               int ldb, int M, int N, int K, int kchunk, Epi ep)
+{
+    __shared__ __align__(16) bf16 As[64][40];
+    __shared__ __align__(16) bf16 Bs[64][40];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+
+    for (int k0 = kbeg; k0 < kend; k0 += 32) {
+#pragma unroll
+        for (int rep = 0; rep < 2; ++rep) {
+            const int c = tid + rep * 128, r = c >> 2, kk = (c & 3) * 8;
+            uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+            if (m0 + r < M && k0 + kk < kend) va = *reinterpret_cast<const uint4*>(A + (long long)(m0 + r) * lda + k0 + kk);
+            if (n0 + r < N && k0 + kk < kend) vb = *reinterpret_cast<const uint4*>(B + (long long)(n0 + r) * ldb + k0 + kk);
+            *reinterpret_cast<uint4*>(&As[r][kk]) = va;
+            *reinterpret_cast<uint4*>(&Bs[r][kk]) = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < 32; ks += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int rb = wm * 32 + mi * 16;
+                a[mi][0] = *reinterpret_cast<const uint32_t*>(&As[rb + g][ks + 2 * t4]);
+                a[mi][1] = *reinterpret_cast<const uint32_t*>(&As[rb + g + 8][ks + 2 * t4]);
+                a[mi][2] = *reinterpret_cast<const uint32_t*>(&As[rb + g][ks + 2 * t4 + 8]);
+                a[mi][3] = *reinterpret_cast<const uint32_t*>(&As[rb + g + 8][ks + 2 * t4 + 8]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const int cb = wn * 32 + ni * 8;
+                b[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[cb + g][ks + 2 * t4]);
+                b[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[cb + g][ks + 2 * t4 + 8]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+                    mma_bf16(acc[mi][ni], a[mi][0], a[mi][1], a[mi][2], a[mi][3], b[ni][0], b[ni][1]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int row = m0 + wm * 32 + mi * 16 + g + (r >= 2 ? 8 : 0);
+                const int col = n0 + wn * 32 + ni * 8 + 2 * t4 + (r & 1);
+                if (col >= N) continue;
+                float v = acc[mi][ni][r];
+                if (EPI == EPI_PARTIAL) {
+                    if (row < M) ep.out_f[((long long)blockIdx.z * M + row) * N + col] = v;
+                    continue;
+                }
+                if (row >= ep.rows_buf) continue;
+                const bool live = row < ep.rows_live;
+                if (EPI == EPI_TANH) {
+                    v = live ? tanhf(v + ep.bias[col]) : 0.f;
+                } else if (EPI == EPI_OUT) {
+                    v = live ? v + ep.bias[col] : 0.f;
+                } else {  // EPI_DTANH
+                    const float h = __bfloat162float(ep.hprev[(long long)row * ep.ld_out + col]);
+                    v = live ? v * (1.f - h * h) : 0.f;
+                }
+                if (EPI == EPI_OUT) {
+                    ep.out_f[(long long)row * ep.ld_out + col] = v;
+                } else {
+                    const bf16 hv = __float2bfloat16_rn(v);
+                    ep.out_b[(long long)row * ep.ld_out + col] = hv;
+                    ep.out_t[(long long)col * ep.ld_t + row] = hv;
+                }
+            }
+}
+
+// z = (x - center) / half_range, padded to 16 columns, both layouts.
+__global__ void normalise_kernel(const float* __restrict__ x, int B, int Bbuf, const float* __restrict__ center,
+                                 const float* __restrict__ half, bf16* __restrict__ z, bf16* __restrict__ zt)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= Bbuf) return;
+    for (int c = 0; c < KIN; ++c) {
+        float v = 0.f;
+        if (b < B && c < NIN) v = (x[b * NIN + c] - center[c]) / half[c];
+        const bf16 hv = __float2bfloat16_rn(v);
+        z[(long long)b * KIN + c] = hv;
+        zt[(long long)c * Bbuf + b] = hv;
+    }
+}
+
+__device__ __forceinline__ float bce_logits(float z, float y)
+{
+    return fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
+}
+
+// dL/dy for y = (stress/scale, logit); per-block loss partials (FP64).
+__global__ void loss_grad_kernel(const float* __restrict__ out, const float* __restrict__ target,
+                                 const float* __restrict__ label, int B, int Bbuf, float inv_scale, float lam,
+                                 bf16* __restrict__ d, bf16* __restrict__ dt, double* __restrict__ part)
+{
+    __shared__ double red[256];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (b < Bbuf) {
+        float d0 = 0.f, d1 = 0.f;
+        if (b < B) {
+            const float y0 = out[(long long)b * NOUTP + 0], y1 = out[(long long)b * NOUTP + 1];
+            const float t = target[b] * inv_scale, lab = label[b];
+            const float e = y0 - t;
+            l = (double)(e * e) + (double)lam * (double)bce_logits(y1, lab);
+            d0 = 2.f * e / (float)B;
+            const float sg = 1.f / (1.f + expf(-y1));
+            d1 = lam * (sg - lab) / (float)B;
+        }
+        for (int c = 0; c < NOUTP; ++c) {
+            const float v = c == 0 ? d0 : (c == 1 ? d1 : 0.f);
+            const bf16 hv = __float2bfloat16_rn(v);
+            d[(long long)b * NOUTP + c] = hv;
+            dt[(long long)c * Bbuf + b] = hv;
+        }
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_finish_kernel(const double* __restrict__ part, int n, int B, float* __restrict__ loss_f,
+                                   double* __restrict__ loss_d)
+{
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    s /= (double)B;
+    if (loss_f) *loss_f = (float)s;
+    if (loss_d) *loss_d = s;
+}
+
+// grad[offW + o*in + i] = sum_s part[s][o][i] for the live block (o < out, i < in).
+__global__ void reduce_wgrad_kernel(const float* __restrict__ part, int S, int Mo, int Ni, int out, int in,
+                                    float* __restrict__ grad)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= out * in) return;
+    const int o = k / in, i = k % in;
+    float s = 0.f;
+    for (int p = 0; p < S; ++p) s += part[((long long)p * Mo + o) * Ni + i];
+    grad[k] = s;
+}
+
+// grad_b[o] = sum over live batch rows of d[o][b] (transposed gradient rows), one warp per o.
+__global__ void bias_grad_kernel(const bf16* __restrict__ dt, int Bbuf, int B, int out, float* __restrict__ grad)
+{
+    const int o = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (o >= out) return;
+    float s = 0.f;
+    for (int b = lane; b < B; b += 32) s += __bfloat162float(dt[(long long)o * Bbuf + b]);
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) s += __shfl_down_sync(0xffffffffu, s, w);
+    if (lane == 0) grad[o] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2)
+{
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.f - b1) * gk;
+    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    p[k] -= lr * (mk * c1) / (sqrtf(vk * c2) + eps);
+}
+
+// FP32 masters -> padded BF16 weights [out_p][in_p], their transposes, padded FP32 biases.
+__global__ void refresh_kernel(const float* __restrict__ p, bf16* w1, bf16* w1t, bf16* w2, bf16* w2t, bf16* w3,
+                               bf16* w3t, bf16* w4, bf16* w4t, float* b1, float* b2, float* b3, float* b4)
+{
+    bf16* W[4] = {w1, w2, w3, w4};
+    bf16* Wt[4] = {w1t, w2t, w3t, w4t};
+    float* Bp[4] = {b1, b2, b3, b4};
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int base = 0;
+    for (int l = 0; l < 4; ++l) {
+        const LayerDef L = layer_def(l);
+        const int nw = L.out_p * L.in_p;
+        if (k >= base && k < base + nw) {
+            const int o = (k - base) / L.in_p, i = (k - base) % L.in_p;
+            const float v = (o < L.out && i < L.in) ? p[L.offW + (long long)o * L.in + i] : 0.f;
+            const bf16 hv = __float2bfloat16_rn(v);
+            W[l][o * L.in_p + i] = hv;
+            Wt[l][i * L.out_p + o] = hv;
+        }
+        base += nw;
+        if (k >= base && k < base + L.out_p) {
+            const int o = k - base;
+            Bp[l][o] = o < L.out ? p[L.offB + o] : 0.f;
+        }
+        base += L.out_p;
+    }
+}
+
+__global__ void output_kernel(const float* __restrict__ out, int B, float scale, float* __restrict__ y)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    y[2 * b] = out[(long long)b * NOUTP] * scale;
+    y[2 * b + 1] = out[(long long)b * NOUTP + 1];
+}
+
+__global__ void serve_kernel(const float* __restrict__ x, const float* __restrict__ out, int B,
+                             const float* __restrict__ center, const float* __restrict__ half, float scale,
+                             float margin, float* __restrict__ stress, float* __restrict__ logit,
+                             int* __restrict__ fallback)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    bool outside = false;
+    for (int c = 0; c < NIN; ++c) {
+        const float xv = x[b * NIN + c];
+        outside |= !(fabsf(xv - center[c]) <= half[c]);  // NaN counts as outside
+    }
+    const float lg = out[(long long)b * NOUTP + 1];
+    stress[b] = out[(long long)b * NOUTP] * scale;
+    logit[b] = lg;
+    fallback[b] = (outside || !(fabsf(lg) >= margin)) ? 1 : 0;
+}
+
+}  // namespace
+
+struct mlp_handle {
+    mlp_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int bbuf = 0;  // batch rows of the buffers (max_batch rounded up to 64)
+    int splits = 0;
+    float *P = nullptr, *M = nullptr, *V = nullptr, *G = nullptr;
+    bf16 *W[4] = {}, *Wt[4] = {};
+    float* bias[4] = {};
+    bf16 *Z = nullptr, *Zt = nullptr;
+    bf16 *H[3] = {}, *Ht[3] = {};
+    float* OUT = nullptr;
+    bf16 *D[4] = {}, *Dt[4] = {};  // gradients w.r.t. pre-activations of layers 1..3, and the output
+    float* part = nullptr;         // split-K partials
+    double* loss_part = nullptr;
+    double* loss_d = nullptr;
+    float *center = nullptr, *half = nullptr;
+    long long adam_t = 0;
+    long long launches = 0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+void release(mlp_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+template <class T>
+cudaError_t alloc(mlp_handle* h, T** p, size_t n)
+{
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaSuccess) {
+        h->allocs.push_back(*p);
+        e = cudaMemsetAsync(*p, 0, n * sizeof(T), h->stream);
+    }
+    return e;
+}
+
+int rows8(int B) { return (B + 7) / 8 * 8; }
+
+template <int EPI>
+cudaError_t gemm(mlp_handle* h, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, int kchunk,
+                 const Epi& ep)
+{
+    const int splits = (K + kchunk - 1) / kchunk;
+    dim3 grid((M + 63) / 64, (N + 63) / 64, splits);
+    gemm_nt<EPI><<<grid, 128, 0, h->stream>>>(A, lda, B, ldb, M, N, K, kchunk, ep);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t forward(mlp_handle* h, const float* x, int B)
+{
+    const int Br = rows8(B), bb = h->bbuf;
+    normalise_kernel<<<(bb + 127) / 128, 128, 0, h->stream>>>(x, B, bb, h->center, h->half, h->Z, h->Zt);
+    h->launches++;
+    const bf16* in = h->Z;
+    int ld_in = KIN;
+    for (int l = 0; l < 4; ++l) {
+        const LayerDef L = layer_def(l);
+        Epi ep{};
+        ep.bias = h->bias[l];
+        ep.rows_live = B;
+        ep.rows_buf = bb;
+        cudaError_t e;
+        if (l < 3) {
+            ep.out_b = h->H[l];
+            ep.out_t = h->Ht[l];
+            ep.ld_out = HID;
+            ep.ld_t = bb;
+            e = gemm<EPI_TANH>(h, in, ld_in, h->W[l], L.in_p, Br, L.out_p, L.in_p, L.in_p, ep);
+            in = h->H[l];
+            ld_in = HID;
+        } else {
+            ep.out_f = h->OUT;
+            ep.ld_out = NOUTP;
+            e = gemm<EPI_OUT>(h, in, ld_in, h->W[l], L.in_p, Br, L.out_p, L.in_p, L.in_p, ep);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Loss gradient and backpropagation into h->G (flat FP32 gradient).
+cudaError_t backward(mlp_handle* h, const float* target, const float* label, int B, float* loss_f, double* loss_d)
+{
+    const int Br = rows8(B), bb = h->bbuf;
+    const int nblk = (bb + 255) / 256;
+    loss_grad_kernel<<<nblk, 256, 0, h->stream>>>(h->OUT, target, label, B, bb, (float)(1.0 / h->cfg.sigma_scale),
+                                                   (float)h->cfg.lam, h->D[3], h->Dt[3], h->loss_part);
+    loss_finish_kernel<<<1, 32, 0, h->stream>>>(h->loss_part, nblk, B, loss_f, loss_d);
+    h->launches += 2;
+    for (int l = 3; l >= 0; --l) {
+        const LayerDef L = layer_def(l);
+        const bf16* xt = l == 0 ? h->Zt : h->Ht[l - 1];  // layer input, transposed [in_p][bb]
+        // weight gradient: dW[o][i] = sum_b D_l[b][o] X[b][i]
+        Epi ep{};
+        ep.out_f = h->part;
+        cudaError_t e = gemm<EPI_PARTIAL>(h, h->Dt[l], bb, xt, bb, L.out_p, L.in_p, Br, KSPLIT, ep);
+        if (e != cudaSuccess) return e;
+        const int S = (Br + KSPLIT - 1) / KSPLIT;
+        reduce_wgrad_kernel<<<(L.out * L.in + 255) / 256, 256, 0, h->stream>>>(h->part, S, L.out_p, L.in_p, L.out,
+                                                                                L.in, h->G + L.offW);
+        bias_grad_kernel<<<(L.out + 7) / 8, 256, 0, h->stream>>>(h->Dt[l], bb, B, L.out, h->G + L.offB);
+        h->launches += 2;
+        if (l > 0) {
+            // D_{l-1} = (D_l W_l) * (1 - h_{l-1}^2)
+            Epi ed{};
+            ed.out_b = h->D[l - 1];
+            ed.out_t = h->Dt[l - 1];
+            ed.hprev = h->H[l - 1];
+            ed.ld_out = HID;
+            ed.ld_t = bb;
+            ed.rows_live = B;
+            ed.rows_buf = bb;
+            e = gemm<EPI_DTANH>(h, h->D[l], L.out_p, h->Wt[l], L.out_p, Br, L.in_p, L.out_p, L.out_p, ed);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t refresh(mlp_handle* h)
+{
+    int total = 0;
+    for (int l = 0; l < 4; ++l) total += layer_def(l).out_p * layer_def(l).in_p + layer_def(l).out_p;
+    refresh_kernel<<<(total + 255) / 256, 256, 0, h->stream>>>(h->P, h->W[0], h->Wt[0], h->W[1], h->Wt[1], h->W[2],
+                                                                h->Wt[2], h->W[3], h->Wt[3], h->bias[0], h->bias[1],
+                                                                h->bias[2], h->bias[3]);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+lb_status check_batch(const mlp_handle* h, int B) { return (B < 1 || B > h->cfg.max_batch) ? LB_ERR_INVALID : LB_OK; }
+
+}  // namespace
+
+extern "C" {
+
+long long mlp_param_count(void) { return NPARAM; }
+
+lb_status mlp_create(const mlp_config* cfg, void* cuda_stream, mlp_handle** out)
+{
+    if (!out || !cfg) return LB_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->max_batch < 1 || cfg->max_batch > (1 << 24) || !(cfg->sigma_scale > 0.0) || !(cfg->lr >= 0.0))
+        return LB_ERR_INVALID;
+    for (int c = 0; c < NIN; ++c)
+        if (!(cfg->half_range[c] > 0.0) || !std::isfinite(cfg->center[c])) return LB_ERR_INVALID;
+    mlp_handle* h = new (std::nothrow) mlp_handle();
+    if (!h) return LB_ERR_NOMEM;
+    h->cfg = *cfg;
+    cudaGetDevice(&h->device);
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
+    else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        h->own_stream = e == cudaSuccess;
+    }
+    h->bbuf = (cfg->max_batch + 63) / 64 * 64;
+    const int bb = h->bbuf;
+    h->splits = (bb + KSPLIT - 1) / KSPLIT;
+    if (e == cudaSuccess) e = alloc(h, &h->P, NPARAM);
+    if (e == cudaSuccess) e = alloc(h, &h->M, NPARAM);
+    if (e == cudaSuccess) e = alloc(h, &h->V, NPARAM);
+    if (e == cudaSuccess) e = alloc(h, &h->G, NPARAM);
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+        e = alloc(h, &h->W[l], (size_t)layer_def(l).out_p * layer_def(l).in_p);
+        if (e == cudaSuccess) e = alloc(h, &h->Wt[l], (size_t)layer_def(l).out_p * layer_def(l).in_p);
+        if (e == cudaSuccess) e = alloc(h, &h->bias[l], (size_t)layer_def(l).out_p);
+    }
+    if (e == cudaSuccess) e = alloc(h, &h->Z, (size_t)bb * KIN);
+    if (e == cudaSuccess) e = alloc(h, &h->Zt, (size_t)bb * KIN);
+    for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+        e = alloc(h, &h->H[l], (size_t)bb * HID);
+        if (e == cudaSuccess) e = alloc(h, &h->Ht[l], (size_t)bb * HID);
+        if (e == cudaSuccess) e = alloc(h, &h->D[l], (size_t)bb * HID);
+        if (e == cudaSuccess) e = alloc(h, &h->Dt[l], (size_t)bb * HID);
+    }
+    if (e == cudaSuccess) e = alloc(h, &h->D[3], (size_t)bb * NOUTP);
+    if (e == cudaSuccess) e = alloc(h, &h->Dt[3], (size_t)bb * NOUTP);
+    if (e == cudaSuccess) e = alloc(h, &h->OUT, (size_t)bb * NOUTP);
+    if (e == cudaSuccess) e = alloc(h, &h->part, (size_t)h->splits * HID * HID);
+    if (e == cudaSuccess) e = alloc(h, &h->loss_part, (size_t)(bb + 255) / 256);
+    if (e == cudaSuccess) e = alloc(h, &h->loss_d, 1);
+    if (e == cudaSuccess) e = alloc(h, &h->center, NIN);
+    if (e == cudaSuccess) e = alloc(h, &h->half, NIN);
+    if (e == cudaSuccess) {
+        float c[NIN], hr[NIN];
+        for (int i = 0; i < NIN; ++i) {
+            c[i] = (float)cfg->center[i];
+            hr[i] = (float)cfg->half_range[i];
+        }
+        e = cudaMemcpyAsync(h->center, c, sizeof c, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->half, hr, sizeof hr, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release(h);
+        return e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+lb_status mlp_set_params(mlp_handle* h, const float* params, long long n)
+{
+    if (!h || !params || n != NPARAM) return LB_ERR_INVALID;
+    cudaError_t e = cudaMemcpyAsync(h->P, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->M, 0, sizeof(float) * NPARAM, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->V, 0, sizeof(float) * NPARAM, h->stream);
+    if (e == cudaSuccess) e = refresh(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->adam_t = 0;
+    return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
+
+lb_status mlp_get_params(mlp_handle* h, float* params, long long n)
+{
+    if (!h || !params || n != NPARAM) return LB_ERR_INVALID;
+    cudaError_t e = cudaMemcpyAsync(params, h->P, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
+
+lb_status mlp_forward(mlp_handle* h, const float* x, int batch, float* out)
+{
+    if (!h || !x || !out) return LB_ERR_INVALID;
+    if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
+    cudaError_t e = forward(h, x, batch);
+    if (e == cudaSuccess) {
+        output_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(h->OUT, batch, (float)h->cfg.sigma_scale, out);
+        h->launches++;
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
+
+lb_status mlp_gradients(mlp_handle* h, const float* x, const float* target_stress, const float* label, int batch,
+                        float* grad, double* loss)
+{
+    if (!h || !x || !target_stress || !label || !grad) return LB_ERR_INVALID;
+    if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
+    cudaError_t e = forward(h, x, batch);
+    if (e == cudaSuccess) e = backward(h, target_stress, label, batch, nullptr, h->loss_d);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad, h->G, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, h->stream);
+    double l = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&l, h->loss_d, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (loss) *loss = l;
+    return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
+
+lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stress, const float* label, int batch,
+                         float* loss_dev)
+{
+    if (!h || !x || !target_stress || !label) return LB_ERR_INVALID;
+    if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
+    cudaError_t e = forward(h, x, batch);
+    if (e == cudaSuccess) e = backward(h, target_stress, label, batch, loss_dev, nullptr);
+    if (e == cudaSuccess) {
+        h->adam_t++;
+        const double b1 = h->cfg.beta1, b2 = h->cfg.beta2;
+        const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)h->adam_t)));
+        const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)h->adam_t)));
+        adam_kernel<<<(int)((NPARAM + 255) / 256), 256, 0, h->stream>>>(h->P, h->M, h->V, h->G, NPARAM,
+                                                                        (float)h->cfg.lr, (float)b1, (float)b2,
+                                                                        (float)h->cfg.eps, c1, c2);
+        h->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = refresh(h);
+    return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
+
+lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit, int* fallback)
+{
+    if (!h || !x || !stress || !logit || !fallback) return LB_ERR_INVALID;
+    if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
+    cudaError_t e = forward(h, x, batch);
+    if (e == cudaSuccess) {
+        serve_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(x, h->OUT, batch, h->center, h->half,
+                                                                 (float)h->cfg.sigma_scale,
+                                                                 (float)h->cfg.logit_margin, stress, logit, fallback);
+        h->launches++;
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
+
+long long mlp_kernel_launches(const mlp_handle* h) { return h ? h->launches : 0; }
+
+void mlp_destroy(mlp_handle* h) { release(h); }
+
+}  // extern "C"

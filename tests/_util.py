@@ -1,19 +1,23 @@
 """Shared helpers of the test suite (no method arithmetic here)."""
+import glob
 import os
 import re
 
 import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "lbhb.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def header_functions(path=HEADER):
-    """Names of the functions include/lbhb.h declares."""
-    src = open(path).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", src, flags=re.M)
-    return sorted({n for n in names if n.startswith("lb_") or n.startswith("mlp_")})
+def header_functions(paths=None):
+    """Names of the functions the headers under include/ declare."""
+    out = set()
+    for path in paths or HEADERS:
+        src = open(path).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", src, flags=re.M)
+        out |= {n for n in names if n.startswith("lb_") or n.startswith("mlp_")}
+    return sorted(out)
 
 
 def oracle_runs(cells, ra, rb, ux=None, uy=None, steps=0, sampling=None):
