@@ -33,6 +33,7 @@ from . import inputs as I
 
 REFERENCE = dict(g_aa1=-9.0, g_aa2=8.1, g_ab=0.405, tau=1.0)
 N_IN = 5
+CUDA_STREAM_LEGACY = 0x1  # the cudaStream_t value of the legacy default stream
 
 
 def param_count() -> int:
@@ -75,7 +76,12 @@ class Surrogate:
     """Handle of the BF16 surrogate kernels (mlp_create .. mlp_destroy)."""
 
     def __init__(self, box: Box, sigma_scale: float, max_batch: int = 4096, lam: float = 1.0, lr: float = 1e-3,
-                 logit_margin: float = 1.0, stream=None):
+                 logit_margin: float = 1.0, stream="current"):
+        """stream: "current" (default) enqueues on torch's current CUDA stream, so
+        the kernels are ordered with torch's own work and with its caching
+        allocator's reuse of the tensors passed in; or a torch stream / raw
+        cudaStream_t value; None for a library-owned stream (the caller must
+        then keep input tensors alive until the stream is done)."""
         self.lib = L.load()
         cfg = L.mlp_config()
         cfg.max_batch = int(max_batch)
@@ -87,8 +93,14 @@ class Surrogate:
         cfg.logit_margin = float(logit_margin)
         self.cfg, self.box, self.max_batch = cfg, box, int(max_batch)
         h = L._H()
-        s = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
-        L.check(self.lib.mlp_create(C.byref(cfg), s or None, C.byref(h)))
+        if isinstance(stream, str) and stream == "current":
+            import torch
+            s = int(torch.cuda.current_stream().cuda_stream) or CUDA_STREAM_LEGACY
+        elif stream is None:
+            s = None
+        else:
+            s = (stream if isinstance(stream, int) else int(stream.cuda_stream)) or CUDA_STREAM_LEGACY
+        L.check(self.lib.mlp_create(C.byref(cfg), s, C.byref(h)))
         self.h = h
         self.n = param_count()
 
