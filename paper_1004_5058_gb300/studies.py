@@ -1,0 +1,132 @@
+"""Runners of the workloads the library is measured on (all through the C ABI):
+
+precision_study  one Couette cell run three ways (FP64, FP32, FP16-shifted
+                 storage), compared with the FP64 run: max |d rho|, relative
+                 sigma_xy error, and MLUPS of each.
+flow_curve       many Couette cells (wall speeds x cross couplings G_AB) in one
+                 batched, graph-captured launch per step; per G_AB the
+                 Herschel-Bulkley fit sigma = sigma_Y + A S^beta; flow-curve
+                 points per second.  With sequential=True the same cells run one
+                 after another with the generic kernel and no graphs, the plain
+                 single-cell baseline of the batched run.
+
+python -m paper_1004_5058_gb300.studies precision|flow_curve [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs as I
+from .lattice import Lattice, hb_fit
+
+
+def _cuda_time(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def precision_study(n: int = 4096, u_wall: float = 1e-3, steps: int = 50000, every: int = 100,
+                    precisions=("fp64", "fp32", "fp16"), seed: int = 1004, g_ab: float = 0.405):
+    """Same cell, same seeded start, three storage precisions."""
+    cell = I.make_cell("paper", nx=n, ny=n, g_ab=g_ab, bc=1, u_wall=u_wall)
+    ra, rb = I.random_fields(n, n, seed=seed)
+    ux, uy = I.couette_velocity(n, n, u_wall)
+    res = {}
+    for prec in precisions:
+        with Lattice([cell], prec) as lat:
+            lat.init_fields(ra, rb, ux, uy).set_sampling(steps // 2, every)
+            lat.step(10)
+            lat.sync()
+            lat.init_fields(ra, rb, ux, uy).set_sampling(steps // 2, every)
+            _, dt = _cuda_time(lambda: lat.step(steps).sync())
+            a, b, _, _ = lat.fields()
+            sigma, S, Sb = lat.shear_stress()
+            mass, _ = lat.reductions()
+            res[prec] = dict(rho_a=a[0], rho_b=b[0], sigma=float(sigma[0]), S=float(S[0]), S_bulk=float(Sb[0]),
+                             mlups=n * n * steps / dt / 1e6, seconds=dt, kernel=lat.kernel(),
+                             mass_drift=float(abs(mass[0, 0] - ra.sum()) / ra.sum()))
+    ref = res.get("fp64")
+    summary = {"n": n, "u_wall": u_wall, "steps": steps, "g_ab": g_ab}
+    for prec, r in res.items():
+        row = {"mlups": r["mlups"], "seconds": r["seconds"], "sigma_xy": r["sigma"], "shear_rate": r["S"],
+               "kernel": r["kernel"], "mass_drift": r["mass_drift"]}
+        if ref is not None and prec != "fp64":
+            row["max_abs_drho"] = float(max(np.abs(r["rho_a"] - ref["rho_a"]).max(),
+                                            np.abs(r["rho_b"] - ref["rho_b"]).max()))
+            row["sigma_rel_err"] = abs(r["sigma"] - ref["sigma"]) / abs(ref["sigma"])
+        summary[prec] = row
+    return summary
+
+
+def flow_curve(L: int = 512, steps: int = 100000, every: int = 20, n_speeds: int = 16, u_lo: float = 1e-5,
+               u_hi: float = 1e-2, g_abs=(0.3, 0.35, 0.405, 0.45), precision: str = "fp32",
+               sequential: bool = False, seed: int = 1004):
+    """Cells = wall speeds x G_AB values (paper couplings otherwise)."""
+    speeds = I.log_spaced(u_lo, u_hi, n_speeds)
+    cells = [I.make_cell("paper", nx=L, ny=L, g_ab=g, bc=1, u_wall=u) for g in g_abs for u in speeds]
+    ra, rb = I.random_fields(L, L, n_cells=len(cells), seed=seed)
+    ux, uy = I.couette_velocity(L, L, [c.u_wall for c in cells], n_cells=len(cells))
+    if not sequential:
+        with Lattice(cells, precision) as lat:
+            lat.init_fields(ra, rb, ux, uy)
+            kern = lat.autotune()
+            lat.init_fields(ra, rb, ux, uy).set_sampling(steps // 2, every)
+            _, dt = _cuda_time(lambda: lat.step(steps).sync())
+            sigma, S, Sb = lat.shear_stress()
+    else:
+        sig_l, S_l, Sb_l = [], [], []
+        kern = ("generic", 32, 8)
+        dt = 0.0
+        for c, cell in enumerate(cells):
+            with Lattice([cell], precision) as lat:
+                lat.set_kernel("generic")
+                lat.init_fields(ra[c:c + 1], rb[c:c + 1], ux[c:c + 1], uy[c:c + 1]).set_sampling(steps // 2, every)
+                _, t = _cuda_time(lambda: lat.step(steps).sync())
+                dt += t
+                s, r, b = lat.shear_stress()
+            sig_l.append(s[0])
+            S_l.append(r[0])
+            Sb_l.append(b[0])
+        sigma, S, Sb = np.array(sig_l), np.array(S_l), np.array(Sb_l)
+    out = {"L": L, "steps": steps, "cells": len(cells), "precision": precision, "kernel": kern,
+           "seconds": dt, "mlups": len(cells) * L * L * steps / dt / 1e6, "points_per_s": len(cells) / dt,
+           "curves": {}}
+    for k, g in enumerate(g_abs):
+        sl = slice(k * n_speeds, (k + 1) * n_speeds)
+        s_, r_ = sigma[sl], S[sl]
+        ok = np.isfinite(r_) & (r_ > 0) & np.isfinite(s_)
+        fit = hb_fit(r_[ok], s_[ok]) if ok.sum() >= 3 else None
+        out["curves"][str(g)] = {"u_wall": list(speeds), "sigma_xy": [float(v) for v in s_],
+                                 "shear_rate": [float(v) for v in r_], "shear_bulk": [float(v) for v in Sb[sl]],
+                                 "hb_fit": fit}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("study", choices=["precision", "flow_curve", "flow_curve_sequential"])
+    ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
+    ap.add_argument("--out", default="")
+    a = ap.parse_args()
+    if a.study == "precision":
+        r = precision_study(n=512, steps=2000) if a.quick else precision_study()
+    else:
+        kw = dict(L=128, steps=2000, n_speeds=4) if a.quick else {}
+        r = flow_curve(sequential=a.study.endswith("sequential"), **kw)
+    s = json.dumps(r, default=lambda o: o.tolist() if hasattr(o, "tolist") else str(o))
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(s + "\n")
+    print(s)
+
+
+if __name__ == "__main__":
+    main()
