@@ -9,7 +9,7 @@
 #include <cmath>
 #include <vector>
 
-#include "../../include/lbhb.h"
+#include "lbhb.h"
 
 namespace {
 

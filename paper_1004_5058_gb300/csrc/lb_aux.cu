@@ -144,17 +144,19 @@ __global__ void state_sums_finish(const double* __restrict__ part, int nblk, dou
 
 // Folds the partials of one sampled step into the time averages:
 // acc_prof[c][y] += sum_b prof_part[c][b][y];  acc_wall[c][w] += sum_b wall_part[c][b][w].
+// One warp per (cell, block of 32 rows), spread over the whole GPU.
 __global__ void accumulate_kernel(const double* __restrict__ prof_part, const double* __restrict__ wall_part,
                                   int nbx, int ny, int bc, double* __restrict__ acc_prof,
                                   double* __restrict__ acc_wall)
 {
     const int cell = blockIdx.x;
-    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+    const int y = blockIdx.y * 32 + threadIdx.x;
+    if (y < ny) {
         double s = 0.0;
         for (int b = 0; b < nbx; ++b) s += prof_part[((long long)cell * nbx + b) * ny + y];
         acc_prof[(long long)cell * ny + y] += s;
     }
-    if (bc == 1 && threadIdx.x < 2) {
+    if (bc == 1 && blockIdx.y == 0 && threadIdx.x < 2) {
         double s = 0.0;
         for (int b = 0; b < nbx; ++b) s += wall_part[((long long)cell * nbx + b) * 2 + threadIdx.x];
         acc_wall[cell * 2 + threadIdx.x] += s;
@@ -217,7 +219,8 @@ cudaError_t launch_state_sums(const T* f, const Geom& g, const CellDev* cells, d
 cudaError_t launch_accumulate(const double* prof_part, const double* wall_part, int nbx, int ny, int bc,
                               int n_cells, double* acc_prof, double* acc_wall, cudaStream_t st)
 {
-    accumulate_kernel<<<n_cells, 256, 0, st>>>(prof_part, wall_part, nbx, ny, bc, acc_prof, acc_wall);
+    accumulate_kernel<<<dim3(n_cells, (ny + 31) / 32), 32, 0, st>>>(prof_part, wall_part, nbx, ny, bc, acc_prof,
+                                                                      acc_wall);
     return cudaGetLastError();
 }
 

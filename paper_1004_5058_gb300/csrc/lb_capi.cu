@@ -14,7 +14,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "../../include/lbhb.h"
+#include "lbhb.h"
 #include "lb_internal.h"
 
 using namespace lbhb;

@@ -13,7 +13,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/lbhb.h"
+#include "lbhb.h"
 #include "lb_internal.h"
 
 using namespace lbhb;

@@ -74,8 +74,13 @@ __host__ __device__ constexpr int ring_species_stride(int tx)
     return RING * (tx + 4) + ((16 - (RING * (tx + 4)) % 32) + 32) % 32;
 }
 
+// Threads per CTA: a thread pair per column (2 TX) plus one service warp that
+// issues the TMA copies and computes the four halo columns of psi/rho, so the
+// column warps all do the same work between two barriers.
+__host__ __device__ constexpr int tiled_threads(int tx) { return 2 * tx + 32; }
+
 template <class T, int TX, bool SAMPLE>
-__global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
+__global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
                                                             const __grid_constant__ CUtensorMap tm_halo,
                                                             T* __restrict__ fout, Geom g, int bc, int ty,
                                                             int n_strips, int n_seg,
@@ -101,10 +106,15 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
     C* rho_ring = psi_ring + 2 * SS;
     uint64_t* bars = reinterpret_cast<uint64_t*>(rho_ring + 2 * SS);
 
+    constexpr int NW = 2 * TX / 32;           // column warps
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
-    const int sp = lane >> 4;                 // species of this thread
-    const int c = warp * 16 + (lane & 15);    // column of this thread in the strip
+    const bool svc = warp == NW;              // the service warp
+    const bool producer = svc && lane == 0;   // issues the TMA copies
+    // column warps: lanes 0-15 species A, 16-31 species B of 16 columns;
+    // service warp: lanes 0-3 species A, 4-7 species B of the halo columns
+    const int sp = svc ? (lane >> 2) & 1 : lane >> 4;
+    const int c = svc ? 0 : warp * 16 + (lane & 15);  // column of this thread in the strip
     if (t == 0) {
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
         fence_mbar_init();
@@ -136,7 +146,7 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
         ixl = ix0 >= H ? ix0 - H : g.nx - H;
         ixr = ix0 + TX < g.nx ? ix0 + TX : 0;
     };
-    if (t == 0) load_item();
+    if (producer) load_item();
     auto issue_upto = [&](uint32_t limit) {
         while (n_issued < limit && iw < items) {
             const int slot = (int)(n_issued % D);
@@ -184,16 +194,16 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
 
         __syncthreads();  // rings of the previous item are no longer read
 
-        if (t == 0) issue_upto(nrow + D);  // rows of earlier items are all done
+        if (producer) issue_upto(nrow + D);  // rows of earlier items are all done
         auto wait_row = [&](int k) -> bool {
             const uint32_t n = nrow + (uint32_t)k;
             return mbar_wait_bounded(&bars[n % D], (n / D) & 1u);
         };
-        // rho_s, psi_s of logical row k (own species, own column; lanes 0 and 16
-        // of warps 0..3 also take the four halo columns)
-        auto psi_stage = [&](int k) {
+        // rho_s, psi_s of logical row k into ring row `ring_row` (own species,
+        // own column; the service warp takes the halo columns)
+        auto psi_stage = [&](int k, int ring_row) {
             const unsigned char* base = fring + ((nrow + (uint32_t)k) % D) * SLOT;
-            const int ring = sp * SS + (k % RING) * W;
+            const int ring = sp * SS + ring_row * W;
             auto site = [&](const T* src, int stride, int col, int pos) {
                 C acc = C(0);
 #pragma unroll
@@ -204,16 +214,14 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
                 psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
                 rho_ring[ring + pos] = acc;
             };
-            site(reinterpret_cast<const T*>(base), TX, c, c + 2);
-            // halo column h (0,1: columns -2,-1; 2,3: columns TX, TX+1) of this
-            // thread's species goes to warp h % NW, lane h / NW of the half-warp
-            constexpr int NW = 2 * TX / 32;
-            const int hl = lane & 15;
-            if (hl < (4 + NW - 1) / NW) {
-                const int h = hl * NW + warp;
+            if (!svc) {
+                site(reinterpret_cast<const T*>(base), TX, c, c + 2);
+            } else if (lane < 8) {
+                // halo column h: 0,1 -> columns -2,-1 (left box); 2,3 -> TX, TX+1 (right box)
+                const int h = lane & 3;
                 if (h < 2)
                     site(reinterpret_cast<const T*>(base + MAIN_AL), H, H - 2 + h, h);
-                else if (h < 4)
+                else
                     site(reinterpret_cast<const T*>(base + MAIN_AL + HALO_AL), H, h - 2, TX + h);
             }
         };
@@ -221,11 +229,16 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
         bool ok = true;
         for (int k = 0; k < 4; ++k) {
             ok = wait_row(k) && ok;
-            psi_stage(k);
+            psi_stage(k, k);
         }
+        int r0 = 0;  // ring row of logical row j (rows j .. j+4 are read by the collision of row j+2)
         for (int j = 0; j < rows; ++j) {
+            int rr[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) rr[d] = r0 + d >= RING ? r0 + d - RING : r0 + d;
             ok = wait_row(j + 4) && ok;
-            psi_stage(j + 4);
+            psi_stage(j + 4, rr[4]);
+            r0 = rr[1];
             // barrier: psi/rho of row j+4 visible, collision of row j+1 finished
             // everywhere; it also tells every thread whether any wait ran out
             if (__syncthreads_or(ok ? 0 : 1)) {
@@ -233,7 +246,8 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
                 break;
             }
             // rows 0 .. j+1 of this item are done with their slots
-            if (t == 0) issue_upto(nrow + (uint32_t)(j + 2 + D));
+            if (producer) issue_upto(nrow + (uint32_t)(j + 2 + D));
+            if (svc) continue;
             // ---- collide logical row k = j + 2 (lattice row y)
             const int k = j + 2, y = y0 + j;
             const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT);
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
             const C* ro = rho_ring + (1 - sp) * SS + c + 2;
             int rb[5];
 #pragma unroll
-            for (int d = 0; d < 5; ++d) rb[d] = ((k - 2 + d) % RING) * W;
+            for (int d = 0; d < 5; ++d) rb[d] = rr[d] * W;
             const C psi_s = ps[rb[2]];
             const C rho_s = rho_ring[sp * SS + c + 2 + rb[2]];
             const C rho_o = ro[rb[2]];
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
             const C jx = jx_s + __shfl_xor_sync(0xffffffffu, jx_s, 16);
             const C jy = jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16);
             const C rho_t = rho_s + rho_o;
-            const C inv_rho = C(1) / rho_t;
+            const C inv_rho = fast_div<C>(C(1), rho_t);
             C fs[9], Fx, Fy;
             collide_species<C>(f, rho_s, psi_s, jx * inv_rho, jy * inv_rho, sm, ga, gr, p, fs, &Fx, &Fy);
 
@@ -307,7 +321,7 @@ __global__ void __launch_bounds__(2 * TX) tiled_step_kernel(const __grid_constan
             }
         }
         if (aborted) {
-            if (t == 0) {
+            if (producer) {
                 atomicOr(err, ERR_TIMEOUT);
                 // drain the copies still in flight before shared memory is released
                 for (uint32_t n = nrow; n < n_issued; ++n) mbar_wait_bounded(&bars[n % D], (n / D) & 1u, 1u << 20);
@@ -457,7 +471,8 @@ TiledPlan* tiled_create(const Geom& g, int elem, int bc, void* f0, void* f1, int
             return nullptr;
         }
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 2 * tile_x, p->smem) != cudaSuccess || o < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, tiled_threads(tile_x), p->smem) != cudaSuccess ||
+            o < 1) {
             cudaGetLastError();
             if (err_msg) *err_msg = "tiled kernel does not fit on an SM";
             delete p;
@@ -492,7 +507,7 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
     void* args[] = {(void*)&p->tm_main[src], (void*)&p->tm_halo[src], (void*)&dst, (void*)&g, (void*)&bc,
                     (void*)&ty, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
                     (void*)&wall_part, (void*)&err};
-    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid), dim3(2 * p->tx), args, p->smem, st);
+    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid), dim3(tiled_threads(p->tx)), args, p->smem, st);
     *n_launches += 1;
     return e;
 }

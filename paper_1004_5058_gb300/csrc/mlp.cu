@@ -20,7 +20,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/lbhb_mlp.h"
+#include "lbhb_mlp.h"
 
 namespace {
 
