@@ -259,6 +259,31 @@ __device__ inline double warp_sum_compensated(float v)
     }
     return (double)hi + (double)lo;
 }
+// Same for the sum of two values per lane (a + b is the first two-sum).
+__device__ inline double warp_sum_compensated2(float a, float b)
+{
+    float hi = __fadd_rn(a, b);
+    const float bp = __fsub_rn(hi, a);
+    float lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bp)), __fsub_rn(b, bp));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const float sum = __fadd_rn(hi, h2);
+        const float bq = __fsub_rn(sum, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bq)), __fsub_rn(h2, bq));
+        hi = sum;
+        lo = __fadd_rn(__fadd_rn(lo, l2), err);
+    }
+    return (double)hi + (double)lo;
+}
+__device__ inline double warp_sum_compensated2(double a, double b)
+{
+    double v = a + b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
 __device__ inline double warp_sum_compensated(double v)
 {
 #pragma unroll

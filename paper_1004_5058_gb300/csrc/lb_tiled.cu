@@ -74,10 +74,42 @@ __host__ __device__ constexpr int ring_species_stride(int tx)
     return RING * (tx + 4) + ((16 - (RING * (tx + 4)) % 32) + 32) % 32;
 }
 
-// Threads per CTA: a thread pair per column (2 TX) plus one service warp that
-// issues the TMA copies and computes the four halo columns of psi/rho, so the
-// column warps all do the same work between two barriers.
-__host__ __device__ constexpr int tiled_threads(int tx) { return 2 * tx + 32; }
+// Two adjacent columns of one species per thread: vector (8-byte for FP32)
+// shared-memory accesses and two independent sites per thread.
+template <class T> struct Vec2;
+template <> struct Vec2<float> {
+    __device__ static void ld(const float* p, float& a, float& b)
+    {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void st(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+};
+template <> struct Vec2<double> {
+    __device__ static void ld(const double* p, double& a, double& b)
+    {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void st(double* p, double a, double b) { *reinterpret_cast<double2*>(p) = make_double2(a, b); }
+};
+template <> struct Vec2<__half> {
+    __device__ static void ld(const __half* p, float& a, float& b)
+    {
+        const __half2 v = *reinterpret_cast<const __half2*>(p);
+        a = __low2float(v);
+        b = __high2float(v);
+    }
+    // FP16 storage of shifted values: the caller subtracts the shift
+    __device__ static void st(__half* p, float a, float b) { *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b); }
+};
+
+// Threads per CTA: a thread per (species, column pair), TX threads, plus one
+// service warp that issues the TMA copies and computes the four halo columns
+// of psi/rho, so the column warps all do the same work between two barriers.
+__host__ __device__ constexpr int tiled_threads(int tx) { return tx + 32; }
 
 template <class T, int TX, bool SAMPLE>
 __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
@@ -106,15 +138,15 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
     C* rho_ring = psi_ring + 2 * SS;
     uint64_t* bars = reinterpret_cast<uint64_t*>(rho_ring + 2 * SS);
 
-    constexpr int NW = 2 * TX / 32;           // column warps
+    constexpr int NW = TX / 32;               // column warps (32 columns x 2 species each)
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     const bool svc = warp == NW;              // the service warp
     const bool producer = svc && lane == 0;   // issues the TMA copies
-    // column warps: lanes 0-15 species A, 16-31 species B of 16 columns;
+    // column warps: lanes 0-15 species A, 16-31 species B, columns c0 and c0+1;
     // service warp: lanes 0-3 species A, 4-7 species B of the halo columns
     const int sp = svc ? (lane >> 2) & 1 : lane >> 4;
-    const int c = svc ? 0 : warp * 16 + (lane & 15);  // column of this thread in the strip
+    const int c0 = svc ? 0 : warp * 32 + 2 * (lane & 15);
     if (t == 0) {
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
         fence_mbar_init();
@@ -128,7 +160,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
     uint32_t nrow = 0;  // global index of row 0 of the current item (rows consumed before it)
     bool aborted = false;
 
-    // Issue cursor (thread 0): the next row to load may belong to a later item
+    // Issue cursor (producer): the next row to load may belong to a later item
     // of this CTA, so the row pipeline does not drain between items.  Global
     // row n always lives in slot n % D with mbarrier phase (n / D) & 1.  The
     // geometry of the item being issued is cached (one division per item).
@@ -187,9 +219,9 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         C shift[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) shift[i] = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
-        // destination columns x-1, x, x+1 (periodic)
-        const int x = x0 + c;
-        const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p = x == g.nx - 1 ? 0 : x + 1;
+        // destination columns of the two sites x, x+1 shifted by -1/0/+1 (periodic)
+        const int x = x0 + c0;
+        const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p2 = x + 2 == g.nx ? 0 : x + 2;
         T* const dst_s = fout + (long long)cell * g.cellstride + (long long)sp * 9 * g.plane;
 
         __syncthreads();  // rings of the previous item are no longer read
@@ -200,29 +232,37 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             return mbar_wait_bounded(&bars[n % D], (n / D) & 1u);
         };
         // rho_s, psi_s of logical row k into ring row `ring_row` (own species,
-        // own column; the service warp takes the halo columns)
+        // own two columns; the service warp takes the halo columns)
         auto psi_stage = [&](int k, int ring_row) {
             const unsigned char* base = fring + ((nrow + (uint32_t)k) % D) * SLOT;
             const int ring = sp * SS + ring_row * W;
-            auto site = [&](const T* src, int stride, int col, int pos) {
-                C acc = C(0);
+            if (!svc) {
+                const T* src = reinterpret_cast<const T*>(base) + sp * 9 * TX + c0;
+                C r0 = C(0), r1 = C(0);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    const T v = src[(sp * 9 + i) * stride + col];
-                    acc += Store<T>::shifted ? to_c(v) + shift[i] : to_c(v);
+                    C a, b;
+                    Vec2<T>::ld(src + i * TX, a, b);
+                    r0 += Store<T>::shifted ? a + shift[i] : a;
+                    r1 += Store<T>::shifted ? b + shift[i] : b;
                 }
-                psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
-                rho_ring[ring + pos] = acc;
-            };
-            if (!svc) {
-                site(reinterpret_cast<const T*>(base), TX, c, c + 2);
+                Vec2<C>::st(psi_ring + ring + c0 + 2, psi_of<C>(r0, p.rho0, p.inv_rho0),
+                            psi_of<C>(r1, p.rho0, p.inv_rho0));
+                Vec2<C>::st(rho_ring + ring + c0 + 2, r0, r1);
             } else if (lane < 8) {
                 // halo column h: 0,1 -> columns -2,-1 (left box); 2,3 -> TX, TX+1 (right box)
                 const int h = lane & 3;
-                if (h < 2)
-                    site(reinterpret_cast<const T*>(base + MAIN_AL), H, H - 2 + h, h);
-                else
-                    site(reinterpret_cast<const T*>(base + MAIN_AL + HALO_AL), H, h - 2, TX + h);
+                const T* src = reinterpret_cast<const T*>(base + (h < 2 ? MAIN_AL : MAIN_AL + HALO_AL)) + sp * 9 * H +
+                               (h < 2 ? H - 2 + h : h - 2);
+                C acc = C(0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const C v = to_c(src[i * H]);
+                    acc += Store<T>::shifted ? v + shift[i] : v;
+                }
+                const int pos = h < 2 ? h : TX + h;
+                psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
+                rho_ring[ring + pos] = acc;
             }
         };
 
@@ -248,73 +288,100 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             // rows 0 .. j+1 of this item are done with their slots
             if (producer) issue_upto(nrow + (uint32_t)(j + 2 + D));
             if (svc) continue;
-            // ---- collide logical row k = j + 2 (lattice row y)
+            // ---- collide logical row k = j + 2 (lattice row y), sites x and x+1
             const int k = j + 2, y = y0 + j;
-            const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT);
-            C f[9];
+            const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT) + sp * 9 * TX + c0;
+            C f[2][9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const T v = fm[(sp * 9 + i) * TX + c];
-                f[i] = Store<T>::shifted ? to_c(v) + shift[i] : to_c(v);
+                C a, b;
+                Vec2<T>::ld(fm + i * TX, a, b);
+                f[0][i] = Store<T>::shifted ? a + shift[i] : a;
+                f[1][i] = Store<T>::shifted ? b + shift[i] : b;
             }
-            const C* ps = psi_ring + sp * SS + c + 2;
-            const C* ro = rho_ring + (1 - sp) * SS + c + 2;
-            int rb[5];
+            // psi window rows k-2..k+2, columns c0-2..c0+3 (six, as three pairs);
+            // pair differences d_q = psi(r + c_q) - psi(r - c_q) of both sites
+            const C* ps = psi_ring + sp * SS + c0;  // ring column c0 + 2 + dx  <->  column c0 + dx
+            const C* ro = rho_ring + (1 - sp) * SS + c0;
+            C v[5][6];
 #pragma unroll
-            for (int d = 0; d < 5; ++d) rb[d] = rr[d] * W;
-            const C psi_s = ps[rb[2]];
-            const C rho_s = rho_ring[sp * SS + c + 2 + rb[2]];
-            const C rho_o = ro[rb[2]];
-            C dps[12], dro[4];
+            for (int d = 0; d < 5; ++d)
 #pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                const int dx = hs_dx(q), dy = hs_dy(q);
-                dps[q] = ps[rb[2 + dy] + dx] - ps[rb[2 - dy] - dx];
-                if (q < 4) dro[q] = ro[rb[2 + dy] + dx] - ro[rb[2 - dy] - dx];
+                for (int m = 0; m < 3; ++m) Vec2<C>::ld(ps + rr[d] * W + 2 * m, v[d][2 * m], v[d][2 * m + 1]);
+            C e[3][6];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) Vec2<C>::ld(ro + rr[d + 1] * W + 2 * m, e[d][2 * m], e[d][2 * m + 1]);
+            C rho_s[2];
+            Vec2<C>::ld(rho_ring + sp * SS + rr[2] * W + c0 + 2, rho_s[0], rho_s[1]);
+            // window column of site o, offset dx: o + 2 + dx
+            C jx[2], jy[2], fs[2][9];
+            C Fx[2], Fy[2];
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                C dps[12], dro[4];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    const int dx = hs_dx(q), dy = hs_dy(q);
+                    dps[q] = v[2 + dy][o + 2 + dx] - v[2 - dy][o + 2 - dx];
+                    if (q < 4) dro[q] = e[1 + dy][o + 2 + dx] - e[1 - dy][o + 2 - dx];
+                }
+                const Sums<C> sm = stencil_sums<C>(dps, dro);
+                const C jx_s = mom_x<C>(f[o]), jy_s = mom_y<C>(f[o]);
+                jx[o] = jx_s + __shfl_xor_sync(0xffffffffu, jx_s, 16);
+                jy[o] = jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16);
+                const C rho_t = rho_s[o] + e[1][o + 2];
+                const C inv_rho = fast_div<C>(C(1), rho_t);
+                collide_species<C>(f[o], rho_s[o], v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho, sm, ga, gr, p,
+                                   fs[o], &Fx[o], &Fy[o]);
             }
-            const Sums<C> sm = stencil_sums<C>(dps, dro);
-            // barycentric velocity: own species' momentum + the partner lane's
-            const C jx_s = mom_x<C>(f), jy_s = mom_y<C>(f);
-            const C jx = jx_s + __shfl_xor_sync(0xffffffffu, jx_s, 16);
-            const C jy = jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16);
-            const C rho_t = rho_s + rho_o;
-            const C inv_rho = fast_div<C>(C(1), rho_t);
-            C fs[9], Fx, Fy;
-            collide_species<C>(f, rho_s, psi_s, jx * inv_rho, jy * inv_rho, sm, ga, gr, p, fs, &Fx, &Fy);
 
             // push streaming; rows next to a Couette wall bounce back in place
             const bool wall_lo = bc == 1 && y == 0, wall_hi = bc == 1 && y == g.ny - 1;
-            const int row_m = (y == 0 ? g.ny - 1 : y - 1) * g.pitch;
-            const int row_0 = y * g.pitch;
-            const int row_p = (y == g.ny - 1 ? 0 : y + 1) * g.pitch;
             const int pl = (int)g.plane;  // < 2^31 / 18, checked on the host
-            const int col3[3] = {col_m, x, col_p};
-            const int row3[3] = {row_m, row_0, row_p};
+            const int row3[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.pitch, y * g.pitch,
+                                 (y == g.ny - 1 ? 0 : y + 1) * g.pitch};
+            const int colA[3] = {col_m, x, x + 1};   // site x,   shifts -1, 0, +1
+            const int colB[3] = {x, x + 1, col_p2};  // site x+1, shifts -1, 0, +1
             C dpx_site = C(0);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const int cy = q_cy(i);
+                const int cy = q_cy(i), cx = q_cx(i);
                 const bool into_wall = (cy < 0 && wall_lo) || (cy > 0 && wall_hi);
                 if (into_wall) {
-                    C dpx;
-                    const C back = bounce<C>(i, fs[i], rho_s, cy < 0 ? -p.u_wall : p.u_wall, &dpx);
-                    Store<T>::st(dst_s, q_opp(i) * pl + row_0 + x, back, shift[q_opp(i)]);
-                    dpx_site += dpx;
+                    C dpa, dpb;
+                    const C uw = cy < 0 ? -p.u_wall : p.u_wall;
+                    const C ba = bounce<C>(i, fs[0][i], rho_s[0], uw, &dpa);
+                    const C bb = bounce<C>(i, fs[1][i], rho_s[1], uw, &dpb);
+                    const C so = shift[q_opp(i)];
+                    Vec2<T>::st(dst_s + q_opp(i) * pl + row3[1] + x, Store<T>::shifted ? ba - so : ba,
+                                Store<T>::shifted ? bb - so : bb);
+                    dpx_site += dpa + dpb;
+                } else if (cx == 0) {
+                    Vec2<T>::st(dst_s + i * pl + row3[cy + 1] + x, Store<T>::shifted ? fs[0][i] - shift[i] : fs[0][i],
+                                Store<T>::shifted ? fs[1][i] - shift[i] : fs[1][i]);
                 } else {
-                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + col3[q_cx(i) + 1], fs[i], shift[i]);
+                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], shift[i]);
+                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], shift[i]);
                 }
             }
             if (SAMPLE) {
-                const C Fx_t = Fx + __shfl_xor_sync(0xffffffffu, Fx, 16);
-                const C up = sp == 0 ? (jx + C(0.5) * Fx_t) / rho_t : C(0);
-                if (!(rho_t > C(0)) || !isfinite(rho_s)) atomicOr(err, ERR_NONFINITE);
+                C up[2];
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const C Fx_t = Fx[o] + __shfl_xor_sync(0xffffffffu, Fx[o], 16);
+                    const C rho_t = rho_s[o] + e[1][o + 2];
+                    up[o] = sp == 0 ? (jx[o] + C(0.5) * Fx_t) / rho_t : C(0);
+                    if (!(rho_t > C(0)) || !isfinite(rho_s[o])) atomicOr(err, ERR_NONFINITE);
+                }
                 // lane sums carried as an unevaluated pair (error-free two-sum),
                 // then added in FP64: ~2^-48 relative, no FP64 pipe in the tree
-                const double usum = warp_sum_compensated(up);
+                const double usum = warp_sum_compensated2(up[0], up[1]);
                 double wsum = 0.0;
-                if (wall_lo || wall_hi) wsum = warp_sum_compensated((C)dpx_site);
+                if (wall_lo || wall_hi) wsum = warp_sum_compensated2(dpx_site, C(0));
                 if (lane == 0) {
-                    const int nbx = g.nx / 16, wg = (x0 >> 4) + warp;
+                    const int nbx = g.nx / 32, wg = (x0 >> 5) + warp;
                     prof_part[((long long)cell * nbx + wg) * g.ny + y] = usum;
                     if (wall_lo || wall_hi) wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = wsum;
                 }
@@ -389,7 +456,7 @@ bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
     return encode_fn() != nullptr;
 }
 
-int tiled_partials_nbx(const Geom& g, int) { return (g.nx + 15) / 16; }
+int tiled_partials_nbx(const Geom& g, int) { return (g.nx + 31) / 32; }
 
 template <class T, int TX, bool S>
 static const void* kernel_ptr()
