@@ -61,10 +61,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1004_5058_gb300.dist import rank_world
+    return rank_world()
 
 
 def workload_cells(nx, ny, n_cells, rank):
@@ -240,6 +238,7 @@ def run_ours(args):
     import __graft_entry__ as g
     g.build()
     from paper_1004_5058_gb300 import Lattice, hb_fit
+    from paper_1004_5058_gb300.dist import max_over_ranks
 
     nx, ny, n_cells, chunk = args.nx, args.ny, args.cells, args.chunk
     cells = workload_cells(nx, ny, n_cells, rank)
@@ -282,10 +281,7 @@ def run_ours(args):
     launches = lat.kernel_launches - launches0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device="cuda")  # the job takes as long as its slowest rank
     sites = nx * ny * n_cells
     value = sites * chunk * args.steps * world / (ms * 1e-3) / 1e6
     sigma, S, Sb = lat.shear_stress()
@@ -331,11 +327,7 @@ def run_ours(args):
         e2e_step()
     torch.cuda.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e_value = sites * chunk * e2e_steps * world / e2e_s / 1e6
     h2d = 4 * sites * 8
     d2h = n_cells * 8 * 2 + n_cells * 8 * 2 + n_cells * ny * 8 + n_cells * 8 * 2

@@ -7,8 +7,12 @@ flow_curve       many Couette cells (wall speeds x cross couplings G_AB) in one
                  batched, graph-captured launch per step; per G_AB the
                  Herschel-Bulkley fit sigma = sigma_Y + A S^beta; flow-curve
                  points per second.  With sequential=True the same cells run one
-                 after another with the generic kernel and no graphs, the plain
-                 single-cell baseline of the batched run.
+                 after another (no batching), the plain single-cell baseline of
+                 the batched run.
+surrogate        LB flow-curve points -> training of the BF16 surrogate ->
+                 held-out queries served with LB fallback: served fraction,
+                 stress error against the LB, and queries per second of the
+                 network vs. the LB.
 
 python -m paper_1004_5058_gb300.studies precision|flow_curve [--quick]
 """
@@ -82,12 +86,14 @@ def flow_curve(L: int = 512, steps: int = 100000, every: int = 20, n_speeds: int
             _, dt = _cuda_time(lambda: lat.step(steps).sync())
             sigma, S, Sb = lat.shear_stress()
     else:
+        # the same cells one at a time (no batching), each with its own tuned tile
         sig_l, S_l, Sb_l = [], [], []
-        kern = ("generic", 32, 8)
+        kern = None
         dt = 0.0
         for c, cell in enumerate(cells):
             with Lattice([cell], precision) as lat:
-                lat.set_kernel("generic")
+                lat.init_fields(ra[c:c + 1], rb[c:c + 1], ux[c:c + 1], uy[c:c + 1])
+                kern = lat.autotune()
                 lat.init_fields(ra[c:c + 1], rb[c:c + 1], ux[c:c + 1], uy[c:c + 1]).set_sampling(steps // 2, every)
                 _, t = _cuda_time(lambda: lat.step(steps).sync())
                 dt += t
@@ -110,14 +116,61 @@ def flow_curve(L: int = 512, steps: int = 100000, every: int = 20, n_speeds: int
     return out
 
 
+def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L: int = 64, steps: int = 20000,
+                    epochs: int = 300, batch: int = 256, lr: float = 2e-3, seed: int = 11):
+    """Train on n_train x n_speeds LB points, judge on n_test x n_speeds held-out points."""
+    import time as _t
+    import torch
+    from . import surrogate as S
+    speeds = I.log_spaced(2e-4, 2e-2, n_speeds)
+    t0 = _t.perf_counter()
+    x, sig, lab, _ = S.flow_curve_dataset(n_train, speeds, L_side=L, steps=steps, seed=seed)
+    t_data = _t.perf_counter() - t0
+    xt, st, lt, _ = S.flow_curve_dataset(n_test, speeds, L_side=L, steps=steps, seed=seed + 1000)
+    t0 = _t.perf_counter()
+    sg, hist = S.train(x, sig, lab, epochs=epochs, batch=batch, lr=lr, logit_margin=0.5)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t0
+    inside = np.all(np.abs(xt - sg.box.center) <= sg.box.half_range, axis=1)
+    q, qs, ql = xt[inside], st[inside], lt[inside]
+    X = torch.tensor(q, dtype=torch.float32, device="cuda")
+    sg.serve(X)
+    torch.cuda.synchronize()
+    reps = 50
+    t0 = _t.perf_counter()
+    for _ in range(reps):
+        stress, logit, fb = sg.serve(X)
+    torch.cuda.synchronize()
+    t_serve = (_t.perf_counter() - t0) / reps
+    stress, logit, fb = stress.cpu().numpy(), logit.cpu().numpy(), fb.cpu().numpy().astype(bool)
+    served = ~fb
+    err = np.abs(stress - qs)
+    scale = float(np.max(np.abs(st)))
+    # the method without the network: one LB cell run per point, batched (data generation rate)
+    return {"train_points": int(len(x)), "test_points": int(len(q)), "cell": L, "steps": steps,
+            "data_seconds": t_data, "lb_points_per_s": len(x) / t_data, "train_seconds": t_train,
+            "loss_first": hist[0], "loss_last": hist[-1], "served_fraction": float(served.mean()),
+            "stress_scale": scale, "median_abs_err_served": float(np.median(err[served])) if served.any() else None,
+            "p90_abs_err_served": float(np.quantile(err[served], 0.9)) if served.any() else None,
+            "median_rel_err_served": float(np.median(err[served]) / scale) if served.any() else None,
+            "yield_agreement_served": float(np.mean((logit[served] > 0) == (ql[served] > 0.5))) if served.any() else None,
+            "network_queries_per_s": len(q) / t_serve, "network_seconds_per_batch": t_serve,
+            "gain_queries_per_s": (len(q) / t_serve) / (len(x) / t_data)}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "flow_curve", "flow_curve_sequential"])
+    ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
+                                      "surrogate"])
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
     if a.study == "precision":
         r = precision_study(n=512, steps=2000) if a.quick else precision_study()
+    elif a.study == "precision_mixed":  # the paper's footnote G_AB = 0.045: the mixture stays mixed
+        r = precision_study(n=512, steps=2000, g_ab=0.045) if a.quick else precision_study(g_ab=0.045)
+    elif a.study == "surrogate":
+        r = surrogate_study(n_train=48, n_test=12, n_speeds=8, L=32, steps=3000) if a.quick else surrogate_study()
     else:
         kw = dict(L=128, steps=2000, n_speeds=4) if a.quick else {}
         r = flow_curve(sequential=a.study.endswith("sequential"), **kw)

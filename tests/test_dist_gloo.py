@@ -1,0 +1,79 @@
+"""Multi-rank host logic on CPU (gloo, world size 2): cells sharded across
+ranks with no data exchange, per-cell results gathered, the job time taken as
+the maximum over ranks.  Each rank runs its own cells through the oracle (no
+GPU here); the gathered flow-curve points must equal a single-process run
+bit for bit, since cells are independent."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1004_5058_gb300 import dist as D
+from paper_1004_5058_gb300 import inputs as I
+
+
+def cells_and_fields():
+    cells = [I.make_cell("paper", nx=16, ny=12, g_ab=0.405, bc=1, u_wall=u) for u in (2e-3, 5e-3, 1e-2, 2e-2, 3e-2)]
+    ra, rb = I.random_fields(16, 12, n_cells=len(cells), seed=77)
+    ux, uy = I.couette_velocity(16, 12, [c.u_wall for c in cells], n_cells=len(cells))
+    return cells, ra, rb, ux, uy
+
+
+def run_cells(idx):
+    from oracle import lb as orc
+    cells, ra, rb, ux, uy = cells_and_fields()
+    out = []
+    for c in idx:
+        r = orc.Run(cells[c], ra[c], rb[c], ux[c], uy[c], threads=1)
+        r.set_sampling(10, 2)
+        r.step(30)
+        s, S, Sb, _ = r.shear()
+        out.append([s, S, Sb])
+    return np.array(out).reshape(-1, 3)
+
+
+def _worker(rank, world, port, outdir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    n = len(cells_and_fields()[0])
+    mine = D.shard(n, rank, world)
+    local = run_cells(list(mine))
+    allrows = D.gather_rows(local, n)
+    tmax = D.max_over_ranks(1.5 + rank)
+    np.save(os.path.join(outdir, "rows_%d.npy" % rank), allrows)
+    np.save(os.path.join(outdir, "tmax_%d.npy" % rank), np.array([tmax, len(mine)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_shard_covers_once():
+    for n in (0, 1, 5, 8, 64, 65):
+        for w in (1, 2, 3, 8):
+            got = [i for r in range(w) for i in D.shard(n, r, w)]
+            assert got == list(range(n))
+            sizes = [len(D.shard(n, r, w)) for r in range(w)]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        D.shard(4, 2, 2)
+
+
+def test_two_ranks_gloo(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_worker, args=(world, free_port(), str(tmp_path)), nprocs=world, join=True)
+    ref = run_cells(range(len(cells_and_fields()[0])))
+    for r in range(world):
+        rows = np.load(tmp_path / ("rows_%d.npy" % r))
+        assert np.array_equal(rows, ref)  # independent cells: bitwise equal
+        tmax, n_local = np.load(tmp_path / ("tmax_%d.npy" % r))
+        assert tmax == 2.5
+    assert D.job_rate([3, 2], 2.5) == 2.0
