@@ -36,7 +36,11 @@
  *    term, walls at y=-1/2 (x-velocity -U) and y=ny-1/2 (+U); the interaction
  *    stencil sees mirror ghosts psi(x,-k) = psi(x,k-1), rho likewise;
  *  - sampled observables: physical velocity (j + F/2)/rho, wall x-momentum
- *    delivered by bounce-back per step (Pi_top, Pi_bot).
+ *    delivered by bounce-back per step (Pi_top, Pi_bot);
+ *  - the Kolmogorov forcing of section "Numerical Results", F_x(y) = F0 sin(k_f y),
+ *    k_f = 2 pi / L, is a force density shared by the species in proportion to
+ *    their density (F_s gains (rho_s / rho) F_x), so it shifts both species'
+ *    equilibrium velocities by tau F_x / rho.
  *
  * Layout of a population array: [species s=0(A),1(B)][i=0..8][y][x], x fastest.
  * D2Q9 order: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
@@ -58,7 +62,8 @@ typedef struct {
     double tau, rho0;
     double g_aa1, g_aa2, g_bb1, g_bb2, g_ab;
     double u_wall;
-    int bc; /* 0: periodic in x and y; 1: Couette (periodic x, walls in y) */
+    double f0;  /* Kolmogorov body force F_x(y) = f0 sin(2 pi y / ny) */
+    int bc;     /* 0: periodic in x and y; 1: Couette (periodic x, walls in y) */
 } orc_params;
 
 /* Per-step observables of one sampled step (all FP64). */
@@ -305,6 +310,8 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
             double rtot = rho[k] + rho[n + k];
             double u[2] = {jj[k] / rtot, jj[n + k] / rtot};
             double Ftot[2] = {0.0, 0.0};
+            const double pi = 3.14159265358979323846;
+            const double fx_body = p->f0 == 0.0 ? 0.0 : p->f0 * sin(2.0 * pi * y / p->ny);
             for (int s = 0; s < 2; ++s) {
                 double S1[2], S2[2], X[2], ga, gr;
                 stencil_sums(p, psi + s * n, rho + (1 - s) * n, x, y, S1, S2, X);
@@ -316,8 +323,9 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
                     /* F_s and the shift tau F_s / rho_s, without dividing by rho_s */
                     double G = ga * S1[a] + gr * S2[a];
                     double F = -psi[s * n + k] * G - (p->g_ab / rho0) * rs * X[a];
-                    Ftot[a] += F;
-                    us[a] = u[a] - tau * (por * G + (p->g_ab / rho0) * X[a]);
+                    double body = a == 0 ? fx_body : 0.0;  /* F_x shared as rho_s / rho */
+                    Ftot[a] += F + (rs / rtot) * body;
+                    us[a] = u[a] - tau * (por * G + (p->g_ab / rho0) * X[a]) + tau * body / rtot;
                 }
                 double usq = us[0] * us[0] + us[1] * us[1];
                 for (int i = 0; i < 9; ++i) {

@@ -358,3 +358,43 @@ def test_hb_oracle_misfit_has_single_minimum():
     k = int(np.argmin(r))
     assert abs(bs[k] - 0.25) <= 0.03
     assert np.all(np.diff(r[: k + 1]) <= 1e-30) and np.all(np.diff(r[k:]) >= -1e-30)
+
+
+# ------------------------------------------------------- Kolmogorov forcing --
+def test_kolmogorov_tau1_exact_discrete_steady_state():
+    """Body force F_x(y) = F0 sin(k y) (section "Numerical Results") at G = 0,
+    tau = 1: post-collision populations are f^eq(rho, u + F/rho), so the steady
+    line profile of u = j/rho is A sin(k y) with A = 3 lam Phi / (1 - cos k),
+    lam = (2 + cos k)/3, Phi = F0/rho -- the discrete counterpart of
+    F0 / (rho nu k^2), nu = 1/6."""
+    ny, F0 = 32, 1e-6
+    k = 2 * math.pi / ny
+    c = I.make_cell("ideal", nx=4, ny=ny, tau=1.0, f0=F0)
+    r = lb.Run(c, np.full((ny, 4), 0.6), np.full((ny, 4), 0.6))
+    r.step(4000)
+    _, _, u, _ = r.fields()
+    y = np.arange(ny)
+    amp = 2.0 / ny * np.sum(u.mean(axis=1) * np.sin(k * y))
+    lam = (2 + math.cos(k)) / 3
+    phi = F0 / 1.2
+    assert amp == pytest.approx(3 * lam * phi / (1 - math.cos(k)), rel=1e-6)
+    # the profile is a pure sine (no other harmonics)
+    np.testing.assert_allclose(u.mean(axis=1), amp * np.sin(k * y), rtol=0, atol=1e-6 * abs(amp))
+    # the forcing injects momentum F0 sum sin = 0 per step: total momentum stays 0
+    assert abs(r.last["mom"][0]) < 1e-15 * ny * 4
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.4])
+def test_kolmogorov_laminar_amplitude(tau):
+    """Peak speed of the laminar Kolmogorov flow u0 = F0 / (rho nu k^2), up to O(k^2)."""
+    ny = 64
+    k = 2 * math.pi / ny
+    F0 = I.kolmogorov_f0(1e-3, ny, rho=1.2, tau=tau)
+    c = I.make_cell("ideal", nx=4, ny=ny, tau=tau, f0=F0)
+    r = lb.Run(c, np.full((ny, 4), 0.6), np.full((ny, 4), 0.6))
+    r.set_sampling(int(40 * ny * ny / ((tau - 0.5) / 3) / (4 * math.pi ** 2)), 10)
+    r.step(int(50 * ny * ny / ((tau - 0.5) / 3) / (4 * math.pi ** 2)))
+    _, _, _, ub = r.shear()  # time-averaged physical velocity (j + F/2)/rho
+    y = np.arange(ny)
+    amp = 2.0 / ny * np.sum(ub * np.sin(k * y))
+    assert amp == pytest.approx(1e-3, rel=2e-2)
