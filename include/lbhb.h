@@ -69,6 +69,9 @@ typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_GENERIC = 1, LB_KERNEL_TILED = 2 } 
  *   g_aa2, g_bb2  G^r_AA, G^r_BB: two-belt self couplings (positive repels)
  *   g_ab     G_AB = G_BA: belt-1 cross-species coupling
  *   u_wall   Couette wall speed U (bottom wall -U, top wall +U); ignored if periodic
+ *   f0       amplitude of the Kolmogorov body force F_x(y) = f0 sin(2 pi y / ny) of
+ *            section "Numerical Results" (force density; each species receives
+ *            rho_s / rho of it); 0 for none
  *   rho_bar_a, rho_bar_b  shift reference of LB_FP16_SHIFTED storage
  *   bc       lb_bc */
 typedef struct {
@@ -76,6 +79,7 @@ typedef struct {
     double tau, rho0;
     double g_aa1, g_aa2, g_bb1, g_bb2, g_ab;
     double u_wall;
+    double f0;
     double rho_bar_a, rho_bar_b;
     int bc;
 } lb_cell_params;

@@ -127,6 +127,8 @@ static void fill(ParamSet<C>& d, const lb_cell_params& c)
     d.g2[0] = C(c.g_aa2);
     d.g2[1] = C(c.g_bb2);
     d.u_wall = C(c.u_wall);
+    d.f0 = C(c.f0);
+    d.two_over_ny = C(2.0 / c.ny);
     d.rho_bar[0] = C(c.rho_bar_a);
     d.rho_bar[1] = C(c.rho_bar_b);
 }
@@ -254,7 +256,7 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
             return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d rho0=%g must be positive", c, p.rho0);
         if (p.bc != LB_BC_PERIODIC && p.bc != LB_BC_COUETTE)
             return fail(nullptr, LB_ERR_INVALID, "lb_create: unknown boundary %d", p.bc);
-        const double v[] = {p.g_aa1, p.g_aa2, p.g_bb1, p.g_bb2, p.g_ab, p.u_wall, p.rho_bar_a, p.rho_bar_b};
+        const double v[] = {p.g_aa1, p.g_aa2, p.g_bb1, p.g_bb2, p.g_ab, p.u_wall, p.f0, p.rho_bar_a, p.rho_bar_b};
         for (double x : v)
             if (!std::isfinite(x)) return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d has a non-finite parameter", c);
     }

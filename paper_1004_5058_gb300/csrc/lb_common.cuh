@@ -52,6 +52,8 @@ template <class C> struct ParamSet {
     C g1[2], g2[2];  // G^a_ss, G^r_ss for s = A, B
     C u_wall;        // top wall +u_wall, bottom wall -u_wall (Couette)
     C rho_bar[2];    // FP16 shift reference
+    C f0;            // Kolmogorov body force F_x(y) = f0 sin(pi y two_over_ny)
+    C two_over_ny;
 };
 struct CellDev {
     ParamSet<double> d;
@@ -110,6 +112,17 @@ template <class C> __device__ inline C fast_div(C a, C b);
 template <> __device__ inline float fast_div<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ inline double fast_div<double>(double a, double b) { return a / b; }
 
+// sin(pi x): the Kolmogorov profile sin(2 pi y / ny) is sin_pi(y * 2/ny).
+template <class C> __device__ inline C sin_pi(C x);
+template <> __device__ inline float sin_pi<float>(float x) { return sinpif(x); }
+template <> __device__ inline double sin_pi<double>(double x) { return sinpi(x); }
+
+// Body force density F_x of row y (zero when f0 = 0).
+template <class C> __device__ inline C body_force_x(const ParamSet<C>& p, int y)
+{
+    return p.f0 == C(0) ? C(0) : p.f0 * sin_pi<C>(C(y) * p.two_over_ny);
+}
+
 template <class C> __device__ inline C expm1_c(C x);
 template <> __device__ inline float expm1_c<float>(float x) { return expm1f(x); }
 template <> __device__ inline double expm1_c<double>(double x) { return expm1(x); }
@@ -156,21 +169,24 @@ __device__ inline Sums<C> stencil_sums(const C d[12], const C e[4])
 // f^eq_i = w_i rho_s (1 + 3 c_i.u_s + 4.5 (c_i.u_s)^2 - 1.5 u_s^2) is evaluated for
 // the pairs +-c_i together (even part + odd part).
 // u is the barycentric velocity j / (rho_A + rho_B) of both species.
+// ax = F_x / rho is the Kolmogorov body force per unit total density: species s
+// receives rho_s ax of it (a share proportional to its density), which shifts
+// its equilibrium velocity by tau ax.
 // psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
 // vanishing species density.  Closing the rest population on rho_s keeps the
 // rounded weights (sum of float(w_i) = 1 + 7.5e-9) from biasing the mass.
 // *Fx, *Fy receive F_s (for the force-corrected velocity of the observables).
 template <class C>
-__device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C uy, const Sums<C>& sm, C ga, C gr,
-                                       const ParamSet<C>& p, C fs[9], C* Fx, C* Fy)
+__device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C uy, C ax, const Sums<C>& sm, C ga,
+                                       C gr, const ParamSet<C>& p, C fs[9], C* Fx, C* Fy)
 {
     const C tau = p.tau, omega = p.omega, gx = p.gab_over_rho0;
     const C Gx = ga * sm.s1x + gr * sm.s2x;
     const C Gy = ga * sm.s1y + gr * sm.s2y;
-    *Fx = -psi_s * Gx - gx * rho_s * sm.xx;
+    *Fx = -psi_s * Gx - gx * rho_s * sm.xx + rho_s * ax;
     *Fy = -psi_s * Gy - gx * rho_s * sm.xy;
     const C por = rho_s != C(0) ? fast_div<C>(psi_s, rho_s) : C(1);
-    const C usx = ux - tau * (por * Gx + gx * sm.xx);
+    const C usx = ux - tau * (por * Gx + gx * sm.xx) + tau * ax;
     const C usy = uy - tau * (por * Gy + gx * sm.xy);
     // f^eq of a pair +-c: w rho (1 - 1.5 u^2 + 4.5 (c.u)^2) +- 3 w rho (c.u)
     const C base = C(1) - C(1.5) * (usx * usx + usy * usy);
@@ -206,16 +222,18 @@ template <class C> struct Collided {
 // Both species at one site: u = j / (rho_A + rho_B), then collide_species each.
 template <class C>
 __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi[2],
-                                    const Sums<C> sm[2], const ParamSet<C>& p, Collided<C>& out)
+                                    const Sums<C> sm[2], const ParamSet<C>& p, C fx_body, Collided<C>& out)
 {
     const C jx = mom_x<C>(f[0]) + mom_x<C>(f[1]);
     const C jy = mom_y<C>(f[0]) + mom_y<C>(f[1]);
     const C inv_rho = fast_div<C>(C(1), rho[0] + rho[1]);
     const C ux = jx * inv_rho, uy = jy * inv_rho;
+    const C ax = fx_body * inv_rho;
     C Fx[2], Fy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
-        collide_species<C>(f[s], rho[s], psi[s], ux, uy, sm[s], p.g1[s], p.g2[s], p, out.fs[s], &Fx[s], &Fy[s]);
+        collide_species<C>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p, out.fs[s], &Fx[s],
+                           &Fy[s]);
     out.Fx = Fx[0] + Fx[1];
     out.Fy = Fy[0] + Fy[1];
 }

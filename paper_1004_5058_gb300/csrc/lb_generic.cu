@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
             sm[s] = stencil_sums<C>(dpsi, drho);
         }
         Collided<C> c;
-        collide_site<C>(f, rho, psi, sm, p, c);
+        collide_site<C>(f, rho, psi, sm, p, body_force_x<C>(p, y), c);
 
         const C u_top = p.u_wall, u_bot = -p.u_wall;
 #pragma unroll

@@ -214,6 +214,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         p.inv_rho0 = pg.inv_rho0;
         p.gab_over_rho0 = pg.gab_over_rho0;
         p.u_wall = pg.u_wall;
+        p.f0 = pg.f0;
+        p.two_over_ny = pg.two_over_ny;
         const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
         C shift[9];
@@ -318,6 +320,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             // window column of site o, offset dx: o + 2 + dx
             C jx[2], jy[2], fs[2][9];
             C Fx[2], Fy[2];
+            const C fx_body = body_force_x<C>(p, y);
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
                 C dps[12], dro[4];
@@ -333,8 +336,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 jy[o] = jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16);
                 const C rho_t = rho_s[o] + e[1][o + 2];
                 const C inv_rho = fast_div<C>(C(1), rho_t);
-                collide_species<C>(f[o], rho_s[o], v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho, sm, ga, gr, p,
-                                   fs[o], &Fx[o], &Fy[o]);
+                collide_species<C>(f[o], rho_s[o], v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho, fx_body * inv_rho,
+                                   sm, ga, gr, p, fs[o], &Fx[o], &Fy[o]);
             }
 
             // push streaming; rows next to a Couette wall bounce back in place

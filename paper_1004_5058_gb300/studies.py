@@ -9,6 +9,8 @@ flow_curve       many Couette cells (wall speeds x cross couplings G_AB) in one
                  points per second.  With sequential=True the same cells run one
                  after another (no batching), the plain single-cell baseline of
                  the batched run.
+kolmogorov       the paper's forced periodic flow: profiles, shear vs exact
+                 stress scatter, Herschel-Bulkley fit, response R.
 surrogate        LB flow-curve points -> training of the BF16 surrogate ->
                  held-out queries served with LB fallback: served fraction,
                  stress error against the LB, and queries per second of the
@@ -116,6 +118,46 @@ def flow_curve(L: int = 512, steps: int = 100000, every: int = 20, n_speeds: int
     return out
 
 
+def kolmogorov(L: int = 512, steps: int = 1000000, every: int = 100, rho0s=(0.83, 0.81),
+               u0s=(0.02, 0.04, 0.07, 0.1, 0.15, 0.2, 0.3, 0.4), g_ab: float = 0.405, precision: str = "fp32"):
+    """The paper's own workload (section "Numerical Results"): a fully periodic
+    L x L box, body force F_x(y) = F0 sin(k y), k = 2 pi / L, with F0 tuned so
+    that the laminar flow would peak at U0 (F0 = rho nu k^2 U0), the paper's
+    sinusoidal initial densities, footnote couplings (G_AB read as 0.405).
+    Per cell: the time- and line-averaged profile U(y), the shear S(y) = dU/dy
+    (central difference), the exact stress sigma(y) = (F0/k) cos(k y) of the
+    momentum balance, the response R = U_hat / U0 with
+    U_hat = 2/L sum_y U(y) sin(k y), and the Herschel-Bulkley fit of the
+    (S, sigma) scatter where both are positive."""
+    k = 2.0 * np.pi / L
+    cells = []
+    for r0 in rho0s:
+        for u0 in u0s:
+            cells.append(I.make_cell("paper", nx=L, ny=L, rho0=r0, g_ab=g_ab, f0=I.kolmogorov_f0(u0, L)))
+    ra, rb = I.sine_fields(L, L, n_cells=len(cells))
+    with Lattice(cells, precision) as lat:
+        lat.init_fields(ra, rb)
+        kern = lat.autotune()
+        lat.init_fields(ra, rb).set_sampling(steps // 2, every)
+        _, dt = _cuda_time(lambda: lat.step(steps).sync())
+        ub, ns = lat.profile()
+    y = np.arange(L)
+    out = {"L": L, "steps": steps, "cells": len(cells), "kernel": kern, "seconds": dt,
+           "mlups": len(cells) * L * L * steps / dt / 1e6, "samples": ns, "runs": []}
+    for c, cell in enumerate(cells):
+        u0 = u0s[c % len(u0s)]
+        U = ub[c]
+        S = (np.roll(U, -1) - np.roll(U, 1)) / 2.0
+        sig = cell.f0 / k * np.cos(k * y)
+        R = 2.0 / L * np.sum(U * np.sin(k * y)) / u0
+        ok = (S > 0) & (sig > 0)
+        fit = hb_fit(S[ok], sig[ok]) if ok.sum() >= 3 else None
+        out["runs"].append({"rho0": cell.rho0, "u0": u0, "f0": cell.f0, "R": float(R),
+                            "u_max": float(np.max(np.abs(U))), "hb_fit": fit,
+                            "profile": [float(v) for v in U]})
+    return out
+
+
 def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L: int = 64, steps: int = 20000,
                     epochs: int = 300, batch: int = 256, lr: float = 2e-3, seed: int = 11):
     """Train on n_train x n_speeds LB points, judge on n_test x n_speeds held-out points."""
@@ -164,7 +206,7 @@ def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
-                                      "surrogate"])
+                                      "surrogate", "kolmogorov"])
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
@@ -172,6 +214,8 @@ def main():
         r = precision_study(n=512, steps=2000) if a.quick else precision_study()
     elif a.study == "precision_mixed":  # the paper's footnote G_AB = 0.045: the mixture stays mixed
         r = precision_study(n=512, steps=2000, g_ab=0.045) if a.quick else precision_study(g_ab=0.045)
+    elif a.study == "kolmogorov":
+        r = kolmogorov(L=128, steps=20000, u0s=(0.05, 0.1)) if a.quick else kolmogorov()
     elif a.study == "surrogate":
         r = surrogate_study(n_train=48, n_test=12, n_speeds=8, L=32, steps=3000) if a.quick else surrogate_study()
     else:

@@ -31,7 +31,7 @@ def test_null_and_invalid_arguments_rejected_before_device_work(lib):
     h = L._H()
     assert lib.lb_create(None, 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID
     assert not h.value
-    cell = L.lb_cell_params(64, 64, 0.5, 0.83, -9, 8.1, -8, 7.1, 0.045, 0, 0.6, 0.6, 0)
+    cell = L.lb_cell_params(64, 64, 0.5, 0.83, -9, 8.1, -8, 7.1, 0.045, 0, 0, 0.6, 0.6, 0)
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID  # tau = 1/2
     assert b"tau" in lib.lb_last_error(None)
     cell.tau, cell.nx = 1.0, 4
@@ -40,7 +40,7 @@ def test_null_and_invalid_arguments_rejected_before_device_work(lib):
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID
     cell.bc = 0
     assert lib.lb_create(C.byref(cell), 1, 9, None, C.byref(h)) == L.LB_ERR_INVALID  # precision
-    cells = (L.lb_cell_params * 2)(cell, L.lb_cell_params(32, 64, 1.0, 0.83, 0, 0, 0, 0, 0, 0, 0.6, 0.6, 0))
+    cells = (L.lb_cell_params * 2)(cell, L.lb_cell_params(32, 64, 1.0, 0.83, 0, 0, 0, 0, 0, 0, 0, 0.6, 0.6, 0))
     assert lib.lb_create(cells, 2, 0, None, C.byref(h)) == L.LB_ERR_INVALID  # mixed shapes
     assert lib.lb_create(C.byref(cell), 1, 0, None, None) == L.LB_ERR_INVALID
     # NULL handles

@@ -238,3 +238,44 @@ def test_autotune_keeps_state_and_caches(tmp_path):
     with Lattice([cell], "fp32") as lat2:
         lat2.init_fields(ra, rb)
         assert lat2.autotune(cache) == choice
+
+
+# ----------------------------------------------------- Kolmogorov forcing --
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 2e-15), ("fp32", 4e-7)])
+def test_one_step_kolmogorov_forcing(kernel, prec, tol):
+    from oracle import lb as orc
+    cell = I.make_cell("paper", nx=64, ny=64, g_ab=0.405, f0=I.kolmogorov_f0(0.05, 64))
+    r = evolved_state(cell, 300, seed=41)
+    f0 = r.f.copy()
+    with lattice([cell], prec, kernel) as lat:
+        lat.set_populations(f0[None])
+        start = lat.get_populations()[0]
+        lat.set_sampling(0, 1).step(1)
+        g1 = lat.get_populations()[0]
+        ub, ns = lat.profile()
+    f1, _, prof = orc.step(cell, start, want_profile=True)
+    assert max_abs(g1, f1) <= tol
+    np.testing.assert_allclose(ub[0], prof / cell.nx, rtol=0, atol=1e-14 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_kolmogorov_flow_paper_start(kernel, prec, tol):
+    """The paper's workload in small: fully periodic box, body force
+    F0 sin(2 pi y / L), the sinusoidal initial densities of the paper."""
+    L = 64
+    cell = I.make_cell("paper", nx=L, ny=L, f0=I.kolmogorov_f0(0.02, L))
+    ra, rb = I.sine_fields(L, L)
+    with lattice([cell], prec, kernel) as lat:
+        lat.init_fields(ra, rb).set_sampling(200, 5).step(500)
+        ga, gb, gu, _ = lat.fields()
+        ub, ns = lat.profile()
+        mass, mom = lat.reductions()
+    (r,) = oracle_runs([cell], ra, rb, steps=500, sampling=(200, 5))
+    oa, ob, ou, _ = r.fields()
+    _, _, _, oub = r.shear()
+    assert max_abs(ga[0], oa) <= tol and max_abs(gu[0], ou) <= tol
+    np.testing.assert_allclose(ub[0], oub, rtol=0, atol=tol)
+    # sin(k y) forcing injects no net momentum
+    assert abs(mom[0, 0]) <= (1e-12 if prec == "fp64" else 1e-4) * (ra.sum() + rb.sum())
