@@ -207,6 +207,45 @@ __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C u
     fs[0] = rho_s - moving;
 }
 
+// The same collision for shifted populations g_i = f_i - w_i rho_bar (FP16
+// storage), computed on g directly: with dr = rho_s - rho_bar,
+//   g^eq_i = f^eq_i - w_i rho_bar = w_i (dr + rho_s (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)),
+//   g*_i = g_i + omega (g^eq_i - g_i),  g*_0 = dr - sum_{i>=1} g*_i,
+// so no population needs its shift added or removed, and the arithmetic works
+// on the small deviations.  Momenta of g equal those of f (opposite directions
+// carry equal weights).
+template <class C>
+__device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar, C psi_s, C ux, C uy, C ax,
+                                               const Sums<C>& sm, C ga, C gr, const ParamSet<C>& p, C gs[9],
+                                               C* Fx, C* Fy)
+{
+    const C tau = p.tau, omega = p.omega, gx = p.gab_over_rho0;
+    const C Gx = ga * sm.s1x + gr * sm.s2x;
+    const C Gy = ga * sm.s1y + gr * sm.s2y;
+    *Fx = -psi_s * Gx - gx * rho_s * sm.xx + rho_s * ax;
+    *Fy = -psi_s * Gy - gx * rho_s * sm.xy;
+    const C por = rho_s != C(0) ? fast_div<C>(psi_s, rho_s) : C(1);
+    const C usx = ux - tau * (por * Gx + gx * sm.xx) + tau * ax;
+    const C usy = uy - tau * (por * Gy + gx * sm.xy);
+    const C dr = rho_s - rho_bar;
+    const C usq = C(1.5) * (usx * usx + usy * usy);
+    const C w1 = C(q_w(1)), w5 = C(q_w(5));
+    const C cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
+    const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
+    C moving = C(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const C w = k < 2 ? w1 : w5;
+        const C a = w * (dr + rho_s * (C(4.5) * cu[k] * cu[k] - usq));
+        const C b = (C(3) * w * rho_s) * cu[k];
+        const int i = lo[k], j = hi[k];
+        gs[i] = g[i] + omega * ((a + b) - g[i]);
+        gs[j] = g[j] + omega * ((a - b) - g[j]);
+        moving += gs[i] + gs[j];
+    }
+    gs[0] = dr - moving;
+}
+
 // Momentum of one species' populations, as differences of opposite directions
 // (a state at rest gives exactly zero).
 template <class C> __device__ inline C mom_x(const C f[9]) { return (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]); }

@@ -218,9 +218,6 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         p.two_over_ny = pg.two_over_ny;
         const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
-        C shift[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) shift[i] = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
         // destination columns of the two sites x, x+1 shifted by -1/0/+1 (periodic)
         const int x = x0 + c0;
         const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p2 = x + 2 == g.nx ? 0 : x + 2;
@@ -245,8 +242,12 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 for (int i = 0; i < 9; ++i) {
                     C a, b;
                     Vec2<T>::ld(src + i * TX, a, b);
-                    r0 += Store<T>::shifted ? a + shift[i] : a;
-                    r1 += Store<T>::shifted ? b + shift[i] : b;
+                    r0 += a;
+                    r1 += b;
+                }
+                if (Store<T>::shifted) {  // sum of the shifts w_i rho_bar is rho_bar
+                    r0 += rho_bar;
+                    r1 += rho_bar;
                 }
                 Vec2<C>::st(psi_ring + ring + c0 + 2, psi_of<C>(r0, p.rho0, p.inv_rho0),
                             psi_of<C>(r1, p.rho0, p.inv_rho0));
@@ -258,10 +259,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                                (h < 2 ? H - 2 + h : h - 2);
                 C acc = C(0);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const C v = to_c(src[i * H]);
-                    acc += Store<T>::shifted ? v + shift[i] : v;
-                }
+                for (int i = 0; i < 9; ++i) acc += to_c(src[i * H]);
+                if (Store<T>::shifted) acc += rho_bar;
                 const int pos = h < 2 ? h : TX + h;
                 psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
                 rho_ring[ring + pos] = acc;
@@ -293,14 +292,10 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             // ---- collide logical row k = j + 2 (lattice row y), sites x and x+1
             const int k = j + 2, y = y0 + j;
             const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT) + sp * 9 * TX + c0;
+            // populations as stored: f for FP32/FP64, the shifted g for FP16
             C f[2][9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                C a, b;
-                Vec2<T>::ld(fm + i * TX, a, b);
-                f[0][i] = Store<T>::shifted ? a + shift[i] : a;
-                f[1][i] = Store<T>::shifted ? b + shift[i] : b;
-            }
+            for (int i = 0; i < 9; ++i) Vec2<T>::ld(fm + i * TX, f[0][i], f[1][i]);
             // psi window rows k-2..k+2, columns c0-2..c0+3 (six, as three pairs);
             // pair differences d_q = psi(r + c_q) - psi(r - c_q) of both sites
             const C* ps = psi_ring + sp * SS + c0;  // ring column c0 + 2 + dx  <->  column c0 + dx
@@ -336,8 +331,12 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 jy[o] = jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16);
                 const C rho_t = rho_s[o] + e[1][o + 2];
                 const C inv_rho = fast_div<C>(C(1), rho_t);
-                collide_species<C>(f[o], rho_s[o], v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho, fx_body * inv_rho,
-                                   sm, ga, gr, p, fs[o], &Fx[o], &Fy[o]);
+                if (Store<T>::shifted)
+                    collide_species_shifted<C>(f[o], rho_s[o], rho_bar, v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho,
+                                               fx_body * inv_rho, sm, ga, gr, p, fs[o], &Fx[o], &Fy[o]);
+                else
+                    collide_species<C>(f[o], rho_s[o], v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho, fx_body * inv_rho,
+                                       sm, ga, gr, p, fs[o], &Fx[o], &Fy[o]);
             }
 
             // push streaming; rows next to a Couette wall bounce back in place
@@ -355,18 +354,19 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 if (into_wall) {
                     C dpa, dpb;
                     const C uw = cy < 0 ? -p.u_wall : p.u_wall;
-                    const C ba = bounce<C>(i, fs[0][i], rho_s[0], uw, &dpa);
-                    const C bb = bounce<C>(i, fs[1][i], rho_s[1], uw, &dpb);
-                    const C so = shift[q_opp(i)];
-                    Vec2<T>::st(dst_s + q_opp(i) * pl + row3[1] + x, Store<T>::shifted ? ba - so : ba,
-                                Store<T>::shifted ? bb - so : bb);
+                    // bounce in the f representation (for shifted storage the shift is
+                    // put back first; opposite directions carry equal weights, so the
+                    // same shift is removed again)
+                    const C sh = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
+                    const C ba = bounce<C>(i, fs[0][i] + sh, rho_s[0], uw, &dpa);
+                    const C bb = bounce<C>(i, fs[1][i] + sh, rho_s[1], uw, &dpb);
+                    Vec2<T>::st(dst_s + q_opp(i) * pl + row3[1] + x, ba - sh, bb - sh);
                     dpx_site += dpa + dpb;
                 } else if (cx == 0) {
-                    Vec2<T>::st(dst_s + i * pl + row3[cy + 1] + x, Store<T>::shifted ? fs[0][i] - shift[i] : fs[0][i],
-                                Store<T>::shifted ? fs[1][i] - shift[i] : fs[1][i]);
+                    Vec2<T>::st(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i]);
                 } else {
-                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], shift[i]);
-                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], shift[i]);
+                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], C(0));
+                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], C(0));
                 }
             }
             if (SAMPLE) {

@@ -10,7 +10,8 @@ flow_curve       many Couette cells (wall speeds x cross couplings G_AB) in one
                  after another (no batching), the plain single-cell baseline of
                  the batched run.
 kolmogorov       the paper's forced periodic flow: profiles, shear vs exact
-                 stress scatter, Herschel-Bulkley fit, response R.
+                 stress scatter, Herschel-Bulkley fit, response R;
+                 kolmogorov_rho0: R against rho0 and its VFT fit.
 surrogate        LB flow-curve points -> training of the BF16 surrogate ->
                  held-out queries served with LB fallback: served fraction,
                  stress error against the LB, and queries per second of the
@@ -158,6 +159,46 @@ def kolmogorov(L: int = 512, steps: int = 1000000, every: int = 100, rho0s=(0.83
     return out
 
 
+def vft_fit(rho0, inv_r, rho_c_hi: float = 1.2):
+    """Vogel-Fulcher-Tammann law 1/R = A exp(B / (rho_c - rho0)) (the paper's fit of
+    the reciprocal response): for fixed rho_c, ln(1/R) is linear in (ln A, B);
+    rho_c > max(rho0) minimises the residual (scan + refinement)."""
+    x = np.asarray(rho0, dtype=np.float64)
+    yl = np.log(np.asarray(inv_r, dtype=np.float64))
+
+    def solve(rc):
+        X = np.stack([np.ones_like(x), 1.0 / (rc - x)], axis=1)
+        coef, *_ = np.linalg.lstsq(X, yl, rcond=None)
+        r = yl - X @ coef
+        return float(r @ r), coef
+
+    lo = x.max() + 1e-4
+    grid = np.linspace(lo, rho_c_hi, 4001)
+    vals = [solve(rc)[0] for rc in grid]
+    k = int(np.argmin(vals))
+    a, b = grid[max(k - 1, 0)], grid[min(k + 1, len(grid) - 1)]
+    for _ in range(100):  # golden section
+        c1, c2 = b - 0.618033988749895 * (b - a), a + 0.618033988749895 * (b - a)
+        if solve(c1)[0] < solve(c2)[0]:
+            b = c2
+        else:
+            a = c1
+    rc = 0.5 * (a + b)
+    rss, coef = solve(rc)
+    return {"A": float(np.exp(coef[0])), "B": float(coef[1]), "rho_c": float(rc), "rss": rss}
+
+
+def kolmogorov_rho0_sweep(L: int = 512, steps: int = 1000000, u0: float = 0.1,
+                          rho0s=(0.70, 0.74, 0.78, 0.81, 0.83, 0.85, 0.87, 0.89), g_ab: float = 0.405):
+    """Response R = U_hat / U0 against rho0 at fixed forcing (U0 = 0.1), and the
+    VFT fit of 1/R (the paper's arrest analysis)."""
+    out = kolmogorov(L=L, steps=steps, rho0s=rho0s, u0s=(u0,), g_ab=g_ab)
+    R = np.array([r["R"] for r in out["runs"]])
+    ok = R > 0
+    out["vft"] = vft_fit(np.array(rho0s)[ok], 1.0 / R[ok]) if ok.sum() >= 3 else None
+    return out
+
+
 def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L: int = 64, steps: int = 20000,
                     epochs: int = 300, batch: int = 256, lr: float = 2e-3, seed: int = 11):
     """Train on n_train x n_speeds LB points, judge on n_test x n_speeds held-out points."""
@@ -206,7 +247,7 @@ def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
-                                      "surrogate", "kolmogorov"])
+                                      "surrogate", "kolmogorov", "kolmogorov_rho0"])
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
@@ -216,6 +257,8 @@ def main():
         r = precision_study(n=512, steps=2000, g_ab=0.045) if a.quick else precision_study(g_ab=0.045)
     elif a.study == "kolmogorov":
         r = kolmogorov(L=128, steps=20000, u0s=(0.05, 0.1)) if a.quick else kolmogorov()
+    elif a.study == "kolmogorov_rho0":
+        r = kolmogorov_rho0_sweep(L=128, steps=20000) if a.quick else kolmogorov_rho0_sweep()
     elif a.study == "surrogate":
         r = surrogate_study(n_train=48, n_test=12, n_speeds=8, L=32, steps=3000) if a.quick else surrogate_study()
     else:

@@ -1,0 +1,124 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+uses (tiled kernel, persistent grid, CUDA-graph chunks):
+
+  * 8 Couette cells of 1024 x 1024 (the benchmark batch): sampled cells
+    compared with the oracle site by site after 1 and 10 steps; mass of every
+    cell after 100 steps;
+  * one 4096 x 4096 cell (the precision-study size) in FP32, FP16-shifted and
+    FP64: one step against the oracle;
+  * 64 cells of 512 x 512 (the batched flow-curve size): two sampled cells
+    against the oracle after 5 steps;
+  * properties at any size: G = 0 Couette from the linear profile stays linear.
+
+Tolerances as in test_gpu_parity.py (FP64 to round-off, FP32 a few ulp per
+step, FP16 one rounding of the shifted value)."""
+import numpy as np
+import pytest
+
+from paper_1004_5058_gb300 import inputs as I
+from tests._util import max_abs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def couette_batch(n_cells, L, seed=1004):
+    cells = [I.make_cell("paper", nx=L, ny=L, g_ab=0.405, bc=1, u_wall=u)
+             for u in I.log_spaced(1e-4, 1e-2, n_cells)]
+    ra, rb = I.random_fields(L, L, n_cells=n_cells, seed=seed)
+    ux, uy = I.couette_velocity(L, L, [c.u_wall for c in cells], n_cells=n_cells)
+    return cells, ra, rb, ux, uy
+
+
+def oracle_fields(cell, ra, rb, ux, uy, steps):
+    from oracle import lb as orc
+    r = orc.Run(cell, ra, rb, ux, uy).step(steps)
+    return r.fields()
+
+
+def test_bench_batch_8x1024():
+    from paper_1004_5058_gb300 import Lattice
+    cells, ra, rb, ux, uy = couette_batch(8, 1024)
+    with Lattice(cells, "fp32") as lat:
+        lat.init_fields(ra, rb, ux, uy).set_kernel("tiled", 128, 147)
+        assert lat.kernel() == ("tiled", 128, 147)
+        lat.step(1)
+        a1, b1, u1, _ = lat.fields()
+        lat.step(9)
+        a10, b10, u10, _ = lat.fields()
+        lat.step(90)
+        mass, _ = lat.reductions()
+    for c in (0, 7):
+        oa, ob, ou, _ = oracle_fields(cells[c], ra[c], rb[c], ux[c], uy[c], 1)
+        assert max_abs(a1[c], oa) <= 1e-6 and max_abs(b1[c], ob) <= 1e-6 and max_abs(u1[c], ou) <= 1e-6
+    oa, ob, ou, _ = oracle_fields(cells[3], ra[3], rb[3], ux[3], uy[3], 10)
+    assert max_abs(a10[3], oa) <= 3e-6 and max_abs(u10[3], ou) <= 3e-6
+    m0 = ra.reshape(8, -1).sum(axis=1)
+    assert np.all(np.abs(mass[:, 0] - m0) / m0 <= 1e-6)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp16", 5e-5), ("fp64", 1e-14)])
+def test_precision_study_cell_4096(prec, tol):
+    from paper_1004_5058_gb300 import Lattice
+    cells, ra, rb, ux, uy = couette_batch(1, 4096, seed=77)
+    cells[0].u_wall = 1e-3
+    ux, uy = I.couette_velocity(4096, 4096, 1e-3)
+    with Lattice(cells, prec) as lat:
+        lat.init_fields(ra, rb, ux, uy)
+        assert lat.kernel()[0] == "tiled"
+        lat.step(1)
+        a, b, u, v = lat.fields()
+    oa, ob, ou, ov = oracle_fields(cells[0], ra[0], rb[0], ux[0], uy[0], 1)
+    assert max_abs(a[0], oa) <= tol and max_abs(b[0], ob) <= tol
+    assert max_abs(u[0], ou) <= tol and max_abs(v[0], ov) <= tol
+
+
+def test_flow_curve_batch_64x512():
+    from paper_1004_5058_gb300 import Lattice
+    speeds = I.log_spaced(1e-5, 1e-2, 16)
+    cells = [I.make_cell("paper", nx=512, ny=512, g_ab=g, bc=1, u_wall=u)
+             for g in (0.3, 0.35, 0.405, 0.45) for u in speeds]
+    ra, rb = I.random_fields(512, 512, n_cells=64, seed=5)
+    ux, uy = I.couette_velocity(512, 512, [c.u_wall for c in cells], n_cells=64)
+    with Lattice(cells, "fp32") as lat:
+        lat.init_fields(ra, rb, ux, uy).step(5)
+        a, b, u, _ = lat.fields()
+    for c in (9, 50):
+        oa, ob, ou, _ = oracle_fields(cells[c], ra[c], rb[c], ux[c], uy[c], 5)
+        assert max_abs(a[c], oa) <= 2e-6 and max_abs(u[c], ou) <= 2e-6
+
+
+def test_g0_couette_stays_linear_at_1024():
+    """With no interactions the linear profile is the steady state of halfway
+    bounce-back (exactly), so the line profile stays linear at any size."""
+    from paper_1004_5058_gb300 import Lattice
+    L, U = 1024, 1e-3
+    cell = I.make_cell("ideal", nx=L, ny=L, bc=1, u_wall=U)
+    ux, uy = I.couette_velocity(L, L, U)
+    with Lattice([cell], "fp32") as lat:
+        lat.init_fields(np.full((L, L), 0.6), np.full((L, L), 0.6), ux, uy)
+        lat.set_sampling(0, 10).step(200)
+        ub, ns = lat.profile()
+        sigma, S, Sb = lat.shear_stress()
+    y = np.arange(L)
+    # FP32 rounding only: u = j/rho from differences of f ~ 0.3 (3e-8) -> 3e-5 U per site
+    np.testing.assert_allclose(ub[0], U * (2 * (y + 0.5) / L - 1), rtol=0, atol=1e-4 * U)
+    assert S[0] == pytest.approx(2 * U / L, rel=1e-4)
+
+
+def test_no_samples_and_zero_steps():
+    from paper_1004_5058_gb300 import Lattice
+    cells, ra, rb, ux, uy = couette_batch(2, 64)
+    with Lattice(cells, "fp32") as lat:
+        lat.init_fields(ra, rb, ux, uy).step(0)
+        sigma, S, Sb = lat.shear_stress()
+        assert np.all(np.isnan(sigma)) and np.all(np.isnan(S))
+        ub, ns = lat.profile()
+        assert ns == 0 and np.all(np.isnan(ub))
+        lat.set_sampling(5, 0).step(20)  # every = 0: sampling off
+        assert lat.profile()[1] == 0
