@@ -351,6 +351,9 @@ def run_ours(args):
                      "bytes_per_site_update": BYTES_PER_SITE[args.precision]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lattice_steps_per_step": chunk},
+        # one flow-curve point = one Couette cell run for 2e5 time steps (the protocol of this
+        # workload), at the measured site-update rate
+        "flow_curve_points_per_s": value * 1e6 / (nx * ny * 2e5),
         "gpu_launches": int(launches),
         "clocks": clk,
         "flow_curve": {"sigma_xy": [float(v) for v in sigma], "shear_rate": [float(v) for v in S]},
