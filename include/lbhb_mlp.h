@@ -71,9 +71,18 @@ lb_status mlp_gradients(mlp_handle* h, const float* x, const float* target_stres
 lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stress, const float* label,
                          int batch, float* loss_dev);
 
+/* Error budget of serving: bin_error (HOST, n_bins floats) is the stress error
+ * the network showed on held-out LB points in n_bins equal bins of log S over
+ * [log_s_lo, log_s_hi]; queries falling in a bin whose error exceeds `budget`
+ * are sent to the LB by mlp_serve.  n_bins = 0 removes the table.  At most 256
+ * bins.  Synchronous. */
+lb_status mlp_set_error_budget(mlp_handle* h, const float* bin_error, int n_bins, double log_s_lo,
+                               double log_s_hi, double budget);
+
 /* Serving: forward pass plus the fallback decision per query: fallback[b] = 1
- * if any input lies outside the training box center +- half_range, or if
- * |logit| < logit_margin (yielded/arrested undecided); 0 otherwise.  stress,
+ * if any input lies outside the training box center +- half_range, if
+ * |logit| < logit_margin (yielded/arrested undecided), or if the query's log S
+ * bin is above the error budget (mlp_set_error_budget); 0 otherwise.  stress,
  * logit: device [B]; fallback: device int [B].  Async. */
 lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit, int* fallback);
 

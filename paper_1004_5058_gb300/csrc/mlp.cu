@@ -300,9 +300,13 @@ __global__ void output_kernel(const float* __restrict__ out, int B, float scale,
     y[2 * b + 1] = out[(long long)b * NOUTP + 1];
 }
 
+constexpr int MAX_BINS = 256;
+
+// bins: per log S bin, 1 if the held-out error of that bin exceeds the budget.
 __global__ void serve_kernel(const float* __restrict__ x, const float* __restrict__ out, int B,
                              const float* __restrict__ center, const float* __restrict__ half, float scale,
-                             float margin, float* __restrict__ stress, float* __restrict__ logit,
+                             float margin, const int* __restrict__ over_budget, int n_bins, float ls_lo,
+                             float ls_hi, float* __restrict__ stress, float* __restrict__ logit,
                              int* __restrict__ fallback)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -312,10 +316,17 @@ __global__ void serve_kernel(const float* __restrict__ x, const float* __restric
         const float xv = x[b * NIN + c];
         outside |= !(fabsf(xv - center[c]) <= half[c]);  // NaN counts as outside
     }
+    bool budget = false;
+    if (n_bins > 0) {
+        const float ls = x[b * NIN];
+        int k = (int)floorf((ls - ls_lo) / (ls_hi - ls_lo) * n_bins);
+        k = k < 0 ? 0 : (k >= n_bins ? n_bins - 1 : k);
+        budget = over_budget[k] != 0;
+    }
     const float lg = out[(long long)b * NOUTP + 1];
     stress[b] = out[(long long)b * NOUTP] * scale;
     logit[b] = lg;
-    fallback[b] = (outside || !(fabsf(lg) >= margin)) ? 1 : 0;
+    fallback[b] = (outside || budget || !(fabsf(lg) >= margin)) ? 1 : 0;
 }
 
 }  // namespace
@@ -338,6 +349,9 @@ struct mlp_handle {
     double* loss_part = nullptr;
     double* loss_d = nullptr;
     float *center = nullptr, *half = nullptr;
+    int* over_budget = nullptr;  // [MAX_BINS]
+    int n_bins = 0;
+    float ls_lo = 0.f, ls_hi = 1.f;
     long long adam_t = 0;
     long long launches = 0;
     std::vector<void*> allocs;
@@ -514,6 +528,7 @@ lb_status mlp_create(const mlp_config* cfg, void* cuda_stream, mlp_handle** out)
     if (e == cudaSuccess) e = alloc(h, &h->loss_d, 1);
     if (e == cudaSuccess) e = alloc(h, &h->center, NIN);
     if (e == cudaSuccess) e = alloc(h, &h->half, NIN);
+    if (e == cudaSuccess) e = alloc(h, &h->over_budget, MAX_BINS);
     if (e == cudaSuccess) {
         float c[NIN], hr[NIN];
         for (int i = 0; i < NIN; ++i) {
@@ -609,13 +624,29 @@ lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, flo
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
     cudaError_t e = forward(h, x, batch);
     if (e == cudaSuccess) {
-        serve_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(x, h->OUT, batch, h->center, h->half,
-                                                                 (float)h->cfg.sigma_scale,
-                                                                 (float)h->cfg.logit_margin, stress, logit, fallback);
+        serve_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(
+            x, h->OUT, batch, h->center, h->half, (float)h->cfg.sigma_scale, (float)h->cfg.logit_margin,
+            h->over_budget, h->n_bins, h->ls_lo, h->ls_hi, stress, logit, fallback);
         h->launches++;
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
+
+lb_status mlp_set_error_budget(mlp_handle* h, const float* bin_error, int n_bins, double log_s_lo,
+                               double log_s_hi, double budget)
+{
+    if (!h || n_bins < 0 || n_bins > MAX_BINS || (n_bins > 0 && (!bin_error || !(log_s_hi > log_s_lo))))
+        return LB_ERR_INVALID;
+    int flags[MAX_BINS] = {0};
+    for (int k = 0; k < n_bins; ++k) flags[k] = !(bin_error[k] <= budget);  // NaN error is over budget
+    cudaError_t e = cudaMemcpyAsync(h->over_budget, flags, sizeof(int) * MAX_BINS, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return LB_ERR_CUDA;
+    h->n_bins = n_bins;
+    h->ls_lo = (float)log_s_lo;
+    h->ls_hi = (float)log_s_hi;
+    return LB_OK;
 }
 
 long long mlp_kernel_launches(const mlp_handle* h) { return h ? h->launches : 0; }

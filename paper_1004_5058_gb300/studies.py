@@ -214,6 +214,9 @@ def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L:
     sg, hist = S.train(x, sig, lab, epochs=epochs, batch=batch, lr=lr, logit_margin=0.5)
     torch.cuda.synchronize()
     t_train = _t.perf_counter() - t0
+    # error budget of serving: 10% of the largest training stress, per log S bin
+    budget = 0.1 * float(np.max(np.abs(sig)))
+    table = sg.calibrate_error_budget(x, sig, budget, n_bins=8)
     inside = np.all(np.abs(xt - sg.box.center) <= sg.box.half_range, axis=1)
     q, qs, ql = xt[inside], st[inside], lt[inside]
     X = torch.tensor(q, dtype=torch.float32, device="cuda")
@@ -236,6 +239,7 @@ def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L:
     return {"train_points": int(len(x)), "test_points": int(len(q)), "cell": L, "steps": steps,
             "data_seconds": t_data, "lb_points_per_s": len(x) / t_data, "train_seconds": t_train,
             "loss_first": hist[0], "loss_last": hist[-1], "served_fraction": float(served.mean()),
+            "error_budget": budget, "error_table_by_logS_bin": [float(v) for v in table],
             "stress_scale": scale, "median_abs_err_served": float(np.median(err[served])) if served.any() else None,
             "p90_abs_err_served": float(np.quantile(err[served], 0.9)) if served.any() else None,
             "median_rel_err_served": float(np.median(err[served]) / scale) if served.any() else None,

@@ -156,6 +156,28 @@ class Surrogate:
         L.check(self.lib.mlp_serve(self.h, self._ptr(x), B, self._ptr(stress), self._ptr(logit), self._ptr(fb)))
         return stress, logit, fb
 
+    def set_error_budget(self, bin_error, log_s_lo: float, log_s_hi: float, budget: float):
+        """Queries whose log S bin showed a held-out stress error above `budget`
+        are sent to the LB by serve()."""
+        e = np.ascontiguousarray(bin_error, dtype=np.float32)
+        L.check(self.lib.mlp_set_error_budget(self.h, e.ctypes.data_as(L._F), int(e.size), float(log_s_lo),
+                                              float(log_s_hi), float(budget)))
+        return self
+
+    def calibrate_error_budget(self, x_val, stress_val, budget: float, n_bins: int = 8):
+        """Per-bin median absolute stress error on held-out LB points (x_val,
+        stress_val), uploaded as the serving error budget; returns the table."""
+        import torch
+        X = torch.tensor(np.asarray(x_val), dtype=torch.float32, device="cuda")
+        pred = self.forward(X)[:, 0].cpu().numpy().astype(np.float64)
+        ls = np.asarray(x_val)[:, 0]
+        lo, hi = self.box.center[0] - self.box.half_range[0], self.box.center[0] + self.box.half_range[0]
+        k = np.clip(np.floor((ls - lo) / (hi - lo) * n_bins).astype(int), 0, n_bins - 1)
+        err = np.abs(pred - np.asarray(stress_val))
+        table = np.array([np.median(err[k == b]) if np.any(k == b) else np.nan for b in range(n_bins)])
+        self.set_error_budget(table, lo, hi, budget)
+        return table
+
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.mlp_kernel_launches(self.h))

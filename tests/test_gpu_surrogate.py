@@ -132,6 +132,32 @@ def test_serve_flags_fallbacks(env):
     sg.close()
 
 
+def test_serve_error_budget_bins(env):
+    """Queries whose log S bin showed a held-out error above the budget go to
+    the LB; the table is validated and can be removed again."""
+    torch, S = env
+    from paper_1004_5058_gb300 import _lib as L
+    box, x = box_and_inputs(S, B=200, seed=8)
+    sg = S.Surrogate(box, sigma_scale=1e-4, max_batch=200, logit_margin=0.5)
+    p = np.zeros(S.param_count(), dtype=np.float32)
+    p[-1] = 3.0
+    sg.set_params(p)
+    lo, hi = box.center[0] - box.half_range[0], box.center[0] + box.half_range[0]
+    table = np.array([1e-6, 5e-5, 1e-6, np.nan])  # bins 1 (error) and 3 (no data) over budget
+    sg.set_error_budget(table, lo, hi, budget=1e-5)
+    X = torch.tensor(x, dtype=torch.float32, device="cuda")
+    _, _, fb = sg.serve(X)
+    f32 = np.float32
+    k = np.clip(np.floor((x[:, 0].astype(f32) - f32(lo)) / (f32(hi) - f32(lo)) * f32(4)), 0, 3).astype(int)
+    np.testing.assert_array_equal(fb.cpu().numpy(), np.isin(k, (1, 3)).astype(np.int32))
+    sg.set_error_budget(np.zeros(0), lo, hi, budget=1e-5)
+    assert np.all(sg.serve(X)[2].cpu().numpy() == 0)
+    e = np.zeros(300, dtype=np.float32)
+    assert sg.lib.mlp_set_error_budget(sg.h, e.ctypes.data_as(L._F), 300, lo, hi, 1.0) == L.LB_ERR_INVALID
+    assert sg.lib.mlp_set_error_budget(sg.h, e.ctypes.data_as(L._F), 4, hi, lo, 1.0) == L.LB_ERR_INVALID
+    sg.close()
+
+
 def test_surrogate_gain_over_lb(env):
     """Train on LB flow-curve points, then answer held-out queries: the network
     serves most of them within the stated stress budget, far faster per query
@@ -145,13 +171,16 @@ def test_surrogate_gain_over_lb(env):
     sg, hist = S.train(x, sig, lab, epochs=300, batch=128, lr=2e-3, logit_margin=0.5)
     assert hist[-1] < 0.3 * hist[0]  # measured ~0.2 on these points
     inside = np.all(np.abs(xt - sg.box.center) <= sg.box.half_range, axis=1)
+    budget = 0.1 * np.max(np.abs(st_))
+    # error table from the training points (no held-out data is used for it)
+    table = sg.calibrate_error_budget(x, sig, budget, n_bins=4)
+    assert table.shape == (4,)
     res = S.serve_with_fallback(sg, xt[inside], L_side=L_side, steps=steps)
     served = ~res["fallback"]
     assert served.mean() > 0.5
     # stress budget: median error of served queries within 10% of the largest
     # held-out stress (measured ~5-7%); short 32x32 runs make the LB points noisy
     err = np.abs(res["stress"][served] - st_[inside][served])
-    budget = 0.1 * np.max(np.abs(st_))
     assert np.median(err) <= budget, (np.median(err), budget)
     # yielded/arrested decision of the served queries
     agree = (res["logit"][served] > 0) == (lt[inside][served] > 0.5)
