@@ -391,6 +391,176 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
     free(uphys);
 }
 
+/*
+ * The same time step for one horizontal slab of the cell, rows [y0, y0 + rows),
+ * as one rank of a decomposition of the cell over several hosts would take it.
+ * It restates orc_step site by site, so a decomposed run equals the whole-cell
+ * run bit for bit.
+ *
+ * Slab arrays hold rows + 4 rows, [s][i][e][x] with slab row e = global row
+ * y0 - 2 + e (taken mod ny for a periodic cell).
+ *   f_in:  rows y0 .. y0+rows-1 of the post-streaming state at t, and in the two
+ *          rows on each side copies of the neighbours' rows y0-2, y0-1 and
+ *          y0+rows, y0+rows+1 (at a Couette wall those rows are not read: the
+ *          interaction stencil mirrors into the cell).
+ *   f_out: the slab's rows of the state at t+1, except the populations that
+ *          stream in from the neighbours (c_y = +1 into the first row, c_y = -1
+ *          into the last), which it does not write; and in slab rows 1 and rows+2
+ *          the populations that stream out of the slab, for the neighbours.
+ * obs (nullable) receives the slab's share of the step's observables (its rows'
+ * sums; Pi of the walls it holds); profile (nullable, length rows) the row sums
+ * of u_phys_x of its rows.  Returns -1 if rows + 4 > ny for a periodic cell or
+ * the slab leaves the cell, else 0.
+ */
+#define SIDX(p, nr, s, i, x, e) ((((size_t)(s) * 9 + (size_t)(i)) * (size_t)(nr) + (size_t)(e)) * (size_t)(p)->nx + (size_t)(x))
+
+/* Slab row of the global row the interaction stencil sees at y. */
+static int slab_row(const orc_params* p, int y0, int y)
+{
+    int g = stencil_row(p, y);
+    return p->bc == 0 ? wrap(g - y0 + 2, p->ny) : g - y0 + 2;
+}
+
+int orc_step_slab(const orc_params* p, int y0, int rows, const double* f_in, double* f_out,
+                  orc_obs* obs, double* profile)
+{
+    const int nx = p->nx, ny = p->ny, nr = rows + 4;
+    if (rows < 1 || y0 < 0 || y0 + rows > ny || (p->bc == 0 && nr > ny)) return -1;
+    const size_t n = (size_t)nx * nr;
+    const double tau = p->tau, rho0 = p->rho0;
+    double* rho = (double*)calloc(2 * n, sizeof(double));
+    double* psi = (double*)calloc(2 * n, sizeof(double));
+    double* jj = (double*)calloc(2 * n, sizeof(double));
+    double* fst = (double*)calloc(18 * n, sizeof(double));
+    double* uphys = (double*)calloc(n, sizeof(double));
+
+    /* 1-2. moments and pseudopotential on every held row */
+    for (int e = 0; e < nr; ++e)
+        for (int x = 0; x < nx; ++x) {
+            size_t k = (size_t)e * nx + x;
+            double jx_s[2], jy_s[2];
+            for (int s = 0; s < 2; ++s) {
+                double r = 0.0;
+                for (int i = 0; i < 9; ++i) r += f_in[SIDX(p, nr, s, i, x, e)];
+                rho[s * n + k] = r;
+                double f1 = f_in[SIDX(p, nr, s, 1, x, e)], f2 = f_in[SIDX(p, nr, s, 2, x, e)];
+                double f3 = f_in[SIDX(p, nr, s, 3, x, e)], f4 = f_in[SIDX(p, nr, s, 4, x, e)];
+                double f5 = f_in[SIDX(p, nr, s, 5, x, e)], f6 = f_in[SIDX(p, nr, s, 6, x, e)];
+                double f7 = f_in[SIDX(p, nr, s, 7, x, e)], f8 = f_in[SIDX(p, nr, s, 8, x, e)];
+                jx_s[s] = (f1 - f3) + (f5 - f7) + (f8 - f6);
+                jy_s[s] = (f2 - f4) + (f5 - f7) + (f6 - f8);
+                psi[s * n + k] = psi_of(r, rho0);
+            }
+            jj[k] = jx_s[0] + jx_s[1];
+            jj[n + k] = jy_s[0] + jy_s[1];
+        }
+
+    /* 3-6. forces, shifted equilibrium and collision on the slab's own rows */
+    for (int yl = 0; yl < rows; ++yl)
+        for (int x = 0; x < nx; ++x) {
+            const int y = y0 + yl, e = yl + 2;
+            size_t k = (size_t)e * nx + x;
+            double rtot = rho[k] + rho[n + k];
+            double u[2] = {jj[k] / rtot, jj[n + k] / rtot};
+            double Ftot[2] = {0.0, 0.0};
+            const double pi = 3.14159265358979323846;
+            const double fx_body = p->f0 == 0.0 ? 0.0 : p->f0 * sin(2.0 * pi * y / p->ny);
+            for (int s = 0; s < 2; ++s) {
+                const double* ps = psi + s * n;
+                const double* ro = rho + (1 - s) * n;
+                double S1[2] = {0.0, 0.0}, S2[2] = {0.0, 0.0}, X[2] = {0.0, 0.0}, ga, gr;
+                for (int dy = 0; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        if (dy == 0 && dx <= 0) continue;
+                        int c2 = dx * dx + dy * dy;
+                        size_t kp = (size_t)slab_row(p, y0, y + dy) * nx + wrap(x + dx, nx);
+                        size_t km = (size_t)slab_row(p, y0, y - dy) * nx + wrap(x - dx, nx);
+                        double dpsi = ps[kp] - ps[km];
+                        double w1 = belt1_weight(c2), w2 = belt2_weight(c2);
+                        if (w1 != 0.0) {
+                            double drho = ro[kp] - ro[km];
+                            S1[0] += w1 * dx * dpsi;
+                            S1[1] += w1 * dy * dpsi;
+                            X[0] += w1 * dx * drho;
+                            X[1] += w1 * dy * drho;
+                        }
+                        S2[0] += w2 * dx * dpsi;
+                        S2[1] += w2 * dy * dpsi;
+                    }
+                coupling(p, s, &ga, &gr);
+                double rs = rho[s * n + k];
+                double por = psi_over_rho(rs, rho0);
+                double us[2];
+                for (int a = 0; a < 2; ++a) {
+                    double G = ga * S1[a] + gr * S2[a];
+                    double F = -psi[s * n + k] * G - (p->g_ab / rho0) * rs * X[a];
+                    double body = a == 0 ? fx_body : 0.0;
+                    Ftot[a] += F + (rs / rtot) * body;
+                    us[a] = u[a] - tau * (por * G + (p->g_ab / rho0) * X[a]) + tau * body / rtot;
+                }
+                double usq = us[0] * us[0] + us[1] * us[1];
+                for (int i = 0; i < 9; ++i) {
+                    double cu = CX[i] * us[0] + CY[i] * us[1];
+                    double feq = W[i] * rs * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                    double fi = f_in[SIDX(p, nr, s, i, x, e)];
+                    fst[SIDX(p, nr, s, i, x, e)] = fi - (fi - feq) / tau;
+                }
+            }
+            uphys[k] = (jj[k] + 0.5 * Ftot[0]) / rtot;
+        }
+
+    /* 7. streaming inside the slab and into slab rows 1 and rows+2; walls as in orc_step */
+    double pi_top = 0.0, pi_bot = 0.0;
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < 9; ++i)
+            for (int yl = 0; yl < rows; ++yl)
+                for (int x = 0; x < nx; ++x) {
+                    const int y = y0 + yl, e = yl + 2;
+                    double v = fst[SIDX(p, nr, s, i, x, e)];
+                    int yd = y + CY[i];
+                    if (p->bc == 1 && (yd < 0 || yd >= ny)) {
+                        double uw = yd < 0 ? -p->u_wall : p->u_wall;
+                        double rs = rho[s * n + (size_t)e * nx + x];
+                        double back = v - 2.0 * W[i] * rs * (CX[i] * uw) * 3.0;
+                        f_out[SIDX(p, nr, s, OPP[i], x, e)] = back;
+                        double dpx = (double)CX[OPP[i]] * back - (double)CX[i] * v;
+                        if (yd < 0) pi_bot += dpx; else pi_top += dpx;
+                    } else {
+                        f_out[SIDX(p, nr, s, i, wrap(x + CX[i], nx), e + CY[i])] = v;
+                    }
+                }
+
+    if (obs) {
+        double m[2] = {0.0, 0.0}, mo[2] = {0.0, 0.0};
+        for (int e = 2; e < rows + 2; ++e)
+            for (int x = 0; x < nx; ++x) {
+                size_t k = (size_t)e * nx + x;
+                m[0] += rho[k];
+                m[1] += rho[n + k];
+                mo[0] += jj[k];
+                mo[1] += jj[n + k];
+            }
+        obs->mass[0] = m[0];
+        obs->mass[1] = m[1];
+        obs->mom[0] = mo[0];
+        obs->mom[1] = mo[1];
+        obs->pi_top = pi_top;
+        obs->pi_bot = pi_bot;
+    }
+    if (profile)
+        for (int yl = 0; yl < rows; ++yl) {
+            double acc = 0.0;
+            for (int x = 0; x < nx; ++x) acc += uphys[(size_t)(yl + 2) * nx + x];
+            profile[yl] = acc;
+        }
+    free(rho);
+    free(psi);
+    free(jj);
+    free(fst);
+    free(uphys);
+    return 0;
+}
+
 /* Time averages collected over sampled steps. */
 typedef struct {
     double sum_pi_top, sum_pi_bot;

@@ -77,3 +77,58 @@ def test_two_ranks_gloo(tmp_path):
         tmax, n_local = np.load(tmp_path / ("tmax_%d.npy" % r))
         assert tmax == 2.5
     assert D.job_rate([3, 2], 2.5) == 2.0
+
+
+# ---- one cell split into slabs over gloo ranks ------------------------------
+def _slab_worker(rank, world, port, outdir, bc):
+    import torch
+    import torch.distributed as dist
+    from oracle import slab
+    from tests.test_oracle_slab import case
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    cell, f = case(bc)
+    y0, rows = slab.split_rows(cell.ny, world)[rank]
+    below, above = slab.neighbours(cell, rank, world)
+    mine = slab.scatter(f, y0, rows)
+
+    def trade(to_below, to_above):
+        """Send to the neighbours, receive from them; tag 1 travels down, tag 2 up."""
+        reqs, got = [], [None, None]
+        if below is not None:
+            reqs.append(dist.isend(torch.from_numpy(to_below), below, tag=1))
+            got[0] = torch.empty(to_above.shape, dtype=torch.float64)
+            reqs.append(dist.irecv(got[0], below, tag=2))
+        if above is not None:
+            reqs.append(dist.isend(torch.from_numpy(to_above), above, tag=2))
+            got[1] = torch.empty(to_below.shape, dtype=torch.float64)
+            reqs.append(dist.irecv(got[1], above, tag=1))
+        for q in reqs:
+            q.wait()
+        return [None if g is None else g.numpy() for g in got]
+
+    for _ in range(12):
+        fb, fa = trade(*slab.ghost_send(mine))
+        slab.ghost_recv(mine, fb, fa)
+        out, _ = slab.step_slab(cell, y0, mine)
+        fb, fa = trade(*slab.outflow_send(out))
+        slab.inflow_recv(out, fb, fa)
+        mine = out
+    np.save(os.path.join(outdir, "slab_%d.npy" % rank), mine[:, :, 2:rows + 2])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("bc", [0, 1], ids=["periodic", "couette"])
+def test_slab_ranks_gloo(tmp_path, bc):
+    """Two gloo ranks each step one slab of a cell and trade rows over
+    send/recv: the joined state equals the whole-cell oracle bit for bit."""
+    import torch.multiprocessing as mp
+    from oracle import lb, slab
+    from tests.test_oracle_slab import case
+    world = 2
+    mp.spawn(_slab_worker, args=(world, free_port(), str(tmp_path), bc), nprocs=world, join=True)
+    cell, f = case(bc)
+    for _ in range(12):
+        f, _, _ = lb.step(cell, f)
+    got = np.concatenate([np.load(tmp_path / ("slab_%d.npy" % r)) for r in range(world)], axis=2)
+    assert np.array_equal(got, f)
