@@ -39,6 +39,13 @@ METRIC = "MLUPS (2-species site updates/s) and % of HBM roofline at 1 GB300; flo
 UNIT = "MLUPS"
 BYTES_PER_SITE = {"fp32": 144, "fp16": 72, "fp64": 288}
 FALLBACK_HBM_GBS = 6800.0
+# The FP64 step is bound by the FP64 pipe, not by HBM: its roofline counts the
+# FP64 operations one site update issues (ncu counts of the fused kernel: dadd
+# 140, dmul 60, dfma 142 per site, a dfma counted as two flops) against the
+# nominal FP64 rate, 1.25 TFLOP/s at the 2070 MHz maximum SM clock (152 SMs x
+# 2 FP64 FMA per clock), scaled to the SM clock sampled during the run.
+FP64_FLOPS_PER_SITE = 140 + 60 + 2 * 142
+FP64_TFLOPS_NOMINAL, SM_MAX_MHZ = 1.25, 2070.0
 
 
 def parse():
@@ -305,6 +312,20 @@ def run_ours(args):
     achieved = alg_bytes / (t_launch if kernels_per_step == 1 else t_launch * kernels_per_step) / 1e9
     traffic = committed_traffic(args.precision, nx, ny, n_cells) if kernel == "tiled" else None
 
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "%s copy bandwidth" % peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": t_launch * 1e3,
+                "bytes_per_site_update": BYTES_PER_SITE[args.precision]}
+    if args.precision == "fp64":
+        tflops = FP64_FLOPS_PER_SITE * sites / t_launch / 1e12
+        sm_mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
+        p64 = FP64_TFLOPS_NOMINAL * sm_mhz / SM_MAX_MHZ
+        roofline = {"bound": "alu", "achieved": tflops, "peak": p64, "unit": "TFLOP/s", "frac": tflops / p64,
+                    "traffic": traffic, "peak_source": "nominal FP64 rate at the sampled SM clock (%.0f MHz)" % sm_mhz,
+                    "flops_per_site_update": FP64_FLOPS_PER_SITE, "mean_launch_ms": t_launch * 1e3,
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
+
     # end to end through the C ABI with host buffers
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     h_ra, h_rb, h_ux, h_uy = pin(ra), pin(rb), pin(ux), pin(uy)
@@ -337,18 +358,14 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "fp64": "f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": "couette batch: %d cells of %dx%d, FP32, %d time steps per step, FP64 "
-                               "reductions every %d" % (n_cells, nx, ny, chunk, args.every),
+        "config": {"workload": "couette batch: %d cells of %dx%d, %s, %d time steps per step, FP64 "
+                               "reductions every %d" % (n_cells, nx, ny, args.precision.upper(), chunk, args.every),
                    "cells": n_cells, "nx": nx, "ny": ny, "lattice_steps_per_step": chunk,
                    "sampling_every": args.every, "precision": args.precision, "kernel": kernel,
                    "tile": [tx, ty], "couplings": "paper footnote, G_AB=0.405", "u_wall": "1e-4..1e-2 log",
                    "l2": "inputs larger than L2 (%.2f GB populations, ping-pong)" %
                          (2 * sites * BYTES_PER_SITE[args.precision] / 2 / 1e9)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": "%s copy bandwidth" % peak_kind,
-                     "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": t_launch * 1e3,
-                     "bytes_per_site_update": BYTES_PER_SITE[args.precision]},
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lattice_steps_per_step": chunk},
         # one flow-curve point = one Couette cell run for 2e5 time steps (the protocol of this

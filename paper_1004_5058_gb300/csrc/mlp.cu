@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "lbhb_mlp.h"
+#include "lb_internal.h"
 
 namespace {
 
@@ -474,7 +475,20 @@ cudaError_t refresh(mlp_handle* h)
     return cudaGetLastError();
 }
 
-lb_status check_batch(const mlp_handle* h, int B) { return (B < 1 || B > h->cfg.max_batch) ? LB_ERR_INVALID : LB_OK; }
+lb_status invalid(const char* msg)
+{
+    lbhb::set_handleless_error(msg);
+    return LB_ERR_INVALID;
+}
+
+lb_status check_batch(const mlp_handle* h, int B)
+{
+    if (B >= 1 && B <= h->cfg.max_batch) return LB_OK;
+    char buf[128];
+    snprintf(buf, sizeof buf, "mlp: batch %d outside 1..max_batch (%d)", B, h->cfg.max_batch);
+    lbhb::set_handleless_error(buf);
+    return LB_ERR_INVALID;
+}
 
 }  // namespace
 
@@ -484,12 +498,13 @@ long long mlp_param_count(void) { return NPARAM; }
 
 lb_status mlp_create(const mlp_config* cfg, void* cuda_stream, mlp_handle** out)
 {
-    if (!out || !cfg) return LB_ERR_INVALID;
+    if (!out || !cfg) return invalid("mlp_create: NULL config or output");
     *out = nullptr;
     if (cfg->max_batch < 1 || cfg->max_batch > (1 << 24) || !(cfg->sigma_scale > 0.0) || !(cfg->lr >= 0.0))
-        return LB_ERR_INVALID;
+        return invalid("mlp_create: max_batch, sigma_scale or lr out of range");
     for (int c = 0; c < NIN; ++c)
-        if (!(cfg->half_range[c] > 0.0) || !std::isfinite(cfg->center[c])) return LB_ERR_INVALID;
+        if (!(cfg->half_range[c] > 0.0) || !std::isfinite(cfg->center[c]))
+            return invalid("mlp_create: half_range must be > 0 and center finite");
     mlp_handle* h = new (std::nothrow) mlp_handle();
     if (!h) return LB_ERR_NOMEM;
     h->cfg = *cfg;
@@ -550,7 +565,7 @@ lb_status mlp_create(const mlp_config* cfg, void* cuda_stream, mlp_handle** out)
 
 lb_status mlp_set_params(mlp_handle* h, const float* params, long long n)
 {
-    if (!h || !params || n != NPARAM) return LB_ERR_INVALID;
+    if (!h || !params || n != NPARAM) return invalid("mlp: NULL handle or parameters, or wrong count");
     cudaError_t e = cudaMemcpyAsync(h->P, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->M, 0, sizeof(float) * NPARAM, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->V, 0, sizeof(float) * NPARAM, h->stream);
@@ -562,7 +577,7 @@ lb_status mlp_set_params(mlp_handle* h, const float* params, long long n)
 
 lb_status mlp_get_params(mlp_handle* h, float* params, long long n)
 {
-    if (!h || !params || n != NPARAM) return LB_ERR_INVALID;
+    if (!h || !params || n != NPARAM) return invalid("mlp: NULL handle or parameters, or wrong count");
     cudaError_t e = cudaMemcpyAsync(params, h->P, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
@@ -570,7 +585,7 @@ lb_status mlp_get_params(mlp_handle* h, float* params, long long n)
 
 lb_status mlp_forward(mlp_handle* h, const float* x, int batch, float* out)
 {
-    if (!h || !x || !out) return LB_ERR_INVALID;
+    if (!h || !x || !out) return invalid("mlp: NULL handle or buffer");
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
     cudaError_t e = forward(h, x, batch);
     if (e == cudaSuccess) {
@@ -584,7 +599,7 @@ lb_status mlp_forward(mlp_handle* h, const float* x, int batch, float* out)
 lb_status mlp_gradients(mlp_handle* h, const float* x, const float* target_stress, const float* label, int batch,
                         float* grad, double* loss)
 {
-    if (!h || !x || !target_stress || !label || !grad) return LB_ERR_INVALID;
+    if (!h || !x || !target_stress || !label || !grad) return invalid("mlp: NULL handle or buffer");
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
     cudaError_t e = forward(h, x, batch);
     if (e == cudaSuccess) e = backward(h, target_stress, label, batch, nullptr, h->loss_d);
@@ -599,7 +614,7 @@ lb_status mlp_gradients(mlp_handle* h, const float* x, const float* target_stres
 lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stress, const float* label, int batch,
                          float* loss_dev)
 {
-    if (!h || !x || !target_stress || !label) return LB_ERR_INVALID;
+    if (!h || !x || !target_stress || !label) return invalid("mlp: NULL handle or buffer");
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
     cudaError_t e = forward(h, x, batch);
     if (e == cudaSuccess) e = backward(h, target_stress, label, batch, loss_dev, nullptr);
@@ -620,7 +635,7 @@ lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stre
 
 lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit, int* fallback)
 {
-    if (!h || !x || !stress || !logit || !fallback) return LB_ERR_INVALID;
+    if (!h || !x || !stress || !logit || !fallback) return invalid("mlp: NULL handle or buffer");
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
     cudaError_t e = forward(h, x, batch);
     if (e == cudaSuccess) {
@@ -637,7 +652,7 @@ lb_status mlp_set_error_budget(mlp_handle* h, const float* bin_error, int n_bins
                                double log_s_hi, double budget)
 {
     if (!h || n_bins < 0 || n_bins > MAX_BINS || (n_bins > 0 && (!bin_error || !(log_s_hi > log_s_lo))))
-        return LB_ERR_INVALID;
+        return invalid("mlp_set_error_budget: NULL handle, n_bins outside 0..256 or empty log S range");
     int flags[MAX_BINS] = {0};
     for (int k = 0; k < n_bins; ++k) flags[k] = !(bin_error[k] <= budget);  // NaN error is over budget
     cudaError_t e = cudaMemcpyAsync(h->over_budget, flags, sizeof(int) * MAX_BINS, cudaMemcpyHostToDevice, h->stream);

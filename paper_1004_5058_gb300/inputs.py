@@ -108,16 +108,28 @@ def couette_velocity(nx: int, ny: int, u_wall, n_cells: int = 1):
     return ux, np.zeros_like(ux)
 
 
-def sine_fields(nx: int, ny: int, n_cells: int = 1):
+def sine_fields(nx: int, ny: int, n_cells: int = 1, noise: float = 0.0, seed: int = 1004):
     """The paper's initial state (Numerical Results): rho_A = 0.61(1+0.1 sin(k y)),
-    rho_B = 0.61(1+0.01 sin(k y)), k = 64*pi/L with L = ny."""
+    rho_B = 0.61(1+0.01 sin(k y)), k = 64*pi/L with L = ny.
+
+    That state is invariant under translations in x, and so is every later state
+    of an update that treats all columns with the same arithmetic: the lamellae
+    never break up into the droplets the paper shows.  noise > 0 multiplies each
+    density by (1 + noise xi), xi uniform in [-1, 1) from the SplitMix64 stream
+    (species A then B, cell-major, y-major), to break that symmetry."""
     k = 64.0 * math.pi / ny
     y = np.arange(ny, dtype=np.float64)
     ra = 0.61 * (1.0 + 0.1 * np.sin(k * y))
     rb = 0.61 * (1.0 + 0.01 * np.sin(k * y))
     shape = (n_cells, ny, nx)
-    return (np.broadcast_to(ra[None, :, None], shape).copy(),
-            np.broadcast_to(rb[None, :, None], shape).copy())
+    ra = np.broadcast_to(ra[None, :, None], shape).copy()
+    rb = np.broadcast_to(rb[None, :, None], shape).copy()
+    if noise > 0.0:
+        n = n_cells * nx * ny
+        xi = 2.0 * uniform01(seed, 2 * n) - 1.0
+        ra *= 1.0 + noise * xi[:n].reshape(shape)
+        rb *= 1.0 + noise * xi[n:].reshape(shape)
+    return ra, rb
 
 
 def kolmogorov_f0(u0: float, ny: int, rho: float = 1.22, tau: float = 1.0) -> float:

@@ -169,7 +169,8 @@ class Surrogate:
         stress_val), uploaded as the serving error budget; returns the table."""
         import torch
         X = torch.tensor(np.asarray(x_val), dtype=torch.float32, device="cuda")
-        pred = self.forward(X)[:, 0].cpu().numpy().astype(np.float64)
+        pred = np.concatenate([self.forward(X[k:k + self.max_batch].contiguous())[:, 0].cpu().numpy()
+                               for k in range(0, X.shape[0], self.max_batch)]).astype(np.float64)
         ls = np.asarray(x_val)[:, 0]
         lo, hi = self.box.center[0] - self.box.half_range[0], self.box.center[0] + self.box.half_range[0]
         k = np.clip(np.floor((ls - lo) / (hi - lo) * n_bins).astype(int), 0, n_bins - 1)

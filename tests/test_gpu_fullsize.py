@@ -65,9 +65,9 @@ def test_bench_batch_8x1024():
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp16", 5e-5), ("fp64", 1e-14)])
 def test_precision_study_cell_4096(prec, tol):
     from paper_1004_5058_gb300 import Lattice
-    cells, ra, rb, ux, uy = couette_batch(1, 4096, seed=77)
-    cells[0].u_wall = 1e-3
-    ux, uy = I.couette_velocity(4096, 4096, 1e-3)
+    cells = [I.make_cell("paper", nx=4096, ny=4096, g_ab=0.405, bc=1, u_wall=1e-3)]
+    ra, rb = I.random_fields(4096, 4096, n_cells=1, seed=77)
+    ux, uy = I.couette_velocity(4096, 4096, [1e-3], n_cells=1)
     with Lattice(cells, prec) as lat:
         lat.init_fields(ra, rb, ux, uy)
         assert lat.kernel()[0] == "tiled"
