@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (2-species site updates/s) and % of HBM roofline at 1 GB300; flow-curve points/s"
 UNIT = "MLUPS"
-BYTES_PER_SITE = {"fp32": 144, "fp16": 72, "fp64": 288}
+BYTES_PER_SITE = {"fp32": 144, "fp16": 72, "fp16sr": 72, "fp64": 288}
 FALLBACK_HBM_GBS = 6800.0
 # The FP64 step is bound by the FP64 pipe, not by HBM: its roofline counts the
 # FP64 operations one site update issues (ncu counts of the fused kernel: dadd
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--cells", type=int, default=8)
     ap.add_argument("--chunk", type=int, default=100, help="lattice time steps per benchmark step")
     ap.add_argument("--every", type=int, default=10, help="sampling interval of the FP64 reductions")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp16sr", "fp64"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "tiled"])
     ap.add_argument("--tile", default="", help="TXxTY for the tiled kernel (default: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
@@ -356,7 +356,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "fp64": "f64"}[args.precision],
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "fp16sr": "f16-storage/f32",
+                                       "fp64": "f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": "couette batch: %d cells of %dx%d, %s, %d time steps per step, FP64 "
                                "reductions every %d" % (n_cells, nx, ny, args.precision.upper(), chunk, args.every),

@@ -55,8 +55,15 @@ typedef enum { LB_BC_PERIODIC = 0, LB_BC_COUETTE = 1 } lb_bc;
 
 /* Storage precision of the populations.  Arithmetic is FP32 for LB_FP32 and
  * LB_FP16_SHIFTED (populations stored as g_i = f_i - w_i rho_bar_s in FP16,
- * round to nearest) and FP64 for LB_FP64.  Observables are reduced in FP64. */
-typedef enum { LB_FP32 = 0, LB_FP16_SHIFTED = 1, LB_FP64 = 2 } lb_precision;
+ * round to nearest) and FP64 for LB_FP64.  LB_FP16_SHIFTED_SR stores 4096 g_i
+ * in FP16 with stochastic rounding in the time step (unbiased: the stored value
+ * equals the computed one in expectation, so rounding errors do not accumulate
+ * into a drift of mass or momentum in near-uniform states); the random bits come
+ * from a hash of each site and its densities, so runs are reproducible.  Its
+ * 2 bytes per value and FP32 arithmetic are those of LB_FP16_SHIFTED.  The paper
+ * stores populations in one precision and says nothing of reduced storage.
+ * Observables are reduced in FP64. */
+typedef enum { LB_FP32 = 0, LB_FP16_SHIFTED = 1, LB_FP64 = 2, LB_FP16_SHIFTED_SR = 3 } lb_precision;
 
 /* Kernel family: AUTO picks TILED when the shape allows it, else GENERIC. */
 typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_GENERIC = 1, LB_KERNEL_TILED = 2 } lb_kernel;
@@ -182,8 +189,8 @@ long long lb_kernel_launches(const lb_handle* h);
  * lb_reductions that needs no handle.
  *   populations  caller's device buffer, layout [n_cells][18][ny][pitch]
  *                (species A then B, D2Q9 order as in lb_set_populations), in
- *                LB_FP32 or LB_FP64 storage; LB_FP16_SHIFTED is rejected
- *                (LB_ERR_UNSUPPORTED)
+ *                LB_FP32 or LB_FP64 storage; LB_FP16_SHIFTED and
+ *                LB_FP16_SHIFTED_SR are rejected (LB_ERR_UNSUPPORTED)
  *   sums         caller's device buffer [n_cells][4] float64, receives
  *                (sum rho_A, sum rho_B, sum j_x, sum j_y) per cell; a
  *                non-finite density makes its cell's sums non-finite

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "LB_OK", -1: "LB_ERR_INVALID", -2: "LB_ERR_CUDA", -3: "LB_ERR
                 -4: "LB_ERR_NONFINITE", -5: "LB_ERR_TIMEOUT", -6: "LB_ERR_STATE",
                 -7: "LB_ERR_UNSUPPORTED"}
 LB_BC_PERIODIC, LB_BC_COUETTE = 0, 1
-LB_FP32, LB_FP16_SHIFTED, LB_FP64 = 0, 1, 2
+LB_FP32, LB_FP16_SHIFTED, LB_FP64, LB_FP16_SHIFTED_SR = 0, 1, 2, 3
 LB_KERNEL_AUTO, LB_KERNEL_GENERIC, LB_KERNEL_TILED = 0, 1, 2
 
 # Every function the header declares, with its ctypes signature.

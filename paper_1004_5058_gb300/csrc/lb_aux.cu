@@ -235,5 +235,6 @@ cudaError_t launch_accumulate(const double* prof_part, const double* wall_part, 
 LBHB_INST(float)
 LBHB_INST(double)
 LBHB_INST(__half)
+LBHB_INST(half_sr)
 
 }  // namespace lbhb

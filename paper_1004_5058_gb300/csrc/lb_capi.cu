@@ -148,6 +148,7 @@ static cudaError_t with_type(const lb_handle* h, F&& fn)
     switch (h->prec) {
     case LB_FP32: return fn((float*)nullptr);
     case LB_FP64: return fn((double*)nullptr);
+    case LB_FP16_SHIFTED_SR: return fn((half_sr*)nullptr);
     default: return fn((__half*)nullptr);
     }
 }
@@ -224,7 +225,7 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
     if (tiled_partials_nbx(h->g, tx) > h->nbx_alloc)
         return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: tile %d too narrow for the partial buffers", tx);
     const char* msg = nullptr;
-    TiledPlan* p = tiled_create(h->g, h->elem, h->bc, h->f[0], h->f[1], tx, ty, &msg);
+    TiledPlan* p = tiled_create(h->g, (int)h->prec, h->elem, h->bc, h->f[0], h->f[1], tx, ty, &msg);
     if (!p) return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: %s", msg ? msg : "tiled plan failed");
     if (h->plan) tiled_destroy(h->plan);
     h->plan = p;
@@ -241,7 +242,7 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
     if (!out) return fail(nullptr, LB_ERR_INVALID, "lb_create: out is NULL");
     *out = nullptr;
     if (!cells || n_cells < 1) return fail(nullptr, LB_ERR_INVALID, "lb_create: need n_cells >= 1 cells");
-    if (prec != LB_FP32 && prec != LB_FP16_SHIFTED && prec != LB_FP64)
+    if (prec != LB_FP32 && prec != LB_FP16_SHIFTED && prec != LB_FP64 && prec != LB_FP16_SHIFTED_SR)
         return fail(nullptr, LB_ERR_INVALID, "lb_create: unknown precision %d", (int)prec);
     const lb_cell_params& c0 = cells[0];
     for (int c = 0; c < n_cells; ++c) {

@@ -80,31 +80,101 @@ __host__ __device__ inline long long fidx(const Geom& g, int cell, int q, int y,
 }
 
 // ------------------------------------------------------- storage formats --
+// Random bits for stochastic rounding.  A thread seeds one stream per row it
+// stores from a hash of the site and of the site's current densities (so the
+// stream changes from one step to the next without a step counter, and a run
+// is reproducible bit for bit), then advances it by one 32-bit linear
+// congruential step per stored value (the Numerical Recipes constants) and uses
+// its top 13 bits.  The seed hash is the "lowbias32" integer finaliser found by
+// C. Wellons' hash-prospector search.
+struct Dither {
+    uint32_t s;
+    __device__ static uint32_t mix(uint32_t x)
+    {
+        x ^= x >> 16;
+        x *= 0x7feb352du;
+        x ^= x >> 15;
+        x *= 0x846ca68bu;
+        x ^= x >> 16;
+        return x;
+    }
+    __device__ void seed(uint32_t site, uint32_t data) { s = mix(site ^ mix(data)); }
+    __device__ uint32_t next13()
+    {
+        s = s * 1664525u + 1013904223u;
+        return s >> 19;
+    }
+};
+
+// FP32 -> FP16 with stochastic rounding: FP16 keeps the top 10 of the 23
+// mantissa bits of a normal FP32 value; adding 13 uniform random bits below
+// them and truncating rounds up with probability (dropped bits) / 2^13, so the
+// stored value is the input in expectation.  Exact for inputs whose FP16 image
+// is a normal number; below 2^-14 the dropped part is wider than the random
+// bits and the rounding leans towards zero (callers scale values away from
+// that range).
+__device__ inline __half half_sr_round(float v, Dither& d)
+{
+    return __float2half_rz(__uint_as_float(__float_as_uint(v) + d.next13()));
+}
+
+// FP16 element of the stochastically rounded storage (a distinct type so that
+// every kernel is instantiated for it).
+struct half_sr {
+    __half h;
+};
+
 template <class T> struct Store;
+// scale: stored value = scale * (f - shift); dithered: stores round stochastically
 template <> struct Store<float> {
     using C = float;
-    static constexpr bool shifted = false;
+    static constexpr bool shifted = false, dithered = false;
+    static constexpr float scale = 1.f;
     __device__ static C ld(const float* p, long long k, C) { return p[k]; }
     __device__ static void st(float* p, long long k, C v, C) { p[k] = v; }
+    __device__ static void st(float* p, long long k, C v, C, Dither&) { p[k] = v; }
 };
 template <> struct Store<double> {
     using C = double;
-    static constexpr bool shifted = false;
+    static constexpr bool shifted = false, dithered = false;
+    static constexpr double scale = 1.0;
     __device__ static C ld(const double* p, long long k, C) { return p[k]; }
     __device__ static void st(double* p, long long k, C v, C) { p[k] = v; }
+    __device__ static void st(double* p, long long k, C v, C, Dither&) { p[k] = v; }
 };
 // FP16 storage of the shifted populations g_i = f_i - w_i rho_bar_s.
 template <> struct Store<__half> {
     using C = float;
-    static constexpr bool shifted = true;
+    static constexpr bool shifted = true, dithered = false;
+    static constexpr float scale = 1.f;
     __device__ static C ld(const __half* p, long long k, C shift) { return __half2float(p[k]) + shift; }
     __device__ static void st(__half* p, long long k, C v, C shift) { p[k] = __float2half_rn(v - shift); }
+    __device__ static void st(__half* p, long long k, C v, C shift, Dither&) { p[k] = __float2half_rn(v - shift); }
+};
+// FP16 storage of 4096 g_i, rounded stochastically by the step kernels (round to
+// nearest where a state is set from outside: initialisation and import).  The
+// power-of-two scale is exact and moves every |g| >= 2^-26 into the FP16
+// normal range, where the stochastic rounding is exact; |g| <= 16 fits.
+template <> struct Store<half_sr> {
+    using C = float;
+    static constexpr bool shifted = true, dithered = true;
+    static constexpr float scale = 4096.f;
+    __device__ static C ld(const half_sr* p, long long k, C shift)
+    {
+        return __half2float(p[k].h) * (1.f / 4096.f) + shift;
+    }
+    __device__ static void st(half_sr* p, long long k, C v, C shift) { p[k].h = __float2half_rn((v - shift) * scale); }
+    __device__ static void st(half_sr* p, long long k, C v, C shift, Dither& d)
+    {
+        p[k].h = half_sr_round((v - shift) * scale, d);
+    }
 };
 
-// Stored element -> compute type (shift not included).
+// Stored element -> compute type (shift and scale not included).
 __device__ inline float to_c(float v) { return v; }
 __device__ inline double to_c(double v) { return v; }
 __device__ inline float to_c(__half v) { return __half2float(v); }
+__device__ inline float to_c(half_sr v) { return __half2float(v.h); }
 
 // Quotient for the collision: FP32 uses the fast division intrinsic (2 ulp),
 // FP64 the correctly rounded one.
@@ -214,10 +284,12 @@ __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C u
 // so no population needs its shift added or removed, and the arithmetic works
 // on the small deviations.  Momenta of g equal those of f (opposite directions
 // carry equal weights).
+// With scale != 1 the populations are scale * g (FP16 storage with stochastic
+// rounding) and so are the results; rho_s, psi_s, u and the forces are not scaled.
 template <class C>
 __device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar, C psi_s, C ux, C uy, C ax,
                                                const Sums<C>& sm, C ga, C gr, const ParamSet<C>& p, C gs[9],
-                                               C* Fx, C* Fy)
+                                               C* Fx, C* Fy, C scale = C(1))
 {
     const C tau = p.tau, omega = p.omega, gx = p.gab_over_rho0;
     const C Gx = ga * sm.s1x + gr * sm.s2x;
@@ -227,7 +299,7 @@ __device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar,
     const C por = rho_s != C(0) ? fast_div<C>(psi_s, rho_s) : C(1);
     const C usx = ux - tau * (por * Gx + gx * sm.xx) + tau * ax;
     const C usy = uy - tau * (por * Gy + gx * sm.xy);
-    const C dr = rho_s - rho_bar;
+    const C dr = (rho_s - rho_bar) * scale, rs = rho_s * scale;
     const C usq = C(1.5) * (usx * usx + usy * usy);
     const C w1 = C(q_w(1)), w5 = C(q_w(5));
     const C cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
@@ -236,8 +308,8 @@ __device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const C w = k < 2 ? w1 : w5;
-        const C a = w * (dr + rho_s * (C(4.5) * cu[k] * cu[k] - usq));
-        const C b = (C(3) * w * rho_s) * cu[k];
+        const C a = w * (dr + rs * (C(4.5) * cu[k] * cu[k] - usq));
+        const C b = (C(3) * w * rs) * cu[k];
         const int i = lo[k], j = hi[k];
         gs[i] = g[i] + omega * ((a + b) - g[i]);
         gs[j] = g[j] + omega * ((a - b) - g[j]);

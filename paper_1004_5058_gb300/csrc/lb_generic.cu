@@ -84,6 +84,10 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
         collide_site<C>(f, rho, psi, sm, p, body_force_x<C>(p, y), c);
 
         const C u_top = p.u_wall, u_bot = -p.u_wall;
+        Dither dz;  // stochastic rounding stream of this site (dithered storage only)
+        if constexpr (Store<T>::dithered)
+            dz.seed(((uint32_t)cell * 0x9E3779B1u) ^ ((uint32_t)y << 15) ^ ((uint32_t)x << 1),
+                    __float_as_uint(rho[0]) ^ (__float_as_uint(rho[1]) * 0x85EBCA6Bu));
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -94,12 +98,12 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
                     C dpx;
                     const C back = bounce<C>(i, c.fs[s][i], rho[s], yd < 0 ? u_bot : u_top, &dpx);
                     const C sho = Store<T>::shifted ? pop_shift<C>(q_opp(i), p, s) : C(0);
-                    Store<T>::st(fout, fidx(g, cell, s * 9 + q_opp(i), y, x), back, sho);
+                    Store<T>::st(fout, fidx(g, cell, s * 9 + q_opp(i), y, x), back, sho, dz);
                     dpx_site += (double)dpx;
                 } else {
                     const int xd = wrap_x(x + q_cx(i), g.nx);
                     const int ydd = yd < 0 ? yd + g.ny : (yd >= g.ny ? yd - g.ny : yd);
-                    Store<T>::st(fout, fidx(g, cell, s * 9 + i, ydd, xd), c.fs[s][i], sh);
+                    Store<T>::st(fout, fidx(g, cell, s * 9 + i, ydd, xd), c.fs[s][i], sh, dz);
                 }
             }
         if (SAMPLE) {
@@ -152,5 +156,7 @@ template cudaError_t launch_generic_step<double>(const double*, double*, const G
                                                  bool, double*, double*, unsigned*, cudaStream_t, int*);
 template cudaError_t launch_generic_step<__half>(const __half*, __half*, const Geom&, int, const CellDev*, void*,
                                                  bool, double*, double*, unsigned*, cudaStream_t, int*);
+template cudaError_t launch_generic_step<half_sr>(const half_sr*, half_sr*, const Geom&, int, const CellDev*, void*,
+                                                  bool, double*, double*, unsigned*, cudaStream_t, int*);
 
 }  // namespace lbhb

@@ -18,7 +18,7 @@ bool tiled_supported(const Geom& g, int elem_bytes, int tile_x, int tile_y);
 int tiled_partials_nbx(const Geom& g, int tile_x);
 // Creates the plan (tensor maps for both ping-pong buffers).  Returns nullptr
 // and sets *err_msg if the shape/tile is not supported or encoding failed.
-TiledPlan* tiled_create(const Geom& g, int elem_bytes, int bc, void* f0, void* f1, int tile_x, int tile_y,
+TiledPlan* tiled_create(const Geom& g, int prec, int elem_bytes, int bc, void* f0, void* f1, int tile_x, int tile_y,
                         const char** err_msg);
 void tiled_destroy(TiledPlan* p);
 template <class T>

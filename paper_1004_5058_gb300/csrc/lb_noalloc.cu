@@ -62,7 +62,8 @@ extern "C" lb_status lb_reductions_noalloc(const void* populations, lb_precision
                                            int n_cells, double* sums, void* cuda_stream)
 {
     if (!populations || !sums) return fail(LB_ERR_INVALID, "populations and sums must be device pointers");
-    if (prec == LB_FP16_SHIFTED) return fail(LB_ERR_UNSUPPORTED, "FP16-shifted storage is not supported");
+    if (prec == LB_FP16_SHIFTED || prec == LB_FP16_SHIFTED_SR)
+        return fail(LB_ERR_UNSUPPORTED, "FP16-shifted storage is not supported");
     if (prec != LB_FP32 && prec != LB_FP64) return fail(LB_ERR_INVALID, "unknown precision");
     if (nx < 1 || ny < 1 || n_cells < 1 || pitch < nx) return fail(LB_ERR_INVALID, "need nx, ny, n_cells >= 1, pitch >= nx");
     const int elem = prec == LB_FP64 ? 8 : 4;

@@ -22,8 +22,10 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "lb_internal.h"
+#include "lbhb.h"
 #include "tma.cuh"
 
 namespace lbhb {
@@ -105,6 +107,41 @@ template <> struct Vec2<__half> {
     // FP16 storage of shifted values: the caller subtracts the shift
     __device__ static void st(__half* p, float a, float b) { *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b); }
 };
+// stochastically rounded FP16: loads as for __half (the caller unscales),
+// stores with the thread's dither stream
+template <> struct Vec2<half_sr> {
+    __device__ static void ld(const half_sr* p, float& a, float& b)
+    {
+        const __half2 v = *reinterpret_cast<const __half2*>(p);
+        a = __low2float(v);
+        b = __high2float(v);
+    }
+    __device__ static void st(half_sr* p, float a, float b, Dither& d)
+    {
+        const __half lo = half_sr_round(a, d), hi = half_sr_round(b, d);
+        *reinterpret_cast<__half2*>(p) = __halves2half2(lo, hi);
+    }
+};
+// paired and single stores of values already in the stored representation,
+// dithered where the storage asks for it
+template <class T, class C>
+__device__ inline void st_pair(T* p, C a, C b, Dither& d)
+{
+    if constexpr (Store<T>::dithered)
+        Vec2<T>::st(p, a, b, d);
+    else
+        Vec2<T>::st(p, a, b);
+}
+template <class T, class C>
+__device__ inline void st_one(T* p, C v, Dither& d)
+{
+    if constexpr (std::is_same<T, half_sr>::value)
+        p->h = half_sr_round(v, d);
+    else if constexpr (std::is_same<T, __half>::value)
+        *p = __float2half_rn(v);
+    else
+        *p = v;
+}
 
 // Threads per CTA: a thread per (species, column pair), TX threads, plus one
 // service warp that issues the TMA copies and computes the four halo columns
@@ -122,6 +159,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                                                             unsigned* __restrict__ err)
 {
     using C = typename Store<T>::C;
+    // stored populations are scale * g (scale 1 except for the dithered FP16 storage)
+    constexpr C scale = C(Store<T>::scale), inv_scale = C(1) / scale;
     constexpr int E = (int)sizeof(T);
     constexpr int H = 16 / E;            // halo columns per side brought by TMA
     constexpr int W = TX + 4;            // ring row: columns -2 .. TX+1
@@ -147,6 +186,10 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
     // service warp: lanes 0-3 species A, 4-7 species B of the halo columns
     const int sp = svc ? (lane >> 2) & 1 : lane >> 4;
     const int c0 = svc ? 0 : warp * 32 + 2 * (lane & 15);
+    // a pipeline that timed out in an earlier launch of the same batch does not
+    // run again (each later launch would otherwise wait out its own bound); the
+    // decision is taken once per CTA
+    if (__syncthreads_or(t == 0 && (*reinterpret_cast<volatile unsigned*>(err) & ERR_TIMEOUT) != 0u)) return;
     if (t == 0) {
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
         fence_mbar_init();
@@ -246,8 +289,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                     r1 += b;
                 }
                 if (Store<T>::shifted) {  // sum of the shifts w_i rho_bar is rho_bar
-                    r0 += rho_bar;
-                    r1 += rho_bar;
+                    r0 = r0 * inv_scale + rho_bar;
+                    r1 = r1 * inv_scale + rho_bar;
                 }
                 Vec2<C>::st(psi_ring + ring + c0 + 2, psi_of<C>(r0, p.rho0, p.inv_rho0),
                             psi_of<C>(r1, p.rho0, p.inv_rho0));
@@ -260,7 +303,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 C acc = C(0);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) acc += to_c(src[i * H]);
-                if (Store<T>::shifted) acc += rho_bar;
+                if (Store<T>::shifted) acc = acc * inv_scale + rho_bar;
                 const int pos = h < 2 ? h : TX + h;
                 psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
                 rho_ring[ring + pos] = acc;
@@ -327,18 +370,24 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 }
                 const Sums<C> sm = stencil_sums<C>(dps, dro);
                 const C jx_s = mom_x<C>(f[o]), jy_s = mom_y<C>(f[o]);
-                jx[o] = jx_s + __shfl_xor_sync(0xffffffffu, jx_s, 16);
-                jy[o] = jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16);
+                jx[o] = (jx_s + __shfl_xor_sync(0xffffffffu, jx_s, 16)) * inv_scale;
+                jy[o] = (jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16)) * inv_scale;
                 const C rho_t = rho_s[o] + e[1][o + 2];
                 const C inv_rho = fast_div<C>(C(1), rho_t);
                 if (Store<T>::shifted)
                     collide_species_shifted<C>(f[o], rho_s[o], rho_bar, v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho,
-                                               fx_body * inv_rho, sm, ga, gr, p, fs[o], &Fx[o], &Fy[o]);
+                                               fx_body * inv_rho, sm, ga, gr, p, fs[o], &Fx[o], &Fy[o], scale);
                 else
                     collide_species<C>(f[o], rho_s[o], v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho, fx_body * inv_rho,
                                        sm, ga, gr, p, fs[o], &Fx[o], &Fy[o]);
             }
 
+            // stochastic rounding: one stream per thread and row, seeded from the
+            // sites and their densities
+            Dither dz;
+            if constexpr (Store<T>::dithered)
+                dz.seed(((uint32_t)cell * 0x9E3779B1u) ^ ((uint32_t)y << 15) ^ ((uint32_t)x << 1) ^ (uint32_t)sp,
+                        __float_as_uint(rho_s[0]) ^ (__float_as_uint(rho_s[1]) * 0x85EBCA6Bu));
             // push streaming; rows next to a Couette wall bounce back in place
             const bool wall_lo = bc == 1 && y == 0, wall_hi = bc == 1 && y == g.ny - 1;
             const int pl = (int)g.plane;  // < 2^31 / 18, checked on the host
@@ -358,15 +407,15 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                     // put back first; opposite directions carry equal weights, so the
                     // same shift is removed again)
                     const C sh = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
-                    const C ba = bounce<C>(i, fs[0][i] + sh, rho_s[0], uw, &dpa);
-                    const C bb = bounce<C>(i, fs[1][i] + sh, rho_s[1], uw, &dpb);
-                    Vec2<T>::st(dst_s + q_opp(i) * pl + row3[1] + x, ba - sh, bb - sh);
+                    const C ba = bounce<C>(i, fs[0][i] * inv_scale + sh, rho_s[0], uw, &dpa);
+                    const C bb = bounce<C>(i, fs[1][i] * inv_scale + sh, rho_s[1], uw, &dpb);
+                    st_pair<T, C>(dst_s + q_opp(i) * pl + row3[1] + x, (ba - sh) * scale, (bb - sh) * scale, dz);
                     dpx_site += dpa + dpb;
                 } else if (cx == 0) {
-                    Vec2<T>::st(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i]);
+                    st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
                 } else {
-                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], C(0));
-                    Store<T>::st(dst_s, i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], C(0));
+                    st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
+                    st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
                 }
             }
             if (SAMPLE) {
@@ -478,11 +527,14 @@ static const void* pick(int tx, bool sample)
     }
 }
 
-static const void* pick_any(int elem, int tx, bool sample)
+static const void* pick_any(int prec, int tx, bool sample)
 {
-    if (elem == 4) return pick<float>(tx, sample);
-    if (elem == 8) return pick<double>(tx, sample);
-    return pick<__half>(tx, sample);
+    switch (prec) {
+    case LB_FP32: return pick<float>(tx, sample);
+    case LB_FP64: return pick<double>(tx, sample);
+    case LB_FP16_SHIFTED_SR: return pick<half_sr>(tx, sample);
+    default: return pick<__half>(tx, sample);
+    }
 }
 
 static bool encode(CUtensorMap* m, void* base, const Geom& g, int elem, int box_x)
@@ -503,7 +555,7 @@ static bool encode(CUtensorMap* m, void* base, const Geom& g, int elem, int box_
     return r == CUDA_SUCCESS;
 }
 
-TiledPlan* tiled_create(const Geom& g, int elem, int bc, void* f0, void* f1, int tile_x, int tile_y,
+TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, void* f1, int tile_x, int tile_y,
                         const char** err_msg)
 {
     if (!tiled_supported(g, elem, tile_x, tile_y)) {
@@ -533,7 +585,7 @@ TiledPlan* tiled_create(const Geom& g, int elem, int bc, void* f0, void* f1, int
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int occ = 1;
     for (int s = 0; s < 2; ++s) {
-        const void* k = pick_any(elem, tile_x, s == 1);
+        const void* k = pick_any(prec, tile_x, s == 1);
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess) {
             cudaGetLastError();
             if (err_msg) *err_msg = "cudaFuncSetAttribute(max dynamic smem) failed";
@@ -588,5 +640,7 @@ template cudaError_t launch_tiled_step<double>(TiledPlan*, int, const CellDev*, 
                                                cudaStream_t, int*);
 template cudaError_t launch_tiled_step<__half>(TiledPlan*, int, const CellDev*, bool, double*, double*, unsigned*,
                                                cudaStream_t, int*);
+template cudaError_t launch_tiled_step<half_sr>(TiledPlan*, int, const CellDev*, bool, double*, double*, unsigned*,
+                                                cudaStream_t, int*);
 
 }  // namespace lbhb

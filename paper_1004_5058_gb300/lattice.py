@@ -13,7 +13,8 @@ import numpy as np
 from . import _lib as L
 from .inputs import CellParams
 
-PRECISIONS = {"fp32": L.LB_FP32, "fp16": L.LB_FP16_SHIFTED, "fp16_shifted": L.LB_FP16_SHIFTED, "fp64": L.LB_FP64}
+PRECISIONS = {"fp32": L.LB_FP32, "fp16": L.LB_FP16_SHIFTED, "fp16_shifted": L.LB_FP16_SHIFTED, "fp64": L.LB_FP64,
+              "fp16sr": L.LB_FP16_SHIFTED_SR}
 KERNELS = {"auto": L.LB_KERNEL_AUTO, "generic": L.LB_KERNEL_GENERIC, "tiled": L.LB_KERNEL_TILED}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 

@@ -41,8 +41,10 @@ def _cuda_time(fn):
 
 
 def precision_study(n: int = 4096, u_wall: float = 1e-3, steps: int = 50000, every: int = 100,
-                    precisions=("fp64", "fp32", "fp16"), seed: int = 1004, g_ab: float = 0.405):
-    """Same cell, same seeded start, three storage precisions."""
+                    precisions=("fp64", "fp32", "fp16", "fp16sr"), seed: int = 1004, g_ab: float = 0.405):
+    """Same cell, same seeded start, each storage precision: MLUPS, the field
+    difference from the FP64 run, the wall stress and shear rate against it,
+    and the drift of each species' mass."""
     cell = I.make_cell("paper", nx=n, ny=n, g_ab=g_ab, bc=1, u_wall=u_wall)
     ra, rb = I.random_fields(n, n, seed=seed)
     ux, uy = I.couette_velocity(n, n, u_wall)
@@ -59,16 +61,18 @@ def precision_study(n: int = 4096, u_wall: float = 1e-3, steps: int = 50000, eve
             mass, _ = lat.reductions()
             res[prec] = dict(rho_a=a[0], rho_b=b[0], sigma=float(sigma[0]), S=float(S[0]), S_bulk=float(Sb[0]),
                              mlups=n * n * steps / dt / 1e6, seconds=dt, kernel=lat.kernel(),
-                             mass_drift=float(abs(mass[0, 0] - ra.sum()) / ra.sum()))
+                             mass_drift=float(abs(mass[0, 0] - ra.sum()) / ra.sum()),
+                             mass_drift_b=float(abs(mass[0, 1] - rb.sum()) / rb.sum()))
     ref = res.get("fp64")
     summary = {"n": n, "u_wall": u_wall, "steps": steps, "g_ab": g_ab}
     for prec, r in res.items():
         row = {"mlups": r["mlups"], "seconds": r["seconds"], "sigma_xy": r["sigma"], "shear_rate": r["S"],
-               "kernel": r["kernel"], "mass_drift": r["mass_drift"]}
+               "kernel": r["kernel"], "mass_drift": r["mass_drift"], "mass_drift_b": r["mass_drift_b"]}
         if ref is not None and prec != "fp64":
             row["max_abs_drho"] = float(max(np.abs(r["rho_a"] - ref["rho_a"]).max(),
                                             np.abs(r["rho_b"] - ref["rho_b"]).max()))
             row["sigma_rel_err"] = abs(r["sigma"] - ref["sigma"]) / abs(ref["sigma"])
+            row["shear_rate_rel_err"] = abs(r["S"] - ref["S"]) / abs(ref["S"])
         summary[prec] = row
     return summary
 
@@ -120,8 +124,8 @@ def flow_curve(L: int = 512, steps: int = 100000, every: int = 20, n_speeds: int
 
 
 def kolmogorov(L: int = 512, steps: int = 1000000, every: int = 100, rho0s=(0.83, 0.81),
-               u0s=(0.02, 0.04, 0.07, 0.1, 0.15, 0.2, 0.3, 0.4), g_ab: float = 0.405, precision: str = "fp32",
-               noise: float = 1e-3, seed: int = 1004):
+               u0s=(0.1, 0.2, 0.25, 0.3, 0.35, 0.4, 0.5, 0.6), g_ab: float = 0.405, precision: str = "fp32",
+               noise: float = 1e-3, seed: int = 1004, r_flow: float = 0.05):
     """The paper's own workload (section "Numerical Results"): a fully periodic
     L x L box, body force F_x(y) = F0 sin(k y), k = 2 pi / L, with F0 tuned so
     that the laminar flow would peak at U0 (F0 = rho nu k^2 U0), the paper's
@@ -136,7 +140,12 @@ def kolmogorov(L: int = 512, steps: int = 1000000, every: int = 100, rho0s=(0.83
     their invariance under x translations (without it the lamellae of the
     sinusoidal start stay lamellae, parallel to the flow, and R = 1).  Per cell
     the final state is summarised by the spread of rho_A (std over the box) and
-    its mean spread along x (droplets: comparable to the total; lamellae: 0)."""
+    its mean spread along x (droplets: comparable to the total; lamellae: 0).
+
+    Per rho0, the (S(y), sigma(y)) points of all runs that flow (R > r_flow)
+    are pooled into one scatter, the paper's master curve, and fitted with the
+    Herschel-Bulkley law; the largest forcing amplitude sigma0 = F0/k of the runs
+    that do not flow bounds the yield stress from below."""
     k = 2.0 * np.pi / L
     cells = []
     for r0 in rho0s:
@@ -161,10 +170,29 @@ def kolmogorov(L: int = 512, steps: int = 1000000, every: int = 100, rho0s=(0.83
         R = 2.0 / L * np.sum(U * np.sin(k * y)) / u0
         ok = (S > 0) & (sig > 0)
         fit = hb_fit(S[ok], sig[ok]) if ok.sum() >= 3 else None
-        out["runs"].append({"rho0": cell.rho0, "u0": u0, "f0": cell.f0, "R": float(R),
+        out["runs"].append({"rho0": cell.rho0, "u0": u0, "f0": cell.f0, "sigma0": cell.f0 / k, "R": float(R),
                             "u_max": float(np.max(np.abs(U))), "hb_fit": fit,
                             "rho_a_std": float(np.std(fa[c])), "rho_a_std_x": float(np.mean(np.std(fa[c], axis=1))),
                             "profile": [float(v) for v in U]})
+    out["master"] = {}
+    for r0 in rho0s:
+        runs = [(c, r) for c, r in enumerate(out["runs"]) if r["rho0"] == r0]
+        pts_S, pts_s = [], []
+        for c, r in runs:
+            if r["R"] <= r_flow:
+                continue
+            U = np.array(r["profile"])
+            S = (np.roll(U, -1) - np.roll(U, 1)) / 2.0
+            sig = r["f0"] / k * np.cos(k * y)
+            ok = (S > 0) & (sig > 0)
+            pts_S.extend(S[ok])
+            pts_s.extend(sig[ok])
+        arrested = [r["sigma0"] for _, r in runs if r["R"] <= r_flow]
+        pts_S, pts_s = np.array(pts_S), np.array(pts_s)
+        out["master"][str(r0)] = {
+            "flowing_runs": int(sum(1 for _, r in runs if r["R"] > r_flow)), "points": int(pts_S.size),
+            "largest_arrested_sigma0": float(max(arrested)) if arrested else None,
+            "hb_fit": hb_fit(pts_S, pts_s) if pts_S.size >= 3 else None}
     return out
 
 
@@ -198,13 +226,17 @@ def vft_fit(rho0, inv_r, rho_c_hi: float = 1.2):
 
 
 def kolmogorov_rho0_sweep(L: int = 512, steps: int = 1000000, u0: float = 0.1,
-                          rho0s=(0.70, 0.74, 0.78, 0.81, 0.83, 0.85, 0.87, 0.89), g_ab: float = 0.405):
+                          rho0s=(0.70, 0.72, 0.74, 0.75, 0.76, 0.77, 0.78, 0.79, 0.80, 0.81, 0.83, 0.85),
+                          g_ab: float = 0.405, r_floor: float = 0.02):
     """Response R = U_hat / U0 against rho0 at fixed forcing (U0 = 0.1), and the
-    VFT fit of 1/R (the paper's arrest analysis)."""
+    VFT fit of 1/R (the paper's arrest analysis) over the runs whose response is
+    above the floor r_floor (below it the box has arrested and the time-averaged
+    profile is residual motion)."""
     out = kolmogorov(L=L, steps=steps, rho0s=rho0s, u0s=(u0,), g_ab=g_ab)
     R = np.array([r["R"] for r in out["runs"]])
-    ok = R > 0
-    out["vft"] = vft_fit(np.array(rho0s)[ok], 1.0 / R[ok]) if ok.sum() >= 3 else None
+    ok = R > r_floor
+    out["vft_points"] = int(ok.sum())
+    out["vft"] = vft_fit(np.array(rho0s)[ok], 1.0 / R[ok]) if ok.sum() >= 4 else None
     return out
 
 

@@ -9,7 +9,8 @@ Tolerances (written per test) follow from the arithmetic:
     (|f| < 0.5) plus the force/shift error, a few ulp; 4e-7 absolute bounds it.
     Over 1000 steps of a relaxing (non-demixing) state, max |d rho| <= 1e-5.
   * FP16-shifted storage (eps_16 = 4.9e-4 on |g| <= 0.06): one rounding of g per
-    step, <= 3.5e-5 absolute on f.
+    step, <= 3.5e-5 absolute on f; with stochastic rounding one full FP16 ulp
+    (2^-10 of |g|), <= 7e-5.
 A demixing state (spinodal growth) amplifies any difference exponentially;
 there the comparison stops before the growth phase, and longer runs are
 compared through exact invariants (mass) instead.
@@ -60,7 +61,7 @@ def evolved_state(cell, steps, seed):
 
 # ------------------------------------------------------------ one step --
 @pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("prec,tol", [("fp64", 2e-15), ("fp32", 4e-7), ("fp16", 3.5e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 2e-15), ("fp32", 4e-7), ("fp16", 3.5e-5), ("fp16sr", 7e-5)])
 @pytest.mark.parametrize("bc", [0, 1])
 def test_one_step_from_evolved_state(kernel, prec, tol, bc):
     cell = I.make_cell("paper", nx=64, ny=48, g_ab=0.405, bc=bc, u_wall=0.02 if bc else 0.0)
@@ -279,3 +280,44 @@ def test_kolmogorov_flow_paper_start(kernel, prec, tol):
     np.testing.assert_allclose(ub[0], oub, rtol=0, atol=tol)
     # sin(k y) forcing injects no net momentum
     assert abs(mom[0, 0]) <= (1e-12 if prec == "fp64" else 1e-4) * (ra.sum() + rb.sum())
+
+
+# ------------------------------------------------- stochastic rounding --
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp16_stochastic_rounding_removes_mass_drift(kernel):
+    """A near-uniform mixed state (footnote couplings, G_AB = 0.045) relaxing
+    for 3000 steps: round-to-nearest FP16 storage repeats the same rounding
+    error at every site and the mass drifts; stochastic rounding makes each
+    error zero-mean, so the drift is a random walk far below it.  The fields
+    stay close to the FP64 oracle in both."""
+    cell = I.make_cell("paper", nx=64, ny=64)
+    ra, rb = I.random_fields(64, 64, seed=21)
+    m0 = np.array([ra.sum(), rb.sum()])
+    (r,) = oracle_runs([cell], ra, rb, steps=3000)
+    oa = r.fields()[0]
+    drift, dev = {}, {}
+    for prec in ("fp16", "fp16sr"):
+        with lattice([cell], prec, kernel) as lat:
+            lat.init_fields(ra, rb).step(3000)
+            mass, _ = lat.reductions()
+            ga = lat.fields()[0]
+        drift[prec] = np.abs(mass[0] - m0) / m0
+        dev[prec] = max_abs(ga[0], oa)
+    print("mass drift", drift, "max |d rho_A| vs FP64", dev)
+    assert np.all(drift["fp16sr"] <= 2e-6)
+    assert np.max(drift["fp16sr"]) < 0.2 * np.max(drift["fp16"])
+    assert dev["fp16sr"] <= 2e-3 and dev["fp16"] <= 2e-3
+
+
+def test_fp16_stochastic_rounding_is_reproducible():
+    """The random bits come from the sites and their densities: two runs from
+    the same start agree bit for bit."""
+    cell = I.make_cell("paper", nx=64, ny=48, g_ab=0.405, bc=1, u_wall=0.01)
+    ra, rb = I.random_fields(64, 48, seed=4)
+    ux, uy = I.couette_velocity(64, 48, 0.01)
+    out = []
+    for _ in range(2):
+        with lattice([cell], "fp16sr", "tiled") as lat:
+            lat.init_fields(ra, rb, ux, uy).step(50)
+            out.append(lat.get_populations())
+    assert np.array_equal(out[0], out[1])
