@@ -188,15 +188,16 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
     const int c0 = svc ? 0 : warp * 32 + 2 * (lane & 15);
     // a pipeline that timed out in an earlier launch of the same batch does not
     // run again (each later launch would otherwise wait out its own bound); the
-    // decision is taken once per CTA
-    if (__syncthreads_or(t == 0 && (*reinterpret_cast<volatile unsigned*>(err) & ERR_TIMEOUT) != 0u)) return;
+    // decision is taken once per CTA, at the barrier that publishes the mbarriers
+    bool stale = false;
     if (t == 0) {
+        stale = (*reinterpret_cast<volatile unsigned*>(err) & ERR_TIMEOUT) != 0u;
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
         fence_mbar_init();
         prefetch_tensormap(&tm_main);
         prefetch_tensormap(&tm_halo);
     }
-    __syncthreads();
+    if (__syncthreads_or(stale)) return;
 
     const long long per_cell = (long long)n_strips * n_seg;
     const long long items = per_cell * g.n_cells;
