@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             Vec2<C>::ld(rho_ring + sp * SS + rr[2] * W + c0 + 2, rho_s[0], rho_s[1]);
             // window column of site o, offset dx: o + 2 + dx
             C jx[2], jy[2], fs[2][9];
-            C Fx[2], Fy[2];
+            C Fx[2], Fy[2], inv_r[2];
             const C fx_body = body_force_x<C>(p, y);
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 jy[o] = (jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16)) * inv_scale;
                 const C rho_t = rho_s[o] + e[1][o + 2];
                 const C inv_rho = fast_div<C>(C(1), rho_t);
+                inv_r[o] = inv_rho;
                 if (Store<T>::shifted)
                     collide_species_shifted<C>(f[o], rho_s[o], rho_bar, v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho,
                                                fx_body * inv_rho, sm, ga, gr, p, fs[o], &Fx[o], &Fy[o], scale);
@@ -397,40 +398,54 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             const int colA[3] = {col_m, x, x + 1};   // site x,   shifts -1, 0, +1
             const int colB[3] = {x, x + 1, col_p2};  // site x+1, shifts -1, 0, +1
             C dpx_site = C(0);
+            if (!(wall_lo || wall_hi)) {
+                // interior row (uniform over the CTA): plain stores, no wall tests
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int cy = q_cy(i), cx = q_cx(i);
-                const bool into_wall = (cy < 0 && wall_lo) || (cy > 0 && wall_hi);
-                if (into_wall) {
-                    C dpa, dpb;
-                    const C uw = cy < 0 ? -p.u_wall : p.u_wall;
-                    // bounce in the f representation (for shifted storage the shift is
-                    // put back first; opposite directions carry equal weights, so the
-                    // same shift is removed again)
-                    const C sh = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
-                    const C ba = bounce<C>(i, fs[0][i] * inv_scale + sh, rho_s[0], uw, &dpa);
-                    const C bb = bounce<C>(i, fs[1][i] * inv_scale + sh, rho_s[1], uw, &dpb);
-                    st_pair<T, C>(dst_s + q_opp(i) * pl + row3[1] + x, (ba - sh) * scale, (bb - sh) * scale, dz);
-                    dpx_site += dpa + dpb;
-                } else if (cx == 0) {
-                    st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
-                } else {
-                    st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
-                    st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                for (int i = 0; i < 9; ++i) {
+                    const int cy = q_cy(i), cx = q_cx(i);
+                    if (cx == 0) {
+                        st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
+                    } else {
+                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
+                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int cy = q_cy(i), cx = q_cx(i);
+                    const bool into_wall = (cy < 0 && wall_lo) || (cy > 0 && wall_hi);
+                    if (into_wall) {
+                        C dpa, dpb;
+                        const C uw = cy < 0 ? -p.u_wall : p.u_wall;
+                        // bounce in the f representation (for shifted storage the shift
+                        // is put back first; opposite directions carry equal weights,
+                        // so the same shift is removed again)
+                        const C sh = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
+                        const C ba = bounce<C>(i, fs[0][i] * inv_scale + sh, rho_s[0], uw, &dpa);
+                        const C bb = bounce<C>(i, fs[1][i] * inv_scale + sh, rho_s[1], uw, &dpb);
+                        st_pair<T, C>(dst_s + q_opp(i) * pl + row3[1] + x, (ba - sh) * scale, (bb - sh) * scale, dz);
+                        dpx_site += dpa + dpb;
+                    } else if (cx == 0) {
+                        st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
+                    } else {
+                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
+                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                    }
                 }
             }
             if (SAMPLE) {
-                C up[2];
-#pragma unroll
-                for (int o = 0; o < 2; ++o) {
-                    const C Fx_t = Fx[o] + __shfl_xor_sync(0xffffffffu, Fx[o], 16);
-                    const C rho_t = rho_s[o] + e[1][o + 2];
-                    up[o] = sp == 0 ? (jx[o] + C(0.5) * Fx_t) / rho_t : C(0);
-                    if (!(rho_t > C(0)) || !isfinite(rho_s[o])) atomicOr(err, ERR_NONFINITE);
-                }
+                // one site per lane: species-A lanes take column x, species-B
+                // lanes column x+1; each lane sends its partner the force the
+                // partner's site needs, so one shuffle gives F_x of both species
+                const C fx_partner = __shfl_xor_sync(0xffffffffu, sp ? Fx[0] : Fx[1], 16);
+                const C Fx_t = (sp ? Fx[1] : Fx[0]) + fx_partner;
+                const C rho_t = sp ? rho_s[1] + e[1][3] : rho_s[0] + e[1][2];
+                const C up = ((sp ? jx[1] : jx[0]) + C(0.5) * Fx_t) * (sp ? inv_r[1] : inv_r[0]);
+                if (!(rho_t > C(0)) || !isfinite(rho_t)) atomicOr(err, ERR_NONFINITE);
                 // lane sums carried as an unevaluated pair (error-free two-sum),
                 // then added in FP64: ~2^-48 relative, no FP64 pipe in the tree
-                const double usum = warp_sum_compensated2(up[0], up[1]);
+                const double usum = warp_sum_compensated(up);
                 double wsum = 0.0;
                 if (wall_lo || wall_hi) wsum = warp_sum_compensated2(dpx_site, C(0));
                 if (lane == 0) {
