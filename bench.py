@@ -40,12 +40,12 @@ UNIT = "MLUPS"
 BYTES_PER_SITE = {"fp32": 144, "fp16": 72, "fp16sr": 72, "fp64": 288}
 FALLBACK_HBM_GBS = 6800.0
 # The FP64 step is bound by the FP64 pipe, not by HBM: its roofline counts the
-# FP64 operations one site update issues (ncu counts of the fused kernel: dadd
-# 140, dmul 60, dfma 142 per site, a dfma counted as two flops) against the
-# nominal FP64 rate, 1.25 TFLOP/s at the 2070 MHz maximum SM clock (152 SMs x
-# 2 FP64 FMA per clock), scaled to the SM clock sampled during the run.
-FP64_FLOPS_PER_SITE = 140 + 60 + 2 * 142
-FP64_TFLOPS_NOMINAL, SM_MAX_MHZ = 1.25, 2070.0
+# FP64 pipe operations one site update issues (ncu counts of the fused kernel:
+# dadd 140, dmul 60, dfma 142 per site; each occupies the pipe once) against the
+# pipe's rate, 152 SMs x 2 FP64 operations per clock (the nominal 1.25 TFLOP/s
+# of FMA at the 2070 MHz maximum SM clock), at the SM clock sampled in the run.
+FP64_OPS_PER_SITE = 140 + 60 + 142
+FP64_OPS_PER_CLOCK, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 
 
 def parse():
@@ -318,12 +318,13 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": t_launch * 1e3,
                 "bytes_per_site_update": BYTES_PER_SITE[args.precision]}
     if args.precision == "fp64":
-        tflops = FP64_FLOPS_PER_SITE * sites / t_launch / 1e12
+        gops = FP64_OPS_PER_SITE * sites / t_launch / 1e9
         sm_mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
-        p64 = FP64_TFLOPS_NOMINAL * sm_mhz / SM_MAX_MHZ
-        roofline = {"bound": "alu", "achieved": tflops, "peak": p64, "unit": "TFLOP/s", "frac": tflops / p64,
-                    "traffic": traffic, "peak_source": "nominal FP64 rate at the sampled SM clock (%.0f MHz)" % sm_mhz,
-                    "flops_per_site_update": FP64_FLOPS_PER_SITE, "mean_launch_ms": t_launch * 1e3,
+        p64 = N_SM * FP64_OPS_PER_CLOCK * sm_mhz * 1e-3
+        roofline = {"bound": "alu", "achieved": gops, "peak": p64, "unit": "G FP64 op/s", "frac": gops / p64,
+                    "traffic": traffic,
+                    "peak_source": "FP64 pipe: 152 SMs x 2 ops per clock at the sampled SM clock (%.0f MHz)" % sm_mhz,
+                    "fp64_ops_per_site_update": FP64_OPS_PER_SITE, "mean_launch_ms": t_launch * 1e3,
                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
 
     # end to end through the C ABI with host buffers
