@@ -40,11 +40,12 @@ UNIT = "MLUPS"
 BYTES_PER_SITE = {"fp32": 144, "fp16": 72, "fp16sr": 72, "fp64": 288}
 FALLBACK_HBM_GBS = 6800.0
 # The FP64 step is bound by the FP64 pipe, not by HBM: its roofline counts the
-# FP64 pipe operations one site update issues (ncu counts of the fused kernel:
-# dadd 140, dmul 60, dfma 142 per site; each occupies the pipe once) against the
-# pipe's rate, 152 SMs x 2 FP64 operations per clock (the nominal 1.25 TFLOP/s
-# of FMA at the 2070 MHz maximum SM clock), at the SM clock sampled in the run.
-FP64_OPS_PER_SITE = 140 + 60 + 142
+# FP64 pipe operations one site update issues (ncu counts of the fused kernel
+# at tau = 1, the workload's: dadd 124, dmul 60, dfma 126 per site; each occupies
+# the pipe once) against the pipe's rate, 152 SMs x 2 FP64 operations per clock
+# (the nominal 1.25 TFLOP/s of FMA at the 2070 MHz maximum SM clock), at the SM
+# clock sampled in the run.
+FP64_OPS_PER_SITE = 124 + 60 + 126
 FP64_OPS_PER_CLOCK, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 
 
@@ -64,6 +65,9 @@ def parse():
     ap.add_argument("--tile", default="", help="TXxTY for the tiled kernel (default: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="only time the FP64 oracle on this host: 1 thread and all cores, at the parity (64^2), "
+                         "bench (1024^2) and precision-study (4096^2) cell sizes; one JSON line, no GPU")
     return ap.parse_args()
 
 
@@ -185,6 +189,37 @@ def cpu_baseline(args, seconds):
     return {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "1 cell of %dx%d (Couette U=%.3g), %d FP64 time steps in %.1f s" %
                       (args.nx, args.ny, cell.u_wall, steps, el)}
+
+
+def cpu_sweep():
+    """The CPU baseline leg at several sizes: the FP64 oracle, as it stands, on
+    one thread and on all host cores.  Each entry runs whole time steps for a
+    bounded time (a 4096^2 step takes seconds); MLUPS are per measured step, so
+    longer runs are extrapolated linearly (the cost per step is constant)."""
+    from oracle import lb as orc
+    from paper_1004_5058_gb300 import inputs as I
+    cores = orc.max_threads()
+    out = {"kind": "oracle", "unit": UNIT, "host_cores": cores, "runs": []}
+    for n, bc, budget in ((64, 0, 5.0), (1024, 1, 12.0), (4096, 1, 25.0)):
+        cell = I.make_cell("paper", nx=n, ny=n, g_ab=0.405, bc=bc, u_wall=1e-3 if bc else 0.0)
+        ra, rb = I.random_fields(n, n, seed=1004)
+        ux, uy = I.couette_velocity(n, n, [1e-3]) if bc else (None, None)
+        for threads in (1, cores):
+            run = orc.Run(cell, ra[0], rb[0], None if ux is None else ux[0], None if uy is None else uy[0],
+                          threads=threads)
+            run.step(1)  # first touch of the arrays
+            t0 = time.perf_counter()
+            steps = 0
+            while True:
+                run.step(1)
+                steps += 1
+                el = time.perf_counter() - t0
+                if el >= budget / 2 or steps >= 1000:
+                    break
+            out["runs"].append({"n": n, "bc": "couette" if bc else "periodic", "threads": threads, "steps": steps,
+                                "seconds": el, "mlups": n * n * steps / el / 1e6})
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -390,6 +425,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.cpu_sweep:
+        return cpu_sweep()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -174,6 +174,26 @@ lb_status lb_sync(lb_handle* h);
 /* Number of time steps taken since the last init (0 for NULL). */
 long long lb_steps_done(const lb_handle* h);
 
+/* Checkpoint and resume of a long run (the paper's runs take 10^6 steps; it
+ * says nothing about restarting them).  lb_save writes the whole state of the
+ * handle to the file `path`: the populations in their storage precision (bit
+ * for bit), the time step, the sampling window with its time sums, and the cell
+ * parameters.  It waits for the handle's work and fails with the pending device
+ * error if there is one (LB_ERR_NONFINITE / LB_ERR_TIMEOUT), LB_ERR_STATE if no
+ * state is loaded, LB_ERR_INVALID if the file cannot be written.
+ * lb_load restores such a file into a handle created with the same number of
+ * cells, lattice size, boundary kind and precision (else LB_ERR_INVALID; the
+ * cell parameters are taken from the file); a run continued after lb_load
+ * equals the run continued after lb_save bit for bit.  A file that is not a
+ * checkpoint, is truncated or fails its checksum gives LB_ERR_INVALID and
+ * leaves the handle without a loaded state.  Both calls are synchronous; the
+ * file is binary in this machine's byte order (format version 1: a 128-byte
+ * header, 14 float64 per cell, the float64 time sums, then the populations
+ * [cell][s][i][y][x] without row padding, FNV-1a 64 checksum of the payload in
+ * the header). */
+lb_status lb_save(lb_handle* h, const char* path);
+lb_status lb_load(lb_handle* h, const char* path);
+
 /* The cudaStream_t the handle enqueues on (the caller's, or the library's own
  * non-blocking stream), for recording events around lb_step. */
 void* lb_stream(const lb_handle* h);

@@ -2,10 +2,12 @@
 // argument validation, device memory, the step loop (with CUDA graphs for
 // chunks of steps), observables and error reporting.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -18,6 +20,12 @@
 #include "lb_internal.h"
 
 using namespace lbhb;
+
+// NVTX range around a C ABI call, for timeline tools (a no-op without one)
+struct Trace {
+    explicit Trace(const char* name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+};
 
 struct lb_handle {
     int n_cells = 0, nx = 0, ny = 0, bc = 0;
@@ -234,6 +242,116 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
     return LB_OK;
 }
 
+// ------------------------------------------------------------ checkpoints --
+// File layout (version 1, this machine's byte order):
+//   header  128 bytes: magic "LBHBCKPT", u32 version, u32 header bytes, i32
+//           n_cells, nx, ny, bc, precision, element bytes, i64 t, start,
+//           every, n_samples, u64 payload bytes, u64 FNV-1a 64 of the payload
+//   payload 14 float64 per cell (lb_cell_params in declaration order), the
+//           time sums of the line profile [cell][ny] and of the wall momenta
+//           [cell][2] (float64), the populations [cell][s][i][y][x] in the
+//           storage precision without row padding
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t n_cells, nx, ny, bc, prec, elem;
+    int64_t t, start, every, n_samples;
+    uint64_t payload_bytes, checksum;
+    unsigned char pad[128 - 8 - 8 - 24 - 32 - 16];
+};
+static_assert(sizeof(CkptHeader) == 128, "checkpoint header layout");
+
+const char kMagic[8] = {'L', 'B', 'H', 'B', 'C', 'K', 'P', 'T'};
+
+// FNV-1a, 64-bit (Fowler, Noll, Vo)
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void* p, size_t n)
+    {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t k = 0; k < n; ++k) h = (h ^ b[k]) * 1099511628211ull;
+    }
+};
+
+void cell_to_doubles(const lb_cell_params& c, double v[14])
+{
+    const double a[14] = {(double)c.nx, (double)c.ny, c.tau, c.rho0, c.g_aa1, c.g_aa2, c.g_bb1,
+                          c.g_bb2, c.g_ab, c.u_wall, c.f0, c.rho_bar_a, c.rho_bar_b, (double)c.bc};
+    for (int k = 0; k < 14; ++k) v[k] = a[k];
+}
+
+// false if the integer fields are not small whole numbers
+bool cell_from_doubles(const double v[14], lb_cell_params* out)
+{
+    for (int k : {0, 1, 13})
+        if (!(v[k] >= 0.0 && v[k] <= 2147483647.0) || v[k] != std::floor(v[k])) return false;
+    lb_cell_params& c = *out;
+    c.nx = (int)v[0];
+    c.ny = (int)v[1];
+    c.tau = v[2];
+    c.rho0 = v[3];
+    c.g_aa1 = v[4];
+    c.g_aa2 = v[5];
+    c.g_bb1 = v[6];
+    c.g_bb2 = v[7];
+    c.g_ab = v[8];
+    c.u_wall = v[9];
+    c.f0 = v[10];
+    c.rho_bar_a = v[11];
+    c.rho_bar_b = v[12];
+    c.bc = (lb_bc)(int)v[13];
+    return true;
+}
+
+struct File {
+    FILE* f = nullptr;
+    ~File()
+    {
+        if (f) fclose(f);
+    }
+};
+
+}  // namespace
+
+// Cells a handle can run: one shape and boundary kind, tau > 1/2, rho0 > 0,
+// finite couplings.  On failure writes the reason to why.
+static bool cells_valid(const lb_cell_params* cells, int n_cells, char* why, size_t n)
+{
+    const lb_cell_params& c0 = cells[0];
+    for (int c = 0; c < n_cells; ++c) {
+        const lb_cell_params& p = cells[c];
+        if (p.nx != c0.nx || p.ny != c0.ny || p.bc != c0.bc) {
+            snprintf(why, n, "cell %d differs in nx/ny/bc from cell 0", c);
+            return false;
+        }
+        if (p.nx < 5 || p.ny < 5 || (long long)p.nx * p.ny > (1LL << 31)) {
+            snprintf(why, n, "lattice %dx%d out of range (5 .. 2^31 sites)", p.nx, p.ny);
+            return false;
+        }
+        if (!(p.tau > 0.5) || !std::isfinite(p.tau)) {
+            snprintf(why, n, "cell %d tau=%g must exceed 1/2", c, p.tau);
+            return false;
+        }
+        if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0)) {
+            snprintf(why, n, "cell %d rho0=%g must be positive", c, p.rho0);
+            return false;
+        }
+        if (p.bc != LB_BC_PERIODIC && p.bc != LB_BC_COUETTE) {
+            snprintf(why, n, "unknown boundary %d", p.bc);
+            return false;
+        }
+        const double v[] = {p.g_aa1, p.g_aa2, p.g_bb1, p.g_bb2, p.g_ab, p.u_wall, p.f0, p.rho_bar_a, p.rho_bar_b};
+        for (double x : v)
+            if (!std::isfinite(x)) {
+                snprintf(why, n, "cell %d has a non-finite parameter", c);
+                return false;
+            }
+    }
+    return true;
+}
+
 extern "C" {
 
 lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec, void* cuda_stream,
@@ -244,23 +362,9 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
     if (!cells || n_cells < 1) return fail(nullptr, LB_ERR_INVALID, "lb_create: need n_cells >= 1 cells");
     if (prec != LB_FP32 && prec != LB_FP16_SHIFTED && prec != LB_FP64 && prec != LB_FP16_SHIFTED_SR)
         return fail(nullptr, LB_ERR_INVALID, "lb_create: unknown precision %d", (int)prec);
+    char why[256];
+    if (!cells_valid(cells, n_cells, why, sizeof why)) return fail(nullptr, LB_ERR_INVALID, "lb_create: %s", why);
     const lb_cell_params& c0 = cells[0];
-    for (int c = 0; c < n_cells; ++c) {
-        const lb_cell_params& p = cells[c];
-        if (p.nx != c0.nx || p.ny != c0.ny || p.bc != c0.bc)
-            return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d differs in nx/ny/bc from cell 0", c);
-        if (p.nx < 5 || p.ny < 5 || (long long)p.nx * p.ny > (1LL << 31))
-            return fail(nullptr, LB_ERR_INVALID, "lb_create: lattice %dx%d out of range (5 .. 2^31 sites)", p.nx, p.ny);
-        if (!(p.tau > 0.5) || !std::isfinite(p.tau))
-            return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d tau=%g must exceed 1/2", c, p.tau);
-        if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0))
-            return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d rho0=%g must be positive", c, p.rho0);
-        if (p.bc != LB_BC_PERIODIC && p.bc != LB_BC_COUETTE)
-            return fail(nullptr, LB_ERR_INVALID, "lb_create: unknown boundary %d", p.bc);
-        const double v[] = {p.g_aa1, p.g_aa2, p.g_bb1, p.g_bb2, p.g_ab, p.u_wall, p.f0, p.rho_bar_a, p.rho_bar_b};
-        for (double x : v)
-            if (!std::isfinite(x)) return fail(nullptr, LB_ERR_INVALID, "lb_create: cell %d has a non-finite parameter", c);
-    }
     lb_handle* h = new (std::nothrow) lb_handle();
     if (!h) return fail(nullptr, LB_ERR_NOMEM, "lb_create: out of host memory");
     h->n_cells = n_cells;
@@ -346,6 +450,7 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
 lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b, const double* ux,
                          const double* uy)
 {
+    Trace trace("lb_init_fields");
     if (!h) return LB_ERR_INVALID;
     if (!rho_a || !rho_b) return fail(h, LB_ERR_INVALID, "lb_init_fields: rho_a and rho_b are required");
     CK(h, cudaSetDevice(h->device));
@@ -375,6 +480,7 @@ lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b,
 
 lb_status lb_set_populations(lb_handle* h, const double* f)
 {
+    Trace trace("lb_set_populations");
     if (!h) return LB_ERR_INVALID;
     if (!f) return fail(h, LB_ERR_INVALID, "lb_set_populations: f is NULL");
     CK(h, cudaSetDevice(h->device));
@@ -400,6 +506,7 @@ lb_status lb_set_populations(lb_handle* h, const double* f)
 
 lb_status lb_get_populations(lb_handle* h, double* f)
 {
+    Trace trace("lb_get_populations");
     if (!h) return LB_ERR_INVALID;
     if (!f) return fail(h, LB_ERR_INVALID, "lb_get_populations: f is NULL");
     if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_get_populations: no state loaded");
@@ -492,6 +599,7 @@ static cudaError_t run_chunk(lb_handle* h, int src, int steps, bool sample_last,
 
 lb_status lb_step(lb_handle* h, long long n_steps)
 {
+    Trace trace("lb_step");
     if (!h) return LB_ERR_INVALID;
     if (n_steps < 0) return fail(h, LB_ERR_INVALID, "lb_step: n_steps < 0");
     if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_step: no state loaded (call lb_init_fields)");
@@ -575,6 +683,7 @@ static lb_status read_acc(lb_handle* h, std::vector<double>& prof, std::vector<d
 
 lb_status lb_shear_stress(lb_handle* h, double* sigma_xy, double* shear_rate, double* shear_bulk)
 {
+    Trace trace("lb_shear_stress");
     if (!h) return LB_ERR_INVALID;
     if (!sigma_xy || !shear_rate) return fail(h, LB_ERR_INVALID, "lb_shear_stress: outputs are NULL");
     std::vector<double> prof, wall;
@@ -618,6 +727,7 @@ lb_status lb_get_profile(lb_handle* h, double* ubar, long long* n_samples)
 
 lb_status lb_get_fields(lb_handle* h, double* rho_a, double* rho_b, double* ux, double* uy)
 {
+    Trace trace("lb_get_fields");
     if (!h) return LB_ERR_INVALID;
     if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_get_fields: no state loaded");
     CK(h, cudaSetDevice(h->device));
@@ -638,6 +748,7 @@ lb_status lb_get_fields(lb_handle* h, double* rho_a, double* rho_b, double* ux, 
 
 lb_status lb_reductions(lb_handle* h, double* mass_ab, double* momentum_xy)
 {
+    Trace trace("lb_reductions");
     if (!h) return LB_ERR_INVALID;
     if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_reductions: no state loaded");
     CK(h, cudaSetDevice(h->device));
@@ -683,6 +794,7 @@ lb_status lb_get_kernel(const lb_handle* h, lb_kernel* kernel, int* tile_x, int*
 
 lb_status lb_autotune(lb_handle* h, const char* cache_path)
 {
+    Trace trace("lb_autotune");
     if (!h) return LB_ERR_INVALID;
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -781,5 +893,151 @@ const char* lb_last_error(const lb_handle* h)
 }
 
 void lb_destroy(lb_handle* h) { release(h); }
+
+
+lb_status lb_save(lb_handle* h, const char* path)
+{
+    Trace trace("lb_save");
+    if (!h) return LB_ERR_INVALID;
+    if (!path) return fail(h, LB_ERR_INVALID, "lb_save: path is NULL");
+    if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_save: no state loaded");
+    lb_status st = sync_and_check(h);
+    if (st != LB_OK) return st;
+    std::vector<double> prof, wall;
+    st = read_acc(h, prof, wall);
+    if (st != LB_OK) return st;
+    File out;
+    out.f = fopen(path, "wb");
+    if (!out.f) return fail(h, LB_ERR_INVALID, "lb_save: cannot open %s for writing", path);
+    CkptHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, kMagic, 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof hd;
+    hd.n_cells = h->n_cells;
+    hd.nx = h->nx;
+    hd.ny = h->ny;
+    hd.bc = h->bc;
+    hd.prec = (int32_t)h->prec;
+    hd.elem = h->elem;
+    hd.t = h->t;
+    hd.start = h->start;
+    hd.every = h->every;
+    hd.n_samples = h->n_samples;
+    bool ok = fwrite(&hd, sizeof hd, 1, out.f) == 1;  // rewritten with the checksum at the end
+    Fnv sum;
+    uint64_t bytes = 0;
+    auto put = [&](const void* p, size_t n) {
+        if (!ok) return;
+        ok = fwrite(p, 1, n, out.f) == n;
+        sum.add(p, n);
+        bytes += n;
+    };
+    for (int c = 0; c < h->n_cells; ++c) {
+        double v[14];
+        cell_to_doubles(h->cells[c], v);
+        put(v, sizeof v);
+    }
+    put(prof.data(), sizeof(double) * prof.size());
+    put(wall.data(), sizeof(double) * wall.size());
+    const size_t row = (size_t)h->nx * h->elem, cell_bytes = row * 18 * h->ny;
+    std::vector<unsigned char> buf(cell_bytes);
+    for (int c = 0; c < h->n_cells && ok; ++c) {
+        const unsigned char* src = (const unsigned char*)h->f[h->cur] + (size_t)c * h->g.cellstride * h->elem;
+        CK(h, cudaMemcpy2D(buf.data(), row, src, (size_t)h->g.pitch * h->elem, row, (size_t)18 * h->ny,
+                           cudaMemcpyDeviceToHost));
+        put(buf.data(), cell_bytes);
+    }
+    hd.payload_bytes = bytes;
+    hd.checksum = sum.h;
+    if (ok) ok = fseek(out.f, 0, SEEK_SET) == 0 && fwrite(&hd, sizeof hd, 1, out.f) == 1;
+    if (ok) ok = fclose(out.f) == 0;
+    out.f = nullptr;
+    if (!ok) return fail(h, LB_ERR_INVALID, "lb_save: writing %s failed", path);
+    return LB_OK;
+}
+
+lb_status lb_load(lb_handle* h, const char* path)
+{
+    Trace trace("lb_load");
+    if (!h) return LB_ERR_INVALID;
+    if (!path) return fail(h, LB_ERR_INVALID, "lb_load: path is NULL");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->batch_pending = false;
+    File in;
+    in.f = fopen(path, "rb");
+    if (!in.f) return fail(h, LB_ERR_INVALID, "lb_load: cannot open %s", path);
+    CkptHeader hd;
+    if (fread(&hd, sizeof hd, 1, in.f) != 1 || memcmp(hd.magic, kMagic, 8) != 0)
+        return fail(h, LB_ERR_INVALID, "lb_load: %s is not a checkpoint", path);
+    if (hd.version != 1 || hd.header_bytes != sizeof hd)
+        return fail(h, LB_ERR_INVALID, "lb_load: checkpoint version %u not supported", hd.version);
+    if (hd.n_cells != h->n_cells || hd.nx != h->nx || hd.ny != h->ny || hd.bc != h->bc ||
+        hd.prec != (int32_t)h->prec || hd.elem != h->elem)
+        return fail(h, LB_ERR_INVALID,
+                    "lb_load: checkpoint holds %d cells of %dx%d (bc %d, precision %d), the handle %d of %dx%d "
+                    "(bc %d, precision %d)", hd.n_cells, hd.nx, hd.ny, hd.bc, hd.prec, h->n_cells, h->nx, h->ny,
+                    h->bc, (int)h->prec);
+    if (hd.t < 0 || hd.start < 0 || hd.every < 0 || hd.n_samples < 0)
+        return fail(h, LB_ERR_INVALID, "lb_load: negative counters in %s", path);
+    // from here on the handle's state is being replaced: it only counts as
+    // loaded once everything has been read and checked
+    h->initialised = false;
+    Fnv sum;
+    uint64_t bytes = 0;
+    bool ok = true;
+    auto get = [&](void* p, size_t n) {
+        if (!ok) return;
+        ok = fread(p, 1, n, in.f) == n;
+        if (ok) {
+            sum.add(p, n);
+            bytes += n;
+        }
+    };
+    std::vector<lb_cell_params> cells(h->n_cells);
+    bool cells_ok = true;
+    for (int c = 0; c < h->n_cells; ++c) {
+        double v[14];
+        get(v, sizeof v);
+        if (ok) cells_ok = cell_from_doubles(v, &cells[c]) && cells_ok;
+    }
+    std::vector<double> prof((size_t)h->n_cells * h->ny), wall((size_t)h->n_cells * 2);
+    get(prof.data(), sizeof(double) * prof.size());
+    get(wall.data(), sizeof(double) * wall.size());
+    const size_t row = (size_t)h->nx * h->elem, cell_bytes = row * 18 * h->ny;
+    std::vector<unsigned char> buf(cell_bytes);
+    for (int c = 0; c < h->n_cells && ok; ++c) {
+        get(buf.data(), cell_bytes);
+        if (!ok) break;
+        unsigned char* dst = (unsigned char*)h->f[0] + (size_t)c * h->g.cellstride * h->elem;
+        CK(h, cudaMemcpy2D(dst, (size_t)h->g.pitch * h->elem, buf.data(), row, row, (size_t)18 * h->ny,
+                           cudaMemcpyHostToDevice));
+    }
+    unsigned char extra;
+    if (!ok || bytes != hd.payload_bytes || fread(&extra, 1, 1, in.f) == 1)
+        return fail(h, LB_ERR_INVALID, "lb_load: %s is truncated or has a different size than recorded", path);
+    if (sum.h != hd.checksum) return fail(h, LB_ERR_INVALID, "lb_load: checksum mismatch in %s", path);
+    char why[256] = "lattice size or boundary differs from the handle's";
+    if (!cells_ok || !cells_valid(cells.data(), h->n_cells, why, sizeof why) || cells[0].nx != h->nx ||
+        cells[0].ny != h->ny || cells[0].bc != h->bc)
+        return fail(h, LB_ERR_INVALID, "lb_load: cell parameters in %s: %s", path, cells_ok ? why : "malformed");
+    std::vector<CellDev> dc(h->n_cells);
+    for (int c = 0; c < h->n_cells; ++c) dc[c] = to_dev(cells[c]);
+    CK(h, cudaMemcpy(h->d_cells, dc.data(), sizeof(CellDev) * h->n_cells, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->acc_prof, prof.data(), sizeof(double) * prof.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->acc_wall, wall.data(), sizeof(double) * wall.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
+    h->h_err[0] = 0;
+    h->cells = cells;
+    h->cur = 0;
+    h->t = hd.t;
+    h->start = hd.start;
+    h->every = hd.every;
+    h->n_samples = hd.n_samples;
+    h->faulted = false;
+    h->initialised = true;
+    return LB_OK;
+}
 
 }  // extern "C"

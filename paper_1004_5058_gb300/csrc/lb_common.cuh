@@ -246,7 +246,9 @@ __device__ inline Sums<C> stencil_sums(const C d[12], const C e[4])
 // vanishing species density.  Closing the rest population on rho_s keeps the
 // rounded weights (sum of float(w_i) = 1 + 7.5e-9) from biasing the mass.
 // *Fx, *Fy receive F_s (for the force-corrected velocity of the observables).
-template <class C>
+// UNIT: tau = 1 (omega = 1, the paper's choice for all its runs), where the BGK
+// update is f*_i = f^eq_i exactly and f_i only enters through the moments.
+template <class C, bool UNIT = false>
 __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C uy, C ax, const Sums<C>& sm, C ga,
                                        C gr, const ParamSet<C>& p, C fs[9], C* Fx, C* Fy)
 {
@@ -270,8 +272,13 @@ __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C u
         const C a = wr * (base + C(4.5) * cu[k] * cu[k]);
         const C b = (C(3) * wr) * cu[k];
         const int i = lo[k], j = hi[k];
-        fs[i] = f[i] + omega * ((a + b) - f[i]);
-        fs[j] = f[j] + omega * ((a - b) - f[j]);
+        if constexpr (UNIT) {
+            fs[i] = a + b;
+            fs[j] = a - b;
+        } else {
+            fs[i] = f[i] + omega * ((a + b) - f[i]);
+            fs[j] = f[j] + omega * ((a - b) - f[j]);
+        }
         moving += fs[i] + fs[j];
     }
     fs[0] = rho_s - moving;
@@ -286,7 +293,7 @@ __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C u
 // carry equal weights).
 // With scale != 1 the populations are scale * g (FP16 storage with stochastic
 // rounding) and so are the results; rho_s, psi_s, u and the forces are not scaled.
-template <class C>
+template <class C, bool UNIT = false>
 __device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar, C psi_s, C ux, C uy, C ax,
                                                const Sums<C>& sm, C ga, C gr, const ParamSet<C>& p, C gs[9],
                                                C* Fx, C* Fy, C scale = C(1))
@@ -311,8 +318,13 @@ __device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar,
         const C a = w * (dr + rs * (C(4.5) * cu[k] * cu[k] - usq));
         const C b = (C(3) * w * rs) * cu[k];
         const int i = lo[k], j = hi[k];
-        gs[i] = g[i] + omega * ((a + b) - g[i]);
-        gs[j] = g[j] + omega * ((a - b) - g[j]);
+        if constexpr (UNIT) {
+            gs[i] = a + b;
+            gs[j] = a - b;
+        } else {
+            gs[i] = g[i] + omega * ((a + b) - g[i]);
+            gs[j] = g[j] + omega * ((a - b) - g[j]);
+        }
         moving += gs[i] + gs[j];
     }
     gs[0] = dr - moving;
@@ -342,9 +354,14 @@ __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi
     const C ax = fx_body * inv_rho;
     C Fx[2], Fy[2];
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-        collide_species<C>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p, out.fs[s], &Fx[s],
-                           &Fy[s]);
+    for (int s = 0; s < 2; ++s) {
+        if (p.omega == C(1))
+            collide_species<C, true>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p, out.fs[s],
+                                     &Fx[s], &Fy[s]);
+        else
+            collide_species<C, false>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p, out.fs[s],
+                                      &Fx[s], &Fy[s]);
+    }
     out.Fx = Fx[0] + Fx[1];
     out.Fy = Fy[0] + Fy[1];
 }

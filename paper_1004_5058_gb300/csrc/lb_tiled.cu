@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         p.f0 = pg.f0;
         p.two_over_ny = pg.two_over_ny;
         const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
+        const bool unit_omega = p.omega == C(1);  // tau = 1: f* = f^eq (uniform over the CTA)
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
         // destination columns of the two sites x, x+1 shifted by -1/0/+1 (periodic)
         const int x = x0 + c0;
@@ -376,12 +377,22 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 const C rho_t = rho_s[o] + e[1][o + 2];
                 const C inv_rho = fast_div<C>(C(1), rho_t);
                 inv_r[o] = inv_rho;
-                if (Store<T>::shifted)
-                    collide_species_shifted<C>(f[o], rho_s[o], rho_bar, v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho,
-                                               fx_body * inv_rho, sm, ga, gr, p, fs[o], &Fx[o], &Fy[o], scale);
-                else
-                    collide_species<C>(f[o], rho_s[o], v[2][o + 2], jx[o] * inv_rho, jy[o] * inv_rho, fx_body * inv_rho,
-                                       sm, ga, gr, p, fs[o], &Fx[o], &Fy[o]);
+                const C ux = jx[o] * inv_rho, uy = jy[o] * inv_rho, ax = fx_body * inv_rho;
+                if (Store<T>::shifted) {
+                    if (unit_omega)
+                        collide_species_shifted<C, true>(f[o], rho_s[o], rho_bar, v[2][o + 2], ux, uy, ax, sm, ga, gr,
+                                                         p, fs[o], &Fx[o], &Fy[o], scale);
+                    else
+                        collide_species_shifted<C, false>(f[o], rho_s[o], rho_bar, v[2][o + 2], ux, uy, ax, sm, ga,
+                                                          gr, p, fs[o], &Fx[o], &Fy[o], scale);
+                } else {
+                    if (unit_omega)
+                        collide_species<C, true>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, p, fs[o], &Fx[o],
+                                                 &Fy[o]);
+                    else
+                        collide_species<C, false>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, p, fs[o],
+                                                  &Fx[o], &Fy[o]);
+                }
             }
 
             // stochastic rounding: one stream per thread and row, seeded from the

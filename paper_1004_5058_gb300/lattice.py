@@ -90,6 +90,18 @@ class Lattice:
         self._chk(self.lib.lb_set_populations(self.h, _dp(f)))
         return self
 
+    def save(self, path: str):
+        """Checkpoint of the whole state (lb_save): populations bit for bit, time
+        step, sampling window and time sums, cell parameters."""
+        self._chk(self.lib.lb_save(self.h, str(path).encode()))
+        return self
+
+    def load(self, path: str):
+        """Resume from a checkpoint written by save() on a handle of the same
+        shape and precision (lb_load)."""
+        self._chk(self.lib.lb_load(self.h, str(path).encode()))
+        return self
+
     def get_populations(self):
         f = np.empty((self.n_cells, 2, 9, self.ny, self.nx))
         self._chk(self.lib.lb_get_populations(self.h, _dp(f)))
