@@ -80,5 +80,6 @@ def test_noalloc_rejects_what_it_cannot_do(env):
     assert lib.lb_reductions_noalloc(p, L.LB_FP32, 4096, 4096, 4096, 17, o, None) == L.LB_ERR_INVALID
     assert b"scratch" in lib.lb_last_error(None)
     assert lib.lb_reductions_noalloc(p, L.LB_FP16_SHIFTED, 8, 8, 8, 1, o, None) == L.LB_ERR_UNSUPPORTED
+    assert lib.lb_reductions_noalloc(p, L.LB_FP16_SHIFTED_SR, 8, 8, 8, 1, o, None) == L.LB_ERR_UNSUPPORTED
     assert lib.lb_reductions_noalloc(None, L.LB_FP32, 8, 8, 8, 1, o, None) == L.LB_ERR_INVALID
     assert lib.lb_reductions_noalloc(p, L.LB_FP32, 8, 8, 4, 1, o, None) == L.LB_ERR_INVALID  # pitch < nx
