@@ -48,11 +48,27 @@ def _digest():
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
+    """Builds liblbhb.so unless it is current.  Processes that build at the same
+    time (one per GPU under torchrun) take turns on a lock file; a process that
+    waited finds the library current and returns."""
     stamp = OUT + ".sha"
     dig = _digest()
-    if not force and os.path.exists(OUT) and os.path.exists(stamp) and open(stamp).read().strip() == dig:
+
+    def current():
+        return os.path.exists(OUT) and os.path.exists(stamp) and open(stamp).read().strip() == dig
+
+    if not force and current():
         return OUT
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    with open(os.path.join(BUILD, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and current():
+            return OUT
+        return _build(stamp, dig, verbose)
+
+
+def _build(stamp: str, dig: str, verbose: bool) -> str:
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
               "--expt-relaxed-constexpr"]
