@@ -167,6 +167,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def workload_config(args):
+    """The workload keys both arms report (the GPU arm adds its kernel and tile)."""
+    n_cells, nx, ny, chunk = args.cells, args.nx, args.ny, args.chunk
+    bytes_pop = 2 * n_cells * nx * ny * BYTES_PER_SITE[args.precision] / 2
+    return {"workload": "couette batch: %d cells of %dx%d, %s, %d time steps per step, FP64 "
+                        "reductions every %d" % (n_cells, nx, ny, args.precision.upper(), chunk, args.every),
+            "cells": n_cells, "nx": nx, "ny": ny, "lattice_steps_per_step": chunk,
+            "sampling_every": args.every, "precision": args.precision,
+            "couplings": "paper footnote, G_AB=0.405", "u_wall": "1e-4..1e-2 log",
+            "l2": "inputs larger than L2 (%.2f GB populations, ping-pong)" % (bytes_pop / 1e9)}
+
+
 def cpu_baseline(args, seconds):
     """The FP64 oracle, as it stands, on this host's cores: one cell of the
     workload, as many time steps as fit in about `seconds`."""
@@ -255,8 +267,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
         "warmup": W, "ms_per_step": 1e3 * tot_t / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "couette %dx%d x %d cells, FP64 oracle on host cores (1 cell sampled)" %
-                               (args.nx, args.ny, args.cells), "nx": args.nx, "ny": args.ny, "cells": args.cells},
+        "config": workload_config(args),
         "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
                          "sample": "1 cell of %dx%d, %d FP64 time steps in %.1f s over %d timed steps" %
                                    (args.nx, args.ny, tot_n, tot_t, K)},
@@ -395,13 +406,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "fp16sr": "f16-storage/f32",
                                        "fp64": "f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": "couette batch: %d cells of %dx%d, %s, %d time steps per step, FP64 "
-                               "reductions every %d" % (n_cells, nx, ny, args.precision.upper(), chunk, args.every),
-                   "cells": n_cells, "nx": nx, "ny": ny, "lattice_steps_per_step": chunk,
-                   "sampling_every": args.every, "precision": args.precision, "kernel": kernel,
-                   "tile": [tx, ty], "couplings": "paper footnote, G_AB=0.405", "u_wall": "1e-4..1e-2 log",
-                   "l2": "inputs larger than L2 (%.2f GB populations, ping-pong)" %
-                         (2 * sites * BYTES_PER_SITE[args.precision] / 2 / 1e9)},
+        "config": dict(workload_config(args), kernel=kernel, tile=[tx, ty]),
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lattice_steps_per_step": chunk},
