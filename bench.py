@@ -302,8 +302,8 @@ def run_ours(args):
         tx, ty = (int(v) for v in args.tile.split("x")) if args.tile else (0, 0)
         lat.set_kernel(args.kernel if args.kernel != "auto" else "tiled", tx, ty)
     else:
-        lat.autotune(os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
-                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        cache_dir = os.path.join(ROOT, "paper_1004_5058_gb300", "_build")  # the library's build folder
+        lat.autotune(os.path.join(cache_dir, "autotune_cache.txt") if os.path.isdir(cache_dir) else None)
     kernel, tx, ty = lat.kernel()
     stream = torch.cuda.ExternalStream(lat.stream_ptr)
     lat.set_sampling(0, args.every)

@@ -6,7 +6,7 @@
  * FP32 master weights.  The paper has no learned component: the network stands
  * in for repeated lattice Boltzmann runs of the Herschel-Bulkley flow curve
  * (sigma = sigma_Y + A S^beta, section "Numerical Results"), and the lattice
- * Boltzmann update stays the fallback and the judge of its error.
+ * Boltzmann update stays the fallback and the reference for its error.
  *
  * Conventions: status codes are lb_status (lbhb.h).  x, targets and outputs
  * are DEVICE float32 buffers of the current device, caller-owned, rows of one

@@ -4,7 +4,10 @@
 
 namespace lbhb {
 
-// f_is = f^eq_is(rho_s, u): w_i rho_s (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u^2), cs^2 = 1/3.
+// f_is = f^eq_is(rho_s, u): w_i rho_s (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u^2), cs^2 = 1/3,
+// evaluated in the compute type of the storage (FP32 for FP32 and FP16 storage:
+// the FP64 pipe would make this initialisation ten times slower than its
+// memory traffic), the +-c pairs together as in the collision.
 // src: device float64 [cell][4][ny][nx] = rho_A, rho_B, u_x, u_y.
 template <class T>
 __global__ void equilibrium_kernel(const double* __restrict__ src, T* __restrict__ f, Geom g,
@@ -15,14 +18,24 @@ __global__ void equilibrium_kernel(const double* __restrict__ src, T* __restrict
     if (x >= g.nx) return;
     const long long n = (long long)g.nx * g.ny, k = (long long)y * g.nx + x;
     const double* s0 = src + (long long)cell * 4 * n;
-    const double ux = s0[2 * n + k], uy = s0[3 * n + k], usq = ux * ux + uy * uy;
+    const C ux = C(s0[2 * n + k]), uy = C(s0[3 * n + k]);
+    const C base = C(1) - C(1.5) * (ux * ux + uy * uy);
+    const C cu[4] = {ux, uy, ux + uy, uy - ux};  // c.u for i = 1, 2, 5, 6
+    const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
+    const ParamSet<C>& p = params<C>(cells[cell]);
+#pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const double r = s0[s * n + k];
-        for (int i = 0; i < 9; ++i) {
-            const double cu = q_cx(i) * ux + q_cy(i) * uy;
-            const double feq = q_w(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-            const C sh = Store<T>::shifted ? pop_shift<C>(i, params<C>(cells[cell]), s) : C(0);
-            Store<T>::st(f, fidx(g, cell, s * 9 + i, y, x), C(feq), sh);
+        const C r = C(s0[s * n + k]);
+        const C sh0 = Store<T>::shifted ? pop_shift<C>(0, p, s) : C(0);
+        Store<T>::st(f, fidx(g, cell, s * 9, y, x), C(q_w(0)) * r * base, sh0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const C wr = C(q_w(lo[q])) * r;
+            const C a = wr * (base + C(4.5) * cu[q] * cu[q]), b = (C(3) * wr) * cu[q];
+            const C shi = Store<T>::shifted ? pop_shift<C>(lo[q], p, s) : C(0);
+            const C sho = Store<T>::shifted ? pop_shift<C>(hi[q], p, s) : C(0);
+            Store<T>::st(f, fidx(g, cell, s * 9 + lo[q], y, x), a + b, shi);
+            Store<T>::st(f, fidx(g, cell, s * 9 + hi[q], y, x), a - b, sho);
         }
     }
 }

@@ -242,7 +242,7 @@ def kolmogorov_rho0_sweep(L: int = 512, steps: int = 1000000, u0: float = 0.1,
 
 def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L: int = 64, steps: int = 20000,
                     epochs: int = 300, batch: int = 256, lr: float = 2e-3, seed: int = 11):
-    """Train on n_train x n_speeds LB points, judge on n_test x n_speeds held-out points."""
+    """Train on n_train x n_speeds LB points, score on n_test x n_speeds held-out points."""
     import time as _t
     import torch
     from . import surrogate as S

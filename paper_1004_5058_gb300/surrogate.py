@@ -1,5 +1,5 @@
 """Learned surrogate of the Herschel-Bulkley flow curve, with the lattice
-Boltzmann update as its fallback and judge.
+Boltzmann update as its fallback and its reference.
 
 The network (include/lbhb_mlp.h) maps (log S, G_AA1, G_AA2, G_AB, tau) to the
 wall stress sigma_xy and a yielded/arrested logit.  It is trained by the
