@@ -289,10 +289,37 @@ def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L:
             "gain_queries_per_s": (4096 / t_serve) / (len(x) / t_data)}
 
 
+def couette_flow_curve(n: int = 1024, n_speeds: int = 8, steps: int = 200000, every: int = 10, g_ab: float = 0.405,
+                       precision: str = "fp32", seed: int = 1004):
+    """The benchmark's configuration run to its end: n_speeds Couette cells of
+    n x n, wall speeds U = 10^(-4 + 2k/(n_speeds-1)), linear-profile start, the
+    second half of the steps sampled; per cell the wall stress and shear rate,
+    and the Herschel-Bulkley fit of the curve."""
+    speeds = I.log_spaced(1e-4, 1e-2, n_speeds)
+    cells = [I.make_cell("paper", nx=n, ny=n, g_ab=g_ab, bc=1, u_wall=u) for u in speeds]
+    ra, rb = I.random_fields(n, n, n_cells=n_speeds, seed=seed)
+    ux, uy = I.couette_velocity(n, n, speeds, n_cells=n_speeds)
+    with Lattice(cells, precision) as lat:
+        lat.init_fields(ra, rb, ux, uy)
+        kern = lat.autotune()
+        lat.init_fields(ra, rb, ux, uy).set_sampling(steps // 2, every)
+        _, dt = _cuda_time(lambda: lat.step(steps).sync())
+        sigma, S, Sb = lat.shear_stress()
+        ub, ns = lat.profile()
+    ok = np.isfinite(S) & (S > 0) & np.isfinite(sigma) & (sigma > 0)
+    return {"n": n, "steps": steps, "cells": n_speeds, "precision": precision, "g_ab": g_ab, "kernel": kern,
+            "seconds": dt, "mlups": n_speeds * n * n * steps / dt / 1e6, "points_per_s": n_speeds / dt,
+            "samples": ns, "u_wall": list(speeds), "sigma_xy": [float(v) for v in sigma],
+            "shear_rate": [float(v) for v in S], "shear_bulk": [float(v) for v in Sb],
+            "nominal_rate": [2.0 * u / n for u in speeds],
+            "hb_fit": hb_fit(S[ok], sigma[ok]) if ok.sum() >= 3 else None}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
-                                      "surrogate", "kolmogorov", "kolmogorov_rho0"])
+                                      "flow_curve_long", "couette_1024", "surrogate", "kolmogorov",
+                                      "kolmogorov_rho0"])
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
@@ -304,6 +331,10 @@ def main():
         r = kolmogorov(L=128, steps=20000, u0s=(0.05, 0.1)) if a.quick else kolmogorov()
     elif a.study == "kolmogorov_rho0":
         r = kolmogorov_rho0_sweep(L=128, steps=20000) if a.quick else kolmogorov_rho0_sweep()
+    elif a.study == "couette_1024":  # the benchmark's 8 cells of 1024^2 for the full 2e5 steps
+        r = couette_flow_curve(n=128, steps=4000) if a.quick else couette_flow_curve()
+    elif a.study == "flow_curve_long":  # the batched 64 x 512^2 cells for 1e6 steps (steady state)
+        r = flow_curve(L=128, steps=4000, n_speeds=4) if a.quick else flow_curve(steps=1000000, every=100)
     elif a.study == "surrogate":
         r = surrogate_study(n_train=48, n_test=12, n_speeds=8, L=32, steps=3000) if a.quick else surrogate_study()
     else:
