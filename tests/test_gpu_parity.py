@@ -333,3 +333,28 @@ def test_fp16_stochastic_rounding_is_reproducible():
             lat.init_fields(ra, rb, ux, uy).step(50)
             out.append(lat.get_populations())
     assert np.array_equal(out[0], out[1])
+
+
+# ------------------------------------------------------- initial state --
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,rel,absol", [("fp64", 1e-15, 0.0), ("fp32", 4e-7, 0.0), ("fp16", 0.0, 2.0 ** -11),
+                                             ("fp16sr", 0.0, 2.0 ** -11)])
+def test_initial_equilibrium(kernel, prec, rel, absol):
+    """lb_init_fields stores f^eq(rho_s, u): FP64 to round-off, FP32 within a few
+    ulp (it is evaluated in FP32), FP16 within one rounding of g = f - w rho_bar
+    (round to nearest there in both FP16 modes)."""
+    from oracle import lb as orc
+    cell = I.make_cell("paper", nx=64, ny=40, g_ab=0.405, bc=1, u_wall=0.03)
+    ra, rb = I.random_fields(64, 40, seed=17)
+    ux, uy = I.couette_velocity(64, 40, 0.03)
+    uy = 0.01 * np.sin(np.arange(64 * 40).reshape(1, 40, 64))
+    with lattice([cell], prec, kernel) as lat:
+        lat.init_fields(ra, rb, ux, uy)
+        got = lat.get_populations()[0]
+    ref = orc.equilibrium(cell, ra[0], rb[0], ux[0], uy[0])
+    if absol:
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[None, :, None, None]
+        g = np.abs(ref - w * np.array([cell.rho_bar_a, cell.rho_bar_b])[:, None, None, None])
+        assert np.all(np.abs(got - ref) <= absol * g + 2e-7)
+    else:
+        assert np.all(np.abs(got - ref) <= rel * np.abs(ref) + 1e-18)
