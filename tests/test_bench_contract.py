@@ -1,0 +1,48 @@
+"""The one-line JSON contract of bench.py: the reference arm (the FP64 oracle
+on the host, no GPU) here, the GPU arm under the gpu marker."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+             "vs_baseline", "dtype", "data", "config", "e2e"}
+
+
+def run_bench(*args, timeout=600):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, capture_output=True,
+                       text=True, timeout=timeout)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = run_bench("--impl", "reference", "--steps", "2", "--warmup", "1", "--nx", "64", "--ny", "64",
+                  "--cells", "2", "--cpu-seconds", "0.5")
+    assert BASE_KEYS <= set(d) and d["impl"] == "reference"
+    assert d["value"] > 0 and d["unit"] == "MLUPS" and d["higher_is_better"] is True
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["config"]["workload"].startswith("couette batch: 2 cells of 64x64")
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line():
+    d = run_bench("--steps", "3", "--warmup", "3", "--nx", "256", "--ny", "256", "--cells", "2", "--chunk", "20",
+                  "--cpu-seconds", "0.5")
+    assert BASE_KEYS <= set(d) and "impl" not in d
+    assert d["value"] > 0 and d["n_gpus"] == 1 and d["dtype"] == "f32" and d["data"] == "synthetic"
+    rf = d["roofline"]
+    assert rf["bound"] == "hbm" and rf["unit"] == "GB/s" and 0 < rf["frac"] < 2 and rf["peak"] > 0
+    assert abs(rf["achieved"] / rf["peak"] - rf["frac"]) < 1e-9
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == 4 * 2 * 256 * 256 * 8 and e["d2h_bytes_per_step"] > 0
+    assert d["gpu_launches"] >= 3 * 20
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert set(d["clocks"] or {}) >= {"sm_mhz", "sm_max_mhz", "reasons"} or d["clocks"] is None
