@@ -98,10 +98,16 @@ def peaks():
 
 
 def source_digest():
+    """Digest of the fused kernel's code (comments and layout removed, so that
+    editing a comment does not orphan the committed DRAM counters)."""
+    import re
     h = hashlib.sha256()
     for f in ("lb_tiled.cu", "lb_common.cuh", "tma.cuh"):
-        with open(os.path.join(ROOT, "paper_1004_5058_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1004_5058_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

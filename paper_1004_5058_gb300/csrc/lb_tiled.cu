@@ -3,7 +3,10 @@
 // in one pass over the populations.
 //
 // Work item = one column strip of TX sites x one segment of TY rows of one cell.
-// A CTA of TX threads (one column each) walks its segment row by row:
+// A CTA has TX column threads (one species and two adjacent columns each: lanes
+// 0-15 of a warp species A, 16-31 species B of the same 32 columns) and one
+// service warp (TMA issue, halo columns of psi/rho).  It walks its segment row
+// by row:
 //   * TMA (cp.async.bulk.tensor, 4-D map [cell][q][y][x]) brings whole rows of all
 //     18 populations into a ring of D shared-memory slots, several rows ahead,
 //     each slot completing on its own mbarrier; a row is TX main columns plus
@@ -13,7 +16,8 @@
 //     on chip when row y is collided: the 25-point stencil reads shared memory;
 //   * row y is collided from its populations still in the slot ring and pushed
 //     to the other ping-pong buffer with plain coalesced stores (x-shifted by
-//     -1/0/+1 element), bounce-back rows handled in place.
+//     -1/0/+1 element), bounce-back rows handled in place; with FP16 storage the
+//     stores round to nearest or stochastically (Store<T>, Dither).
 // HBM traffic per site update is one read and one write of the 18 populations;
 // halo rows/columns are re-read by neighbouring work items (mostly from L2).
 // The grid is persistent (CTAs loop over work items).  Every mbarrier wait is
@@ -31,10 +35,6 @@
 namespace lbhb {
 
 constexpr int RING = 6;  // psi/rho rows on chip: 5 read by a collision + 1 being written
-
-template <class C> struct V2;
-template <> struct V2<float> { using t = float2; };
-template <> struct V2<double> { using t = double2; };
 
 __host__ __device__ constexpr int al128(int b) { return (b + 127) / 128 * 128; }
 
