@@ -46,3 +46,25 @@ def test_gpu_arm_line():
     assert d["gpu_launches"] >= 3 * 20
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert set(d["clocks"] or {}) >= {"sm_mhz", "sm_max_mhz", "reasons"} or d["clocks"] is None
+
+
+def test_traffic_record_matches_the_kernel_sources():
+    """The committed DRAM counters carry the digest of the fused kernel's code
+    (comments and layout ignored); while it matches, the bench reports them and
+    they stay within 10 % of the algorithmic bytes."""
+    import importlib.util
+    import re
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    rec = json.load(open(os.path.join(ROOT, "profiles", "fused_step_dram.json")))
+    if rec["source_digest"] != bench.source_digest():
+        # the kernel changed since the capture: the bench reports traffic null
+        assert bench.committed_traffic("fp32", 1024, 1024, 8) is None
+        pytest.skip("DRAM counters predate the current kernel code")
+    assert {"fp32", "fp16", "fp16sr", "fp64"} <= set(rec)
+    for prec in ("fp32", "fp16", "fp16sr"):
+        per_site = rec[prec]["dram_bytes_per_launch"] / rec[prec]["sites_per_launch"]
+        alg = {"fp32": 144, "fp16": 72, "fp16sr": 72}[prec]
+        assert 0.9 * alg < per_site < 1.1 * alg  # no wasted re-reads
+    assert bench.committed_traffic("fp32", 1024, 1024, 8) == rec["fp32"]["dram_bytes_per_launch"]
