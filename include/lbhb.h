@@ -194,6 +194,19 @@ long long lb_steps_done(const lb_handle* h);
 lb_status lb_save(lb_handle* h, const char* path);
 lb_status lb_load(lb_handle* h, const char* path);
 
+/* Test hook for the failure paths (the paper has no counterpart): arms one
+ * fault for the next lb_step of this handle.
+ *   fault = 1  the first launch of that step leaves one row copy of its first
+ *              CTA unissued (tiled kernel only, else LB_ERR_UNSUPPORTED): the
+ *              waits for it run out after their 1.5 s bound, the kernel records
+ *              a timeout and returns, later launches of the batch exit at once,
+ *              and the next synchronising call reports LB_ERR_TIMEOUT.  Nothing
+ *              faults: the device stays usable and lb_init_fields recovers.
+ *   fault = 2  the step fails at once with LB_ERR_CUDA, as a failed launch
+ *              would, without enqueuing anything; the state is unchanged.
+ *   fault = 0  disarms.  Other values: LB_ERR_INVALID. */
+lb_status lb_test_inject(lb_handle* h, int fault);
+
 /* The cudaStream_t the handle enqueues on (the caller's, or the library's own
  * non-blocking stream), for recording events around lb_step. */
 void* lb_stream(const lb_handle* h);

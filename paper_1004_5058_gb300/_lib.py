@@ -73,6 +73,7 @@ SIGNATURES = {
     "mlp_serve": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mlp_kernel_launches": (C.c_longlong, [_H]),
     "lb_save": (C.c_int, [_H, C.c_char_p]),
+    "lb_test_inject": (C.c_int, [_H, C.c_int]),
     "lb_load": (C.c_int, [_H, C.c_char_p]),
     "mlp_set_error_budget": (C.c_int, [_H, _F, C.c_int, C.c_double, C.c_double, C.c_double]),
     "mlp_destroy": (None, [_H]),

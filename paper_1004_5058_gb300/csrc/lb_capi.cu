@@ -60,6 +60,7 @@ struct lb_handle {
     int tile_x = 0, tile_y = 0;
     TiledPlan* plan = nullptr;
     long long launches = 0;
+    int inject = 0;  // lb_test_inject: 1 = stalled row copy, 2 = failed launch (next lb_step)
     std::string last_error;
     // CUDA graphs of step chunks, keyed by (source buffer, steps, sampled last step)
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
@@ -614,6 +615,10 @@ lb_status lb_step(lb_handle* h, long long n_steps)
         }
     }
     if (n_steps == 0) return LB_OK;
+    if (h->inject == 2) {
+        h->inject = 0;
+        return fail(h, LB_ERR_CUDA, "lb_step: launch failed: injected failure (lb_test_inject)");
+    }
     int nl = 0;
     long long done = 0;
     while (done < n_steps) {
@@ -636,9 +641,18 @@ lb_status lb_step(lb_handle* h, long long n_steps)
         // split long unsampled runs into graph-sized pieces
         while (chunk > 0) {
             const long long piece_max = 64;
-            const long long piece = chunk > piece_max ? piece_max : chunk;
+            // an injected stall applies to one plain launch, never to a captured graph
+            const bool stall = h->inject == 1 && h->plan != nullptr;
+            const long long piece = stall ? 1 : (chunk > piece_max ? piece_max : chunk);
             const bool s_last = sample_last && piece == chunk;
-            cudaError_t e = run_chunk(h, h->cur, (int)piece, s_last, &nl);
+            cudaError_t e;
+            if (stall) {
+                h->inject = 0;
+                tiled_inject_skip(h->plan, 5);
+                e = enqueue_one_step(h, h->cur, s_last, &nl);
+            } else {
+                e = run_chunk(h, h->cur, (int)piece, s_last, &nl);
+            }
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return fail(h, LB_ERR_CUDA, "lb_step: launch failed: %s", cudaGetErrorString(e));
@@ -871,6 +885,16 @@ lb_status lb_autotune(lb_handle* h, const char* cache_path)
             fclose(fp);
         }
     }
+    return LB_OK;
+}
+
+lb_status lb_test_inject(lb_handle* h, int fault)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (fault < 0 || fault > 2) return fail(h, LB_ERR_INVALID, "lb_test_inject: unknown fault %d", fault);
+    if (fault == 1 && h->kernel != LB_KERNEL_TILED)
+        return fail(h, LB_ERR_UNSUPPORTED, "lb_test_inject: a stalled copy needs the tiled kernel");
+    h->inject = fault;
     return LB_OK;
 }
 

@@ -25,6 +25,9 @@ template <class T>
 cudaError_t launch_tiled_step(TiledPlan* p, int src_buf, const CellDev* cells, bool sample, double* prof_part,
                               double* wall_part, unsigned* err, cudaStream_t st, int* n_launches);
 void tiled_tiles(const TiledPlan* p, int* tx, int* ty);
+// Failure injection (tests): the next launch's CTA 0 leaves the copy of its row
+// `row` (counted over its work items) unissued, so the waits for it time out.
+void tiled_inject_skip(TiledPlan* p, uint32_t row);
 
 // auxiliary kernels (lb_aux.cu)
 template <class T>

@@ -62,6 +62,7 @@ struct TiledPlan {
     size_t smem;
     CUtensorMap tm_main[2], tm_halo[2];
     void* f[2];
+    uint32_t skip_row = ~0u;  // failure injection for the next launch (tests)
 };
 
 // Row-slot ring depth: about three rows in flight beyond the three in use.
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                                                             const CellDev* __restrict__ cells,
                                                             double* __restrict__ prof_part,
                                                             double* __restrict__ wall_part,
-                                                            unsigned* __restrict__ err)
+                                                            unsigned* __restrict__ err, uint32_t skip_row_arg)
 {
     using C = typename Store<T>::C;
     // stored populations are scale * g (scale 1 except for the dithered FP16 storage)
@@ -199,6 +200,9 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
     }
     if (__syncthreads_or(stale)) return;
 
+    // failure-injection hook (tests only): CTA 0 leaves the copy of its row
+    // skip_row_arg unissued, so the waits for it run out; ~0u: none
+    const uint32_t skip_row = blockIdx.x == 0 ? skip_row_arg : ~0u;
     const long long per_cell = (long long)n_strips * n_seg;
     const long long items = per_cell * g.n_cells;
     uint32_t nrow = 0;  // global index of row 0 of the current item (rows consumed before it)
@@ -228,10 +232,12 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             const int slot = (int)(n_issued % D);
             unsigned char* dst = fring + slot * SLOT;
             const int yp = stencil_row(iy0 - 2 + ik, g.ny, bc);
-            mbar_arrive_expect_tx(&bars[slot], TX_BYTES);
-            tma_load_4d(dst, &tm_main, ix0, yp, 0, icell, &bars[slot]);
-            tma_load_4d(dst + MAIN_AL, &tm_halo, ixl, yp, 0, icell, &bars[slot]);
-            tma_load_4d(dst + MAIN_AL + HALO_AL, &tm_halo, ixr, yp, 0, icell, &bars[slot]);
+            if (n_issued != skip_row) {
+                mbar_arrive_expect_tx(&bars[slot], TX_BYTES);
+                tma_load_4d(dst, &tm_main, ix0, yp, 0, icell, &bars[slot]);
+                tma_load_4d(dst + MAIN_AL, &tm_halo, ixl, yp, 0, icell, &bars[slot]);
+                tma_load_4d(dst + MAIN_AL + HALO_AL, &tm_halo, ixr, yp, 0, icell, &bars[slot]);
+            }
             ++n_issued;
             if (++ik == iR) {
                 ik = 0;
@@ -470,7 +476,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             if (producer) {
                 atomicOr(err, ERR_TIMEOUT);
                 // drain the copies still in flight before shared memory is released
-                for (uint32_t n = nrow; n < n_issued; ++n) mbar_wait_bounded(&bars[n % D], (n / D) & 1u, 1u << 20);
+                for (uint32_t n = nrow; n < n_issued; ++n)
+                    if (n != skip_row) mbar_wait_bounded(&bars[n % D], (n / D) & 1u, 500000000ull);
             }
             __syncthreads();
             break;
@@ -639,6 +646,8 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
 
 void tiled_destroy(TiledPlan* p) { delete p; }
 
+void tiled_inject_skip(TiledPlan* p, uint32_t row) { p->skip_row = row; }
+
 void tiled_tiles(const TiledPlan* p, int* tx, int* ty)
 {
     *tx = p->tx;
@@ -653,9 +662,11 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
     const void* k = pick<T>(p->tx, sample);
     Geom g = p->g;
     int bc = p->bc, ty = p->ty, ns = p->n_strips, nseg = p->n_seg;
+    uint32_t skip = p->skip_row;
+    p->skip_row = ~0u;  // one launch only
     void* args[] = {(void*)&p->tm_main[src], (void*)&p->tm_halo[src], (void*)&dst, (void*)&g, (void*)&bc,
                     (void*)&ty, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
-                    (void*)&wall_part, (void*)&err};
+                    (void*)&wall_part, (void*)&err, (void*)&skip};
     cudaError_t e = cudaLaunchKernel(k, dim3(p->grid), dim3(tiled_threads(p->tx)), args, p->smem, st);
     *n_launches += 1;
     return e;

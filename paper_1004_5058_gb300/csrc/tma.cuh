@@ -42,13 +42,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for phase `parity` of the barrier with an iteration limit; returns false
-// if the limit ran out (the caller records an error instead of hanging).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iter = (1u << 22))
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (uint32_t it = 0; it < max_iter; ++it)
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of the barrier for at most `limit_ns` nanoseconds of
+// wall time (a row copy takes microseconds); returns false when the time ran
+// out, and the caller records an error instead of hanging.  The clock is read
+// only after the first unsuccessful probe, and then every 16 probes.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 1500000000ull)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if ((it & 15u) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
 }
 
 // 4-D tiled bulk tensor load global -> shared, completing on an mbarrier.

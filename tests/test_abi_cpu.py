@@ -48,6 +48,7 @@ def test_null_and_invalid_arguments_rejected_before_device_work(lib):
     assert lib.lb_sync(None) == L.LB_ERR_INVALID
     assert lib.lb_steps_done(None) == 0
     lib.lb_destroy(None)
+    assert lib.lb_test_inject(None, 1) == L.LB_ERR_INVALID
     assert lib.lb_save(None, b"x.ckpt") == L.LB_ERR_INVALID
     assert lib.lb_load(None, b"x.ckpt") == L.LB_ERR_INVALID
     e = (C.c_float * 4)()
