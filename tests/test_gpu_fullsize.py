@@ -122,3 +122,41 @@ def test_no_samples_and_zero_steps():
         assert ns == 0 and np.all(np.isnan(ub))
         lat.set_sampling(5, 0).step(20)  # every = 0: sampling off
         assert lat.profile()[1] == 0
+
+
+def test_largest_tiled_cell():
+    """The largest cell the tiled kernel takes (18 planes of ny x pitch just
+    under 2^31 elements: 32-bit offsets inside a cell): a uniform periodic
+    background stays bitwise uniform, and a seeded bump placed near the far
+    end of the arrays evolves as the oracle's same bump in a small cell
+    (translation invariance), which checks the high addresses."""
+    from oracle import lb as orc
+    from paper_1004_5058_gb300 import Lattice
+    nx, ny = 10240, 11648
+    assert 18 * ny * nx < 2 ** 31
+    cell = I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=0)
+    bump = 0.05 * (2.0 * I.uniform01(8, 36).reshape(6, 6) - 1.0)
+    ra = np.full((1, ny, nx), 0.6)
+    rb = np.full((1, ny, nx), 0.6)
+    ra[0, ny - 30:ny - 24, nx - 30:nx - 24] += bump
+    with Lattice([cell], "fp32") as lat:
+        lat.init_fields(ra, rb)
+        assert lat.kernel()[0] == "tiled"
+        lat.step(2)
+        ga, gb, gu, _ = lat.fields()
+        mass, _ = lat.reductions()
+    del ra, rb
+    win = (slice(ny - 40, ny - 14), slice(nx - 40, nx - 14))
+    small = I.make_cell("paper", nx=64, ny=64, g_ab=0.405, bc=0)
+    sa = np.full((64, 64), 0.6)
+    sb = np.full((64, 64), 0.6)
+    sa[34:40, 34:40] += bump
+    r = orc.Run(small, sa, sb).step(2)
+    oa, ob, ou, _ = r.fields()
+    assert max_abs(ga[0][win], oa[24:50, 24:50]) <= 1e-6
+    assert max_abs(gb[0][win], ob[24:50, 24:50]) <= 1e-6
+    assert max_abs(gu[0][win], ou[24:50, 24:50]) <= 1e-6
+    bg = ga[0].copy()
+    bg[ny - 40:ny - 14, nx - 40:nx - 14] = bg[0, 0]
+    assert np.ptp(bg) == 0.0  # the untouched background is bitwise uniform
+    assert abs(mass[0, 0] - (0.6 * nx * ny + bump.sum())) <= 1e-6 * 0.6 * nx * ny
