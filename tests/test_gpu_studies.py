@@ -1,0 +1,54 @@
+"""The study runners (paper_1004_5058_gb300/studies.py) at toy sizes: each
+returns its documented keys with finite values, so the full-size runs whose
+results the docs quote stay runnable."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def finite(x):
+    return x is not None and math.isfinite(float(x))
+
+
+def test_precision_study_small():
+    from paper_1004_5058_gb300 import studies
+    r = studies.precision_study(n=128, steps=400, every=10, g_ab=0.045)
+    assert set(r) >= {"fp64", "fp32", "fp16", "fp16sr"}
+    for p in ("fp32", "fp16", "fp16sr"):
+        assert finite(r[p]["sigma_rel_err"]) and finite(r[p]["max_abs_drho"]) and r[p]["mlups"] > 0
+    assert r["fp64"]["mass_drift"] < 1e-12
+
+
+def test_couette_flow_curves_small():
+    from paper_1004_5058_gb300 import studies
+    r = studies.couette_flow_curve(n=64, n_speeds=4, steps=2000, every=10)
+    assert len(r["sigma_xy"]) == 4 and r["samples"] == 100 and r["points_per_s"] > 0
+    b = studies.flow_curve(L=64, steps=1000, n_speeds=4, g_abs=(0.3, 0.405))
+    s = studies.flow_curve(L=64, steps=1000, n_speeds=4, g_abs=(0.3, 0.405), sequential=True)
+    for g in ("0.3", "0.405"):  # batching changes nothing but the rounding of the FP64 sums
+        np.testing.assert_allclose(b["curves"][g]["sigma_xy"], s["curves"][g]["sigma_xy"], rtol=1e-9, atol=1e-15)
+
+
+def test_kolmogorov_runners_small():
+    from paper_1004_5058_gb300 import studies
+    r = studies.kolmogorov(L=64, steps=3000, every=50, rho0s=(0.83,), u0s=(0.1, 0.4))
+    assert len(r["runs"]) == 2 and all(finite(x["R"]) for x in r["runs"])
+    assert "0.83" in r["master"]
+    s = studies.kolmogorov_rho0_sweep(L=64, steps=3000, rho0s=(0.70, 0.74, 0.78, 0.82, 0.86), r_floor=0.0)
+    assert len(s["runs"]) == 5 and "vft" in s
+
+
+def test_surrogate_study_small():
+    from paper_1004_5058_gb300 import studies
+    r = studies.surrogate_study(n_train=24, n_test=8, n_speeds=8, L=32, steps=2000, epochs=30, batch=64)
+    assert r["train_points"] > 0 and 0.0 <= r["served_fraction"] <= 1.0
+    assert r["network_queries_per_s"] > 0 and len(r["error_table_by_logS_bin"]) == 8
