@@ -149,6 +149,51 @@ __device__ inline void st_one(T* p, C v, Dither& d)
 // of psi/rho, so the column warps all do the same work between two barriers.
 __host__ __device__ constexpr int tiled_threads(int tx) { return tx + 32; }
 
+// Service warp, sampled steps: the sums of u_x over each 32-column group of one
+// row of a strip (ub: TX values), one FP64 partial per group as the column warps
+// would have written it.  Lane l takes NW = TX/32 consecutive columns of group
+// l / (32/NW), then a segmented warp sum; FP32 values are carried as an
+// unevaluated (hi, lo) pair (error-free two-sum), ~2^-48 relative.  Not inlined,
+// so its registers do not add to the column warps' in the hot loop.
+template <class C, int TX>
+__device__ __noinline__ void profile_row_sums(const C* ub, int lane, double* __restrict__ prof_part, int cell,
+                                              const Geom& g, int x0, int y)
+{
+    constexpr int NW = TX / 32, SEG = 32 / NW;
+    const int grp = lane / SEG, t = lane % SEG;
+    double part;
+    if constexpr (sizeof(C) == 4) {
+        float hi = ub[grp * 32 + t * NW], lo = 0.f;
+#pragma unroll
+        for (int q = 1; q < NW; ++q) {
+            const float v = ub[grp * 32 + t * NW + q];
+            const float sum = __fadd_rn(hi, v);
+            const float bp = __fsub_rn(sum, hi);
+            lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bp)), __fsub_rn(v, bp)));
+            hi = sum;
+        }
+#pragma unroll
+        for (int o = SEG / 2; o > 0; o >>= 1) {
+            const float h2 = __shfl_down_sync(0xffffffffu, hi, o, SEG);
+            const float l2 = __shfl_down_sync(0xffffffffu, lo, o, SEG);
+            const float sum = __fadd_rn(hi, h2);
+            const float bp = __fsub_rn(sum, hi);
+            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bp)), __fsub_rn(h2, bp));
+            hi = sum;
+            lo = __fadd_rn(__fadd_rn(lo, l2), err);
+        }
+        part = (double)hi + (double)lo;
+    } else {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) v += ub[grp * 32 + t * NW + q];
+#pragma unroll
+        for (int o = SEG / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, SEG);
+        part = v;
+    }
+    if (t == 0) prof_part[((long long)cell * (g.nx / 32) + (x0 >> 5) + grp) * g.ny + y] = part;
+}
+
 template <class T, int TX, bool SAMPLE>
 __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
                                                             const __grid_constant__ CUtensorMap tm_halo,
@@ -177,6 +222,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
     C* psi_ring = reinterpret_cast<C*>(smem + D * SLOT);  // [species][RING][W] (stride SS per species)
     C* rho_ring = psi_ring + 2 * SS;
     uint64_t* bars = reinterpret_cast<uint64_t*>(rho_ring + 2 * SS);
+    // sampled steps: u_x of each site of the last two rows, summed by the service warp
+    C* ubuf = reinterpret_cast<C*>(bars + D);
 
     constexpr int NW = TX / 32;               // column warps (32 columns x 2 species each)
     const int t = threadIdx.x;
@@ -339,7 +386,11 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             }
             // rows 0 .. j+1 of this item are done with their slots
             if (producer) issue_upto(nrow + (uint32_t)(j + 2 + D));
-            if (svc) continue;
+            if (svc) {
+                if (SAMPLE && j > 0)  // its row finished before this barrier
+                    profile_row_sums<C, TX>(ubuf + ((j - 1) & 1) * TX, lane, prof_part, cell, g, x0, y0 + j - 1);
+                continue;
+            }
             // ---- collide logical row k = j + 2 (lattice row y), sites x and x+1
             const int k = j + 2, y = y0 + j;
             const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT) + sp * 9 * TX + c0;
@@ -460,17 +511,22 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 const C rho_t = sp ? rho_s[1] + e[1][3] : rho_s[0] + e[1][2];
                 const C up = ((sp ? jx[1] : jx[0]) + C(0.5) * Fx_t) * (sp ? inv_r[1] : inv_r[0]);
                 if (!(rho_t > C(0)) || !isfinite(rho_t)) atomicOr(err, ERR_NONFINITE);
-                // lane sums carried as an unevaluated pair (error-free two-sum),
-                // then added in FP64: ~2^-48 relative, no FP64 pipe in the tree
-                const double usum = warp_sum_compensated(up);
-                double wsum = 0.0;
-                if (wall_lo || wall_hi) wsum = warp_sum_compensated2(dpx_site, C(0));
-                if (lane == 0) {
-                    const int nbx = g.nx / 32, wg = (x0 >> 5) + warp;
-                    prof_part[((long long)cell * nbx + wg) * g.ny + y] = usum;
-                    if (wall_lo || wall_hi) wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = wsum;
+                // the row sums of u_x are the service warp's (svc_profile, after the
+                // next barrier): sums carried as an unevaluated pair (error-free
+                // two-sum), then added in FP64, ~2^-48 relative
+                ubuf[(j & 1) * TX + c0 + sp] = up;
+                if (wall_lo || wall_hi) {
+                    const double wsum = warp_sum_compensated2(dpx_site, C(0));
+                    if (lane == 0) {
+                        const int nbx = g.nx / 32, wg = (x0 >> 5) + warp;
+                        wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = wsum;
+                    }
                 }
             }
+        }
+        if (SAMPLE && !aborted) {
+            __syncthreads();  // the last row's u_x values are in place
+            if (svc) profile_row_sums<C, TX>(ubuf + ((rows - 1) & 1) * TX, lane, prof_part, cell, g, x0, y0 + rows - 1);
         }
         if (aborted) {
             if (producer) {
@@ -507,7 +563,9 @@ static size_t smem_bytes(int tx, int elem, int depth)
 {
     const SlotGeom sg = slot_geom(tx, elem);
     const int cb = elem == 8 ? 8 : 4;
-    return (size_t)depth * sg.slot_b + (size_t)4 * ring_species_stride(tx) * cb + (size_t)depth * 8;
+    // slots, psi/rho rings, mbarriers, and two rows of per-site profile values
+    return (size_t)depth * sg.slot_b + (size_t)4 * ring_species_stride(tx) * cb + (size_t)depth * 8 +
+           (size_t)2 * tx * cb;
 }
 
 // Segment height from a fill model: work items = strips x segments x cells run
