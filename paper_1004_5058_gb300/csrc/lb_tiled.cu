@@ -5,8 +5,8 @@
 // Work item = one column strip of TX sites x one segment of TY rows of one cell.
 // A CTA has TX column threads (one species and two adjacent columns each: lanes
 // 0-15 of a warp species A, 16-31 species B of the same 32 columns) and one
-// service warp (TMA issue, halo columns of psi/rho).  It walks its segment row
-// by row:
+// service warp (TMA issue, halo columns of psi/rho, row sums of sampled steps).
+// It walks its segment row by row:
 //   * TMA (cp.async.bulk.tensor, 4-D map [cell][q][y][x]) brings whole rows of all
 //     18 populations into a ring of D shared-memory slots, several rows ahead,
 //     each slot completing on its own mbarrier; a row is TX main columns plus
