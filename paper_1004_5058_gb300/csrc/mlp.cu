@@ -356,14 +356,27 @@ struct mlp_handle {
     long long adam_t = 0;
     long long launches = 0;
     std::vector<void*> allocs;
+    // mlp_serve as one CUDA graph for the last (input, batch, outputs) it served
+    cudaGraphExec_t serve_graph = nullptr;
+    const void* serve_key[4] = {};
+    int serve_batch = 0, serve_launches = 0;
+    bool serve_graphs = true;  // false once the stream refused capture
 };
 
 namespace {
+
+void drop_serve_graph(mlp_handle* h)
+{
+    if (h->serve_graph) cudaGraphExecDestroy(h->serve_graph);
+    h->serve_graph = nullptr;
+    h->serve_batch = 0;
+}
 
 void release(mlp_handle* h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_serve_graph(h);
     for (void* p : h->allocs) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -633,10 +646,10 @@ lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stre
     return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }
 
-lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit, int* fallback)
+// The kernels of one serving call: forward pass and the fallback decision.
+static cudaError_t enqueue_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit,
+                                 int* fallback)
 {
-    if (!h || !x || !stress || !logit || !fallback) return invalid("mlp: NULL handle or buffer");
-    if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
     cudaError_t e = forward(h, x, batch);
     if (e == cudaSuccess) {
         serve_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(
@@ -644,6 +657,48 @@ lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, flo
             h->over_budget, h->n_bins, h->ls_lo, h->ls_hi, stress, logit, fallback);
         h->launches++;
         e = cudaGetLastError();
+    }
+    return e;
+}
+
+lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit, int* fallback)
+{
+    if (!h || !x || !stress || !logit || !fallback) return invalid("mlp: NULL handle or buffer");
+    if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
+    // the six launches of a serving call go out as one graph, re-used while the
+    // caller serves from the same buffers (the usual serving loop)
+    const void* key[4] = {x, stress, logit, fallback};
+    const bool same = h->serve_graph && h->serve_batch == batch && memcmp(key, h->serve_key, sizeof key) == 0;
+    if (!same && h->serve_graphs) {
+        drop_serve_graph(h);
+        cudaGraph_t g = nullptr;
+        long long l0 = h->launches;
+        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = enqueue_serve(h, x, batch, stress, logit, fallback);
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+            h->serve_launches = (int)(h->launches - l0);
+            h->launches = l0;  // nothing ran yet
+            if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
+                cudaGraphInstantiate(&h->serve_graph, g, 0) == cudaSuccess) {
+                memcpy(h->serve_key, key, sizeof key);
+                h->serve_batch = batch;
+            } else {
+                h->serve_graph = nullptr;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!h->serve_graph) {  // this stream cannot be captured: plain launches from now on
+            cudaGetLastError();
+            h->serve_graphs = false;
+        }
+    }
+    cudaError_t e;
+    if (h->serve_graph && h->serve_batch == batch && memcmp(key, h->serve_key, sizeof key) == 0) {
+        e = cudaGraphLaunch(h->serve_graph, h->stream);
+        h->launches += h->serve_launches;
+    } else {
+        e = enqueue_serve(h, x, batch, stress, logit, fallback);
     }
     return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }
@@ -661,6 +716,7 @@ lb_status mlp_set_error_budget(mlp_handle* h, const float* bin_error, int n_bins
     h->n_bins = n_bins;
     h->ls_lo = (float)log_s_lo;
     h->ls_hi = (float)log_s_hi;
+    drop_serve_graph(h);  // the serving graph holds the old table size and range
     return LB_OK;
 }
 

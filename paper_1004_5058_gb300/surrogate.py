@@ -147,12 +147,18 @@ class Surrogate:
         L.check(self.lib.mlp_train_step(self.h, self._ptr(x), self._ptr(target), self._ptr(label), int(x.shape[0]),
                                         self._ptr(loss_out) if loss_out is not None else None))
 
-    def serve(self, x):
+    def serve(self, x, out=None):
+        """(stress, logit, fallback) for queries x [B,5] (mlp_serve).  out: optional
+        preallocated (stress, logit, fallback) tensors; serving again from the same
+        buffers replays the library's captured graph of the call."""
         import torch
         B = int(x.shape[0])
-        stress = torch.empty(B, dtype=torch.float32, device=x.device)
-        logit = torch.empty(B, dtype=torch.float32, device=x.device)
-        fb = torch.empty(B, dtype=torch.int32, device=x.device)
+        if out is None:
+            stress = torch.empty(B, dtype=torch.float32, device=x.device)
+            logit = torch.empty(B, dtype=torch.float32, device=x.device)
+            fb = torch.empty(B, dtype=torch.int32, device=x.device)
+        else:
+            stress, logit, fb = out
         L.check(self.lib.mlp_serve(self.h, self._ptr(x), B, self._ptr(stress), self._ptr(logit), self._ptr(fb)))
         return stress, logit, fb
 

@@ -193,3 +193,30 @@ def test_surrogate_gain_over_lb(env):
     t_lb = time.perf_counter() - t0
     assert t_lb / t_net > 100.0
     sg.close()
+
+
+def test_serve_graph_replay_matches_plain_calls(env):
+    """Serving again from the same buffers replays a captured graph: the results
+    equal a fresh call's, and changing the error budget takes effect."""
+    torch, S = env
+    box, x = box_and_inputs(S, B=300, seed=12)
+    sg = S.Surrogate(box, sigma_scale=1e-4, max_batch=300, logit_margin=0.5)
+    sg.set_params(S.init_params(7))
+    X = torch.tensor(x, dtype=torch.float32, device="cuda")
+    outs = sg.serve(X)
+    ref = [o.clone() for o in outs]
+    n0 = sg.kernel_launches
+    for _ in range(3):
+        got = sg.serve(X, out=outs)
+    assert sg.kernel_launches - n0 == 3 * 6
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    fresh = sg.serve(X)  # other output buffers: captured anew
+    for a, b in zip(fresh, ref):
+        assert torch.equal(a, b)
+    lo, hi = box.center[0] - box.half_range[0], box.center[0] + box.half_range[0]
+    sg.set_error_budget(np.array([1.0, 1.0]), lo, hi, budget=0.5)  # every bin over budget
+    assert np.all(sg.serve(X, out=outs)[2].cpu().numpy() == 1)
+    sg.set_error_budget(np.zeros(0), lo, hi, budget=0.5)
+    assert torch.equal(sg.serve(X, out=outs)[2], ref[2])
+    sg.close()
