@@ -79,7 +79,9 @@ lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stre
 lb_status mlp_set_error_budget(mlp_handle* h, const float* bin_error, int n_bins, double log_s_lo,
                                double log_s_hi, double budget);
 
-/* Serving: forward pass plus the fallback decision per query: fallback[b] = 1
+/* Serving: forward pass plus the fallback decision per query, in one kernel
+ * launch (the served stress and logit equal mlp_forward's bit for bit):
+ * fallback[b] = 1
  * if any input lies outside the training box center +- half_range, if
  * |logit| < logit_margin (yielded/arrested undecided), or if the query's log S
  * bin is above the error budget (mlp_set_error_budget); 0 otherwise.  stress,

@@ -301,36 +301,124 @@ __global__ void output_kernel(const float* __restrict__ out, int B, float scale,
     y[2 * b + 1] = out[(long long)b * NOUTP + 1];
 }
 
-constexpr int MAX_BINS = 256;
-
-// bins: per log S bin, 1 if the held-out error of that bin exceeds the budget.
-__global__ void serve_kernel(const float* __restrict__ x, const float* __restrict__ out, int B,
-                             const float* __restrict__ center, const float* __restrict__ half, float scale,
-                             float margin, const int* __restrict__ over_budget, int n_bins, float ls_lo,
-                             float ls_hi, float* __restrict__ stress, float* __restrict__ logit,
-                             int* __restrict__ fallback)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    bool outside = false;
-    for (int c = 0; c < NIN; ++c) {
-        const float xv = x[b * NIN + c];
-        outside |= !(fabsf(xv - center[c]) <= half[c]);  // NaN counts as outside
-    }
-    bool budget = false;
-    if (n_bins > 0) {
-        const float ls = x[b * NIN];
-        int k = (int)floorf((ls - ls_lo) / (ls_hi - ls_lo) * n_bins);
-        k = k < 0 ? 0 : (k >= n_bins ? n_bins - 1 : k);
-        budget = over_budget[k] != 0;
-    }
-    const float lg = out[(long long)b * NOUTP + 1];
-    stress[b] = out[(long long)b * NOUTP] * scale;
-    logit[b] = lg;
-    fallback[b] = (outside || budget || !(fabsf(lg) >= margin)) ? 1 : 0;
-}
+constexpr int MAX_BINS = 256;  // bins of the serving error-budget table
 
 }  // namespace
+
+// ------------------------------------------------------------- serving --
+// The whole serving call in one kernel: a CTA takes 64 queries through the
+// normalisation, the three tanh layers and the output layer with every
+// activation kept in shared memory (each warp owns 16 rows), the layer's
+// weights staged in shared memory, then makes the fallback decision.  The
+// products are the GEMM kernel's, tile for tile: one m16n8k16 BF16 product per
+// 16-wide slice of K in increasing K, bias and tanh in FP32, activations
+// rounded to BF16; so the served values equal the layered forward pass bit for
+// bit.
+constexpr int SRV_ROWS = 64, SRV_LD = HID + 8;  // padded rows: no bank conflicts on fragment loads
+constexpr size_t SRV_SMEM = sizeof(bf16) * (2 * SRV_ROWS * SRV_LD + HID * SRV_LD);
+
+struct ServeArgs {
+    const float* x;
+    int B;
+    const bf16* W[4];
+    const float* bias[4];
+    const float *center, *half;
+    float scale, margin;
+    const int* over_budget;
+    int n_bins;
+    float ls_lo, ls_hi;
+    float *stress, *logit;
+    int* fallback;
+};
+
+__global__ void __launch_bounds__(128) serve_fused_kernel(ServeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char srv_smem[];
+    bf16* act0 = reinterpret_cast<bf16*>(srv_smem);
+    bf16* act1 = act0 + SRV_ROWS * SRV_LD;
+    bf16* Ws = act1 + SRV_ROWS * SRV_LD;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int b0 = blockIdx.x * SRV_ROWS, r0 = warp * 16;
+
+    // z = (x - center) / half_range, padded to KIN columns (zero rows past B)
+    for (int e = tid; e < SRV_ROWS * KIN; e += 128) {
+        const int r = e / KIN, c = e % KIN, b = b0 + r;
+        float v = 0.f;
+        if (b < a.B && c < NIN) v = (a.x[b * NIN + c] - a.center[c]) / a.half[c];
+        act0[r * SRV_LD + c] = __float2bfloat16_rn(v);
+    }
+    bf16* in = act0;
+    bf16* out = act1;
+    for (int l = 0; l < 4; ++l) {
+        const LayerDef L = layer_def(l);
+        __syncthreads();  // previous layer done with Ws; input activations in place
+        for (int e = tid; e < L.out_p * (L.in_p / 8); e += 128) {
+            const int n = e / (L.in_p / 8), k8 = (e % (L.in_p / 8)) * 8;
+            *reinterpret_cast<uint4*>(&Ws[n * SRV_LD + k8]) =
+                *reinterpret_cast<const uint4*>(a.W[l] + (long long)n * L.in_p + k8);
+        }
+        __syncthreads();
+        constexpr int NT = HID / 8;
+        float acc[NT][4];
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[ni][r] = 0.f;
+        const int nt = L.out_p / 8;
+        for (int ks = 0; ks < L.in_p; ks += 16) {
+            const uint32_t x0 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g) * SRV_LD + ks + 2 * t4]);
+            const uint32_t x1 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g + 8) * SRV_LD + ks + 2 * t4]);
+            const uint32_t x2 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g) * SRV_LD + ks + 2 * t4 + 8]);
+            const uint32_t x3 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g + 8) * SRV_LD + ks + 2 * t4 + 8]);
+#pragma unroll
+            for (int ni = 0; ni < NT; ++ni) {
+                if (ni >= nt) break;
+                const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&Ws[(ni * 8 + g) * SRV_LD + ks + 2 * t4]);
+                const uint32_t w1 = *reinterpret_cast<const uint32_t*>(&Ws[(ni * 8 + g) * SRV_LD + ks + 2 * t4 + 8]);
+                mma_bf16(acc[ni], x0, x1, x2, x3, w0, w1);
+            }
+        }
+        if (l < 3) {
+#pragma unroll
+            for (int ni = 0; ni < NT; ++ni)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int row = r0 + g + (r >= 2 ? 8 : 0), col = ni * 8 + 2 * t4 + (r & 1);
+                    out[row * SRV_LD + col] = __float2bfloat16_rn(tanhf(acc[ni][r] + a.bias[l][col]));
+                }
+            __syncwarp();  // a warp reads back only its own rows
+            bf16* t = in;
+            in = out;
+            out = t;
+        } else {
+            // columns 0 (stress / scale) and 1 (logit) sit in n-tile 0: lanes with t4 == 0
+            if (t4 == 0) {
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int row = r0 + g + 8 * h2, b = b0 + row;
+                    if (b >= a.B) continue;
+                    const float y0 = acc[0][2 * h2] + a.bias[3][0], y1 = acc[0][2 * h2 + 1] + a.bias[3][1];
+                    bool outside = false;
+                    for (int c = 0; c < NIN; ++c) {
+                        const float xv = a.x[b * NIN + c];
+                        outside |= !(fabsf(xv - a.center[c]) <= a.half[c]);
+                    }
+                    bool budget = false;
+                    if (a.n_bins > 0) {
+                        const float ls = a.x[b * NIN];
+                        int k = (int)floorf((ls - a.ls_lo) / (a.ls_hi - a.ls_lo) * a.n_bins);
+                        k = k < 0 ? 0 : (k >= a.n_bins ? a.n_bins - 1 : k);
+                        budget = a.over_budget[k] != 0;
+                    }
+                    a.stress[b] = y0 * a.scale;
+                    a.logit[b] = y1;
+                    a.fallback[b] = (outside || budget || !(fabsf(y1) >= a.margin)) ? 1 : 0;
+                }
+            }
+        }
+    }
+}
 
 struct mlp_handle {
     mlp_config cfg{};
@@ -356,27 +444,14 @@ struct mlp_handle {
     long long adam_t = 0;
     long long launches = 0;
     std::vector<void*> allocs;
-    // mlp_serve as one CUDA graph for the last (input, batch, outputs) it served
-    cudaGraphExec_t serve_graph = nullptr;
-    const void* serve_key[4] = {};
-    int serve_batch = 0, serve_launches = 0;
-    bool serve_graphs = true;  // false once the stream refused capture
 };
 
 namespace {
-
-void drop_serve_graph(mlp_handle* h)
-{
-    if (h->serve_graph) cudaGraphExecDestroy(h->serve_graph);
-    h->serve_graph = nullptr;
-    h->serve_batch = 0;
-}
 
 void release(mlp_handle* h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    drop_serve_graph(h);
     for (void* p : h->allocs) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -556,6 +631,8 @@ lb_status mlp_create(const mlp_config* cfg, void* cuda_stream, mlp_handle** out)
     if (e == cudaSuccess) e = alloc(h, &h->loss_d, 1);
     if (e == cudaSuccess) e = alloc(h, &h->center, NIN);
     if (e == cudaSuccess) e = alloc(h, &h->half, NIN);
+    if (e == cudaSuccess)  // the fused serving kernel keeps activations and weights in shared memory
+        e = cudaFuncSetAttribute(serve_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SRV_SMEM);
     if (e == cudaSuccess) e = alloc(h, &h->over_budget, MAX_BINS);
     if (e == cudaSuccess) {
         float c[NIN], hr[NIN];
@@ -646,61 +723,31 @@ lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stre
     return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }
 
-// The kernels of one serving call: forward pass and the fallback decision.
-static cudaError_t enqueue_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit,
-                                 int* fallback)
-{
-    cudaError_t e = forward(h, x, batch);
-    if (e == cudaSuccess) {
-        serve_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(
-            x, h->OUT, batch, h->center, h->half, (float)h->cfg.sigma_scale, (float)h->cfg.logit_margin,
-            h->over_budget, h->n_bins, h->ls_lo, h->ls_hi, stress, logit, fallback);
-        h->launches++;
-        e = cudaGetLastError();
-    }
-    return e;
-}
-
 lb_status mlp_serve(mlp_handle* h, const float* x, int batch, float* stress, float* logit, int* fallback)
 {
     if (!h || !x || !stress || !logit || !fallback) return invalid("mlp: NULL handle or buffer");
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
-    // the six launches of a serving call go out as one graph, re-used while the
-    // caller serves from the same buffers (the usual serving loop)
-    const void* key[4] = {x, stress, logit, fallback};
-    const bool same = h->serve_graph && h->serve_batch == batch && memcmp(key, h->serve_key, sizeof key) == 0;
-    if (!same && h->serve_graphs) {
-        drop_serve_graph(h);
-        cudaGraph_t g = nullptr;
-        long long l0 = h->launches;
-        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t e1 = enqueue_serve(h, x, batch, stress, logit, fallback);
-            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-            h->serve_launches = (int)(h->launches - l0);
-            h->launches = l0;  // nothing ran yet
-            if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
-                cudaGraphInstantiate(&h->serve_graph, g, 0) == cudaSuccess) {
-                memcpy(h->serve_key, key, sizeof key);
-                h->serve_batch = batch;
-            } else {
-                h->serve_graph = nullptr;
-            }
-            if (g) cudaGraphDestroy(g);
-        }
-        if (!h->serve_graph) {  // this stream cannot be captured: plain launches from now on
-            cudaGetLastError();
-            h->serve_graphs = false;
-        }
+    ServeArgs a{};
+    a.x = x;
+    a.B = batch;
+    for (int l = 0; l < 4; ++l) {
+        a.W[l] = h->W[l];
+        a.bias[l] = h->bias[l];
     }
-    cudaError_t e;
-    if (h->serve_graph && h->serve_batch == batch && memcmp(key, h->serve_key, sizeof key) == 0) {
-        e = cudaGraphLaunch(h->serve_graph, h->stream);
-        h->launches += h->serve_launches;
-    } else {
-        e = enqueue_serve(h, x, batch, stress, logit, fallback);
-    }
-    return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+    a.center = h->center;
+    a.half = h->half;
+    a.scale = (float)h->cfg.sigma_scale;
+    a.margin = (float)h->cfg.logit_margin;
+    a.over_budget = h->over_budget;
+    a.n_bins = h->n_bins;
+    a.ls_lo = h->ls_lo;
+    a.ls_hi = h->ls_hi;
+    a.stress = stress;
+    a.logit = logit;
+    a.fallback = fallback;
+    serve_fused_kernel<<<(batch + SRV_ROWS - 1) / SRV_ROWS, 128, SRV_SMEM, h->stream>>>(a);
+    h->launches++;
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }
 
 lb_status mlp_set_error_budget(mlp_handle* h, const float* bin_error, int n_bins, double log_s_lo,
@@ -716,7 +763,6 @@ lb_status mlp_set_error_budget(mlp_handle* h, const float* bin_error, int n_bins
     h->n_bins = n_bins;
     h->ls_lo = (float)log_s_lo;
     h->ls_hi = (float)log_s_hi;
-    drop_serve_graph(h);  // the serving graph holds the old table size and range
     return LB_OK;
 }
 

@@ -148,9 +148,8 @@ class Surrogate:
                                         self._ptr(loss_out) if loss_out is not None else None))
 
     def serve(self, x, out=None):
-        """(stress, logit, fallback) for queries x [B,5] (mlp_serve).  out: optional
-        preallocated (stress, logit, fallback) tensors; serving again from the same
-        buffers replays the library's captured graph of the call."""
+        """(stress, logit, fallback) for queries x [B,5] (mlp_serve, one kernel).
+        out: optional preallocated (stress, logit, fallback) tensors."""
         import torch
         B = int(x.shape[0])
         if out is None:
