@@ -315,7 +315,30 @@ constexpr int MAX_BINS = 256;  // bins of the serving error-budget table
 // rounded to BF16; so the served values equal the layered forward pass bit for
 // bit.
 constexpr int SRV_ROWS = 64, SRV_LD = HID + 8;  // padded rows: no bank conflicts on fragment loads
-constexpr size_t SRV_SMEM = sizeof(bf16) * (2 * SRV_ROWS * SRV_LD + HID * SRV_LD);
+// two activation buffers and two weight buffers (the next layer's weights are
+// copied while the current layer computes)
+constexpr size_t SRV_SMEM = sizeof(bf16) * (2 * SRV_ROWS * SRV_LD + 2 * HID * SRV_LD);
+
+// 16-byte asynchronous global -> shared copies, in commit groups
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Weights of layer l into a padded shared buffer, by all 128 threads.
+__device__ __forceinline__ void stage_weights(bf16* Ws, const bf16* W, int l, int tid)
+{
+    const LayerDef L = layer_def(l);
+    for (int e = tid; e < L.out_p * (L.in_p / 8); e += 128) {
+        const int n = e / (L.in_p / 8), k8 = (e % (L.in_p / 8)) * 8;
+        cp_async16(&Ws[n * SRV_LD + k8], W + (long long)n * L.in_p + k8);
+    }
+}
 
 struct ServeArgs {
     const float* x;
@@ -336,10 +359,16 @@ __global__ void __launch_bounds__(128) serve_fused_kernel(ServeArgs a)
     extern __shared__ __align__(16) unsigned char srv_smem[];
     bf16* act0 = reinterpret_cast<bf16*>(srv_smem);
     bf16* act1 = act0 + SRV_ROWS * SRV_LD;
-    bf16* Ws = act1 + SRV_ROWS * SRV_LD;
+    bf16* const wbuf0 = act1 + SRV_ROWS * SRV_LD;
+    bf16* const wbuf1 = wbuf0 + HID * SRV_LD;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t4 = lane & 3;
     const int b0 = blockIdx.x * SRV_ROWS, r0 = warp * 16;
+    // the first two layers' weights start copying at once
+    stage_weights(wbuf0, a.W[0], 0, tid);
+    cp_async_commit();
+    stage_weights(wbuf1, a.W[1], 1, tid);
+    cp_async_commit();
 
     // z = (x - center) / half_range, padded to KIN columns (zero rows past B)
     for (int e = tid; e < SRV_ROWS * KIN; e += 128) {
@@ -352,13 +381,12 @@ __global__ void __launch_bounds__(128) serve_fused_kernel(ServeArgs a)
     bf16* out = act1;
     for (int l = 0; l < 4; ++l) {
         const LayerDef L = layer_def(l);
-        __syncthreads();  // previous layer done with Ws; input activations in place
-        for (int e = tid; e < L.out_p * (L.in_p / 8); e += 128) {
-            const int n = e / (L.in_p / 8), k8 = (e % (L.in_p / 8)) * 8;
-            *reinterpret_cast<uint4*>(&Ws[n * SRV_LD + k8]) =
-                *reinterpret_cast<const uint4*>(a.W[l] + (long long)n * L.in_p + k8);
-        }
-        __syncthreads();
+        const bf16* Ws = (l & 1) ? wbuf1 : wbuf0;
+        if (l < 3)
+            cp_async_wait<1>();  // this layer's group is done, the next one may still fly
+        else
+            cp_async_wait<0>();
+        __syncthreads();  // weights and input activations visible to all warps
         constexpr int NT = HID / 8;
         float acc[NT][4];
 #pragma unroll
@@ -391,6 +419,11 @@ __global__ void __launch_bounds__(128) serve_fused_kernel(ServeArgs a)
             bf16* t = in;
             in = out;
             out = t;
+            if (l + 2 < 4) {
+                __syncthreads();  // every warp is done with this layer's weights
+                stage_weights((l & 1) ? wbuf1 : wbuf0, a.W[l + 2], l + 2, tid);
+                cp_async_commit();
+            }
         } else {
             // columns 0 (stress / scale) and 1 (logit) sit in n-tile 0: lanes with t4 == 0
             if (t4 == 0) {
