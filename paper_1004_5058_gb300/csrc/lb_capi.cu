@@ -201,11 +201,14 @@ static lb_status reset_counters(lb_handle* h)
 static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
 {
     if (k == LB_KERNEL_AUTO) {
-        const int cand[][2] = {{128, 0}, {64, 0}, {32, 0}};
-        for (auto& c : cand)
-            if (tiled_supported(h->g, h->elem, c[0], c[1])) {
-                if (select_kernel(h, LB_KERNEL_TILED, c[0], c[1]) == LB_OK) return LB_OK;
-            }
+        // the widest tile that divides nx, else the widest that fits (a narrower
+        // last strip), else the generic kernel
+        const int txs[] = {128, 64, 32};
+        for (int pass = 0; pass < 2; ++pass)
+            for (int c : txs)
+                if ((pass == 1 || h->nx % c == 0) && tiled_supported(h->g, h->elem, c, 0) &&
+                    select_kernel(h, LB_KERNEL_TILED, c, 0) == LB_OK)
+                    return LB_OK;
         return select_kernel(h, LB_KERNEL_GENERIC, 0, 0);
     }
     free_graphs(h);

@@ -191,7 +191,8 @@ __device__ __noinline__ void profile_row_sums(const C* ub, int lane, double* __r
         for (int o = SEG / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, SEG);
         part = v;
     }
-    if (t == 0) prof_part[((long long)cell * (g.nx / 32) + (x0 >> 5) + grp) * g.ny + y] = part;
+    const int nbx = (g.nx + 31) / 32;  // 32-column groups of the lattice; a narrow last strip has fewer
+    if (t == 0 && (x0 >> 5) + grp < nbx) prof_part[((long long)cell * nbx + (x0 >> 5) + grp) * g.ny + y] = part;
 }
 
 template <class T, int TX, bool SAMPLE>
@@ -316,6 +317,10 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
         const bool unit_omega = p.omega == C(1);  // tau = 1: f* = f^eq (uniform over the CTA)
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
+        // columns of this strip inside the lattice (the last strip of a width that
+        // is not a multiple of TX is narrower; the TMA box reads zeros beyond it)
+        const int wv = min(TX, g.nx - x0);
+        const bool act = c0 < wv;  // both columns of the pair (wv is even)
         // destination columns of the two sites x, x+1 shifted by -1/0/+1 (periodic)
         const int x = x0 + c0;
         const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p2 = x + 2 == g.nx ? 0 : x + 2;
@@ -334,6 +339,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             const unsigned char* base = fring + ((nrow + (uint32_t)k) % D) * SLOT;
             const int ring = sp * SS + ring_row * W;
             if (!svc) {
+                if (!act) return;  // its ring positions belong to the halo or to nobody
                 const T* src = reinterpret_cast<const T*>(base) + sp * 9 * TX + c0;
                 C r0 = C(0), r1 = C(0);
 #pragma unroll
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
 #pragma unroll
                 for (int i = 0; i < 9; ++i) acc += to_c(src[i * H]);
                 if (Store<T>::shifted) acc = acc * inv_scale + rho_bar;
-                const int pos = h < 2 ? h : TX + h;
+                const int pos = h < 2 ? h : wv + h;
                 psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
                 rho_ring[ring + pos] = acc;
             }
@@ -466,39 +472,41 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             const int colA[3] = {col_m, x, x + 1};   // site x,   shifts -1, 0, +1
             const int colB[3] = {x, x + 1, col_p2};  // site x+1, shifts -1, 0, +1
             C dpx_site = C(0);
-            if (!(wall_lo || wall_hi)) {
-                // interior row (uniform over the CTA): plain stores, no wall tests
+            if (act) {  // columns beyond the lattice store nothing
+                if (!(wall_lo || wall_hi)) {
+                    // interior row (uniform over the CTA): plain stores, no wall tests
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int cy = q_cy(i), cx = q_cx(i);
-                    if (cx == 0) {
-                        st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
-                    } else {
-                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
-                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                    for (int i = 0; i < 9; ++i) {
+                        const int cy = q_cy(i), cx = q_cx(i);
+                        if (cx == 0) {
+                            st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
+                        } else {
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                        }
                     }
-                }
-            } else {
+                } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int cy = q_cy(i), cx = q_cx(i);
-                    const bool into_wall = (cy < 0 && wall_lo) || (cy > 0 && wall_hi);
-                    if (into_wall) {
-                        C dpa, dpb;
-                        const C uw = cy < 0 ? -p.u_wall : p.u_wall;
-                        // bounce in the f representation (for shifted storage the shift
-                        // is put back first; opposite directions carry equal weights,
-                        // so the same shift is removed again)
-                        const C sh = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
-                        const C ba = bounce<C>(i, fs[0][i] * inv_scale + sh, rho_s[0], uw, &dpa);
-                        const C bb = bounce<C>(i, fs[1][i] * inv_scale + sh, rho_s[1], uw, &dpb);
-                        st_pair<T, C>(dst_s + q_opp(i) * pl + row3[1] + x, (ba - sh) * scale, (bb - sh) * scale, dz);
-                        dpx_site += dpa + dpb;
-                    } else if (cx == 0) {
-                        st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
-                    } else {
-                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
-                        st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                    for (int i = 0; i < 9; ++i) {
+                        const int cy = q_cy(i), cx = q_cx(i);
+                        const bool into_wall = (cy < 0 && wall_lo) || (cy > 0 && wall_hi);
+                        if (into_wall) {
+                            C dpa, dpb;
+                            const C uw = cy < 0 ? -p.u_wall : p.u_wall;
+                            // bounce in the f representation (for shifted storage the shift
+                            // is put back first; opposite directions carry equal weights,
+                            // so the same shift is removed again)
+                            const C sh = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
+                            const C ba = bounce<C>(i, fs[0][i] * inv_scale + sh, rho_s[0], uw, &dpa);
+                            const C bb = bounce<C>(i, fs[1][i] * inv_scale + sh, rho_s[1], uw, &dpb);
+                            st_pair<T, C>(dst_s + q_opp(i) * pl + row3[1] + x, (ba - sh) * scale, (bb - sh) * scale, dz);
+                            dpx_site += dpa + dpb;
+                        } else if (cx == 0) {
+                            st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
+                        } else {
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                        }
                     }
                 }
             }
@@ -510,17 +518,15 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 const C Fx_t = (sp ? Fx[1] : Fx[0]) + fx_partner;
                 const C rho_t = sp ? rho_s[1] + e[1][3] : rho_s[0] + e[1][2];
                 const C up = ((sp ? jx[1] : jx[0]) + C(0.5) * Fx_t) * (sp ? inv_r[1] : inv_r[0]);
-                if (!(rho_t > C(0)) || !isfinite(rho_t)) atomicOr(err, ERR_NONFINITE);
+                if (act && (!(rho_t > C(0)) || !isfinite(rho_t))) atomicOr(err, ERR_NONFINITE);
                 // the row sums of u_x are the service warp's (svc_profile, after the
                 // next barrier): sums carried as an unevaluated pair (error-free
                 // two-sum), then added in FP64, ~2^-48 relative
-                ubuf[(j & 1) * TX + c0 + sp] = up;
+                ubuf[(j & 1) * TX + c0 + sp] = act ? up : C(0);
                 if (wall_lo || wall_hi) {
                     const double wsum = warp_sum_compensated2(dpx_site, C(0));
-                    if (lane == 0) {
-                        const int nbx = g.nx / 32, wg = (x0 >> 5) + warp;
-                        wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = wsum;
-                    }
+                    const int nbx = (g.nx + 31) / 32, wg = (x0 >> 5) + warp;
+                    if (lane == 0 && wg < nbx) wall_part[((long long)cell * nbx + wg) * 2 + (wall_lo ? 1 : 0)] = wsum;
                 }
             }
         }
@@ -593,7 +599,10 @@ static int pick_segment_rows(const Geom& g, int tile_x, long long slots)
 bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
 {
     if (tile_x != 32 && tile_x != 64 && tile_x != 128 && tile_x != 256) return false;
-    if (tile_y < 0 || g.nx % tile_x != 0 || g.ny < 5) return false;  // tile_y 0: chosen by the fill model
+    // tile_y 0: chosen by the fill model.  nx need not be a multiple of the tile
+    // (the last strip is narrower) but must be even (column pairs) and its rows
+    // 16-byte multiples (TMA strides and halo coordinates).
+    if (tile_y < 0 || g.nx % 2 != 0 || g.ny < 5) return false;
     if (g.nx < tile_x || (g.nx * elem) % 16 != 0) return false;
     if (18 * g.plane >= (1LL << 31)) return false;  // 32-bit element offsets inside a cell
     if (smem_bytes(tile_x, elem, depth_for(tile_x, elem)) > 227 * 1024) return false;
@@ -661,7 +670,7 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
     p->tx = tile_x;
     p->ty = tile_y;
     p->depth = depth_for(tile_x, elem);
-    p->n_strips = g.nx / tile_x;
+    p->n_strips = (g.nx + tile_x - 1) / tile_x;
     p->smem = smem_bytes(tile_x, elem, p->depth);
     p->f[0] = f0;
     p->f[1] = f1;

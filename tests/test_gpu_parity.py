@@ -358,3 +358,53 @@ def test_initial_equilibrium(kernel, prec, rel, absol):
         assert np.all(np.abs(got - ref) <= absol * g + 2e-7)
     else:
         assert np.all(np.abs(got - ref) <= rel * np.abs(ref) + 1e-18)
+
+
+# ------------------------------------------------ ragged tiled strips --
+@pytest.mark.parametrize("nx,ny,tile,bc", [(80, 40, 64, 1), (200, 24, 128, 0), (136, 30, 128, 1), (36, 20, 32, 1),
+                                           (100, 16, 64, 1)])
+def test_tiled_narrow_last_strip(nx, ny, tile, bc):
+    """Widths that are not a multiple of the tile: the last strip is narrower,
+    its extra columns read zeros and store nothing, and the partial sums of the
+    sampled observables cover only lattice columns.  FP64 against the oracle to
+    round-off, fields and sampled stress and profile."""
+    cell = I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=bc, u_wall=0.01 if bc else 0.0)
+    ra, rb = I.random_fields(nx, ny, seed=nx + ny)
+    ux = uy = None
+    if bc:
+        ux, uy = I.couette_velocity(nx, ny, 0.01)
+    with lattice([cell], "fp64", "tiled", (tile, 8)) as lat:
+        assert lat.kernel() == ("tiled", tile, 8)
+        lat.init_fields(ra, rb, ux, uy).set_sampling(10, 5).step(30)
+        ga, gb, _, _ = lat.fields()
+        sigma, S, _ = lat.shear_stress()
+        ub, ns = lat.profile()
+    (r,) = oracle_runs([cell], ra, rb, ux, uy, steps=30, sampling=(10, 5))
+    oa, ob, _, _ = r.fields()
+    assert max_abs(ga[0], oa) <= 1e-13 and max_abs(gb[0], ob) <= 1e-13
+    osig, oS, _, oub = r.shear()
+    assert ns == 5
+    np.testing.assert_allclose(ub[0], oub, rtol=0, atol=1e-14)
+    if bc:
+        assert sigma[0] == pytest.approx(osig, rel=1e-9, abs=1e-16)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 4e-7), ("fp16", 2.0 ** -11)])
+def test_tiled_narrow_last_strip_reduced_precision(prec, tol):
+    cell = I.make_cell("paper", nx=200, ny=32, g_ab=0.405, bc=1, u_wall=0.02)
+    from oracle import lb as orc
+    r = evolved_state(cell, 200, seed=44)
+    f0 = r.f.copy()
+    with lattice([cell], prec, "tiled", (128, 0)) as lat:
+        lat.set_populations(f0[None])
+        start = lat.get_populations()[0]
+        lat.step(1)
+        g1 = lat.get_populations()[0]
+    f1, _, _ = orc.step(cell, start)
+    if prec == "fp16":
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[None, :, None, None]
+        shift = w * np.array([cell.rho_bar_a, cell.rho_bar_b])[:, None, None, None]
+        gmag = np.maximum(np.abs(g1 - shift), np.abs(f1 - shift))
+        assert np.all(np.abs(g1 - f1) <= tol * gmag + 5e-7)
+    else:
+        assert max_abs(g1, f1) <= tol
