@@ -195,7 +195,9 @@ __device__ __noinline__ void profile_row_sums(const C* ub, int lane, double* __r
     if (t == 0 && (x0 >> 5) + grp < nbx) prof_part[((long long)cell * nbx + (x0 >> 5) + grp) * g.ny + y] = part;
 }
 
-template <class T, int TX, bool SAMPLE>
+// FULL: every strip is TX columns wide (nx a multiple of TX); otherwise the
+// last strip is narrower and its extra columns are masked.
+template <class T, int TX, bool SAMPLE, bool FULL>
 __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
                                                             const __grid_constant__ CUtensorMap tm_halo,
                                                             T* __restrict__ fout, Geom g, int bc, int ty,
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
         // columns of this strip inside the lattice (the last strip of a width that
         // is not a multiple of TX is narrower; the TMA box reads zeros beyond it)
-        const int wv = min(TX, g.nx - x0);
-        const bool act = c0 < wv;  // both columns of the pair (wv is even)
+        const int wv = FULL ? TX : min(TX, g.nx - x0);
+        const bool act = FULL || c0 < wv;  // both columns of the pair (wv is even)
         // destination columns of the two sites x, x+1 shifted by -1/0/+1 (periodic)
         const int x = x0 + c0;
         const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p2 = x + 2 == g.nx ? 0 : x + 2;
@@ -611,30 +613,34 @@ bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
 
 int tiled_partials_nbx(const Geom& g, int) { return (g.nx + 31) / 32; }
 
-template <class T, int TX, bool S>
-static const void* kernel_ptr()
+template <class T, int TX>
+static const void* kernel_ptr(bool sample, bool full)
 {
-    return reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, S>);
+    if (full)
+        return sample ? reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, true, true>)
+                      : reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, false, true>);
+    return sample ? reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, true, false>)
+                  : reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, false, false>);
 }
 
 template <class T>
-static const void* pick(int tx, bool sample)
+static const void* pick(int tx, bool sample, bool full)
 {
     switch (tx) {
-    case 32: return sample ? kernel_ptr<T, 32, true>() : kernel_ptr<T, 32, false>();
-    case 64: return sample ? kernel_ptr<T, 64, true>() : kernel_ptr<T, 64, false>();
-    case 128: return sample ? kernel_ptr<T, 128, true>() : kernel_ptr<T, 128, false>();
-    default: return sample ? kernel_ptr<T, 256, true>() : kernel_ptr<T, 256, false>();
+    case 32: return kernel_ptr<T, 32>(sample, full);
+    case 64: return kernel_ptr<T, 64>(sample, full);
+    case 128: return kernel_ptr<T, 128>(sample, full);
+    default: return kernel_ptr<T, 256>(sample, full);
     }
 }
 
-static const void* pick_any(int prec, int tx, bool sample)
+static const void* pick_any(int prec, int tx, bool sample, bool full)
 {
     switch (prec) {
-    case LB_FP32: return pick<float>(tx, sample);
-    case LB_FP64: return pick<double>(tx, sample);
-    case LB_FP16_SHIFTED_SR: return pick<half_sr>(tx, sample);
-    default: return pick<__half>(tx, sample);
+    case LB_FP32: return pick<float>(tx, sample, full);
+    case LB_FP64: return pick<double>(tx, sample, full);
+    case LB_FP16_SHIFTED_SR: return pick<half_sr>(tx, sample, full);
+    default: return pick<__half>(tx, sample, full);
     }
 }
 
@@ -686,7 +692,7 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int occ = 1;
     for (int s = 0; s < 2; ++s) {
-        const void* k = pick_any(prec, tile_x, s == 1);
+        const void* k = pick_any(prec, tile_x, s == 1, g.nx % tile_x == 0);
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess) {
             cudaGetLastError();
             if (err_msg) *err_msg = "cudaFuncSetAttribute(max dynamic smem) failed";
@@ -726,7 +732,7 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
                               double* wall_part, unsigned* err, cudaStream_t st, int* n_launches)
 {
     T* dst = reinterpret_cast<T*>(p->f[1 - src]);
-    const void* k = pick<T>(p->tx, sample);
+    const void* k = pick<T>(p->tx, sample, p->g.nx % p->tx == 0);
     Geom g = p->g;
     int bc = p->bc, ty = p->ty, ns = p->n_strips, nseg = p->n_seg;
     uint32_t skip = p->skip_row;
