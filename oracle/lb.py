@@ -20,7 +20,7 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("tau", C.c_double), ("rho0", C.c_double),
                 ("g_aa1", C.c_double), ("g_aa2", C.c_double), ("g_bb1", C.c_double),
                 ("g_bb2", C.c_double), ("g_ab", C.c_double), ("u_wall", C.c_double),
-                ("f0", C.c_double), ("bc", C.c_int)]
+                ("f0", C.c_double), ("bc", C.c_int), ("tau_b", C.c_double)]
 
 
 class Obs(C.Structure):
@@ -61,7 +61,8 @@ def _ptr(a):
 def params(cell) -> Params:
     """Params from an inputs.CellParams (or any object with the same fields)."""
     return Params(cell.nx, cell.ny, cell.tau, cell.rho0, cell.g_aa1, cell.g_aa2, cell.g_bb1,
-                  cell.g_bb2, cell.g_ab, cell.u_wall, getattr(cell, "f0", 0.0), cell.bc)
+                  cell.g_bb2, cell.g_ab, cell.u_wall, getattr(cell, "f0", 0.0), cell.bc,
+                  getattr(cell, "tau_b", 0.0))
 
 
 def _f64(a, shape):

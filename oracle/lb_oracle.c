@@ -40,7 +40,14 @@
  *  - the Kolmogorov forcing of section "Numerical Results", F_x(y) = F0 sin(k_f y),
  *    k_f = 2 pi / L, is a force density shared by the species in proportion to
  *    their density (F_s gains (rho_s / rho) F_x), so it shifts both species'
- *    equilibrium velocities by tau F_x / rho.
+ *    equilibrium velocities by tau F_x / rho;
+ *  - a relaxation time per species (the coupling-dependent relaxation time the
+ *    footnote of section "Numerical Results" leaves unexplored; all the paper's
+ *    runs share tau = 1): species s relaxes with tau_s, is shifted by
+ *    tau_s F_s / rho_s, and u is the common velocity of the two relaxations,
+ *    u = (sum_s j_s / tau_s) / (sum_s rho_s / tau_s) (Shan and Doolen, J. Stat.
+ *    Phys. 81 (1995) 379), which equals j / rho when the times are equal and
+ *    keeps the collision from creating momentum when they are not.
  *
  * Layout of a population array: [species s=0(A),1(B)][i=0..8][y][x], x fastest.
  * D2Q9 order: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
@@ -64,6 +71,7 @@ typedef struct {
     double u_wall;
     double f0;  /* Kolmogorov body force F_x(y) = f0 sin(2 pi y / ny) */
     int bc;     /* 0: periodic in x and y; 1: Couette (periodic x, walls in y) */
+    double tau_b; /* relaxation time of species B; 0: tau (one time for both) */
 } orc_params;
 
 /* Per-step observables of one sampled step (all FP64). */
@@ -173,8 +181,22 @@ void orc_equilibrium(const orc_params* p, const double* rho_a, const double* rho
 
 /* Moments: rho_s = sum_i f_is; j = sum_s sum_i f_is c_i, taken as differences of
  * opposite populations so that a state at rest gives exactly j = 0. */
+/* Relaxation time of species s: tau for A; tau_b for B, or tau when tau_b is 0. */
+static double tau_of(const orc_params* p, int s)
+{
+    return s == 1 && p->tau_b != 0.0 ? p->tau_b : p->tau;
+}
+
+/* The common velocity u = (j_A / tau_A + j_B / tau_B) / (rho_A / tau_A + rho_B / tau_B)
+ * multiplied through by tau_A: u = (j_A + r j_B) / (rho_A + r rho_B), r = tau_A / tau_B.
+ * With one relaxation time r = 1 and this is u = j / rho bit for bit. */
+static double mix_ratio(const orc_params* p)
+{
+    return tau_of(p, 0) / tau_of(p, 1);
+}
+
 static void site_moments(const orc_params* p, const double* f, int x, int y,
-                         double rho[2], double j[2])
+                         double rho[2], double j[2], double jw[2])
 {
     j[0] = 0.0;
     j[1] = 0.0;
@@ -192,6 +214,11 @@ static void site_moments(const orc_params* p, const double* f, int x, int y,
     }
     j[0] = jx_s[0] + jx_s[1];
     j[1] = jy_s[0] + jy_s[1];
+    if (jw) {
+        const double r = mix_ratio(p);
+        jw[0] = jx_s[0] + r * jx_s[1];
+        jw[1] = jy_s[0] + r * jy_s[1];
+    }
 }
 
 void orc_moments(const orc_params* p, const double* f, double* rho_a, double* rho_b,
@@ -200,7 +227,7 @@ void orc_moments(const orc_params* p, const double* f, double* rho_a, double* rh
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             double rho[2], j[2];
-            site_moments(p, f, x, y, rho, j);
+            site_moments(p, f, x, y, rho, j, NULL);
             size_t k = IDX(p, x, y);
             if (rho_a) rho_a[k] = rho[0];
             if (rho_b) rho_b[k] = rho[1];
@@ -280,10 +307,11 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
 {
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny;
-    const double tau = p->tau, rho0 = p->rho0;
+    const double rho0 = p->rho0, rmix = mix_ratio(p);
     double* rho = (double*)malloc(2 * n * sizeof(double));
     double* psi = (double*)malloc(2 * n * sizeof(double));
     double* jj = (double*)malloc(2 * n * sizeof(double));
+    double* jw = (double*)malloc(2 * n * sizeof(double)); /* numerator of the common velocity */
     double* fst = (double*)malloc(18 * n * sizeof(double)); /* post-collision f* */
     double* uphys = (double*)malloc(n * sizeof(double));
 
@@ -291,13 +319,15 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
-            double r[2], j[2];
-            site_moments(p, f_in, x, y, r, j);
+            double r[2], j[2], w[2];
+            site_moments(p, f_in, x, y, r, j, w);
             size_t k = IDX(p, x, y);
             rho[k] = r[0];
             rho[n + k] = r[1];
             jj[k] = j[0];
             jj[n + k] = j[1];
+            jw[k] = w[0];
+            jw[n + k] = w[1];
             psi[k] = psi_of(r[0], rho0);
             psi[n + k] = psi_of(r[1], rho0);
         }
@@ -308,7 +338,8 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
         for (int x = 0; x < nx; ++x) {
             size_t k = IDX(p, x, y);
             double rtot = rho[k] + rho[n + k];
-            double u[2] = {jj[k] / rtot, jj[n + k] / rtot};
+            double rw = rho[k] + rmix * rho[n + k];
+            double u[2] = {jw[k] / rw, jw[n + k] / rw}; /* j / rho for one relaxation time */
             double Ftot[2] = {0.0, 0.0};
             const double pi = 3.14159265358979323846;
             const double fx_body = p->f0 == 0.0 ? 0.0 : p->f0 * sin(2.0 * pi * y / p->ny);
@@ -318,6 +349,7 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
                 coupling(p, s, &ga, &gr);
                 double rs = rho[s * n + k];
                 double por = psi_over_rho(rs, rho0);
+                const double tau = tau_of(p, s);
                 double us[2];
                 for (int a = 0; a < 2; ++a) {
                     /* F_s and the shift tau F_s / rho_s, without dividing by rho_s */
@@ -387,6 +419,7 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
     free(rho);
     free(psi);
     free(jj);
+    free(jw);
     free(fst);
     free(uphys);
 }
@@ -427,10 +460,11 @@ int orc_step_slab(const orc_params* p, int y0, int rows, const double* f_in, dou
     const int nx = p->nx, ny = p->ny, nr = rows + 4;
     if (rows < 1 || y0 < 0 || y0 + rows > ny || (p->bc == 0 && nr > ny)) return -1;
     const size_t n = (size_t)nx * nr;
-    const double tau = p->tau, rho0 = p->rho0;
+    const double rho0 = p->rho0, rmix = mix_ratio(p);
     double* rho = (double*)calloc(2 * n, sizeof(double));
     double* psi = (double*)calloc(2 * n, sizeof(double));
     double* jj = (double*)calloc(2 * n, sizeof(double));
+    double* jw = (double*)calloc(2 * n, sizeof(double));
     double* fst = (double*)calloc(18 * n, sizeof(double));
     double* uphys = (double*)calloc(n, sizeof(double));
 
@@ -453,6 +487,8 @@ int orc_step_slab(const orc_params* p, int y0, int rows, const double* f_in, dou
             }
             jj[k] = jx_s[0] + jx_s[1];
             jj[n + k] = jy_s[0] + jy_s[1];
+            jw[k] = jx_s[0] + rmix * jx_s[1];
+            jw[n + k] = jy_s[0] + rmix * jy_s[1];
         }
 
     /* 3-6. forces, shifted equilibrium and collision on the slab's own rows */
@@ -461,7 +497,8 @@ int orc_step_slab(const orc_params* p, int y0, int rows, const double* f_in, dou
             const int y = y0 + yl, e = yl + 2;
             size_t k = (size_t)e * nx + x;
             double rtot = rho[k] + rho[n + k];
-            double u[2] = {jj[k] / rtot, jj[n + k] / rtot};
+            double rw = rho[k] + rmix * rho[n + k];
+            double u[2] = {jw[k] / rw, jw[n + k] / rw};
             double Ftot[2] = {0.0, 0.0};
             const double pi = 3.14159265358979323846;
             const double fx_body = p->f0 == 0.0 ? 0.0 : p->f0 * sin(2.0 * pi * y / p->ny);
@@ -490,6 +527,7 @@ int orc_step_slab(const orc_params* p, int y0, int rows, const double* f_in, dou
                 coupling(p, s, &ga, &gr);
                 double rs = rho[s * n + k];
                 double por = psi_over_rho(rs, rho0);
+                const double tau = tau_of(p, s);
                 double us[2];
                 for (int a = 0; a < 2; ++a) {
                     double G = ga * S1[a] + gr * S2[a];
@@ -556,6 +594,7 @@ int orc_step_slab(const orc_params* p, int y0, int rows, const double* f_in, dou
     free(rho);
     free(psi);
     free(jj);
+    free(jw);
     free(fst);
     free(uphys);
     return 0;

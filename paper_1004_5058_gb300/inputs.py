@@ -50,6 +50,8 @@ class CellParams:
     f0: Kolmogorov body force F_x(y) = f0 sin(2 pi y / ny) (section "Numerical
     Results"), shared by the species in proportion to their density.
     rho_bar_a/b: reference densities of the FP16 shifted storage f_i - w_i*rho_bar.
+    tau_b: relaxation time of species B, 0 for tau (the paper uses one time,
+    tau = 1, and leaves a coupling-dependent one unexplored); tau is species A's.
     """
     nx: int = 64
     ny: int = 64
@@ -65,6 +67,7 @@ class CellParams:
     rho_bar_a: float = 0.6
     rho_bar_b: float = 0.6
     bc: int = 0
+    tau_b: float = 0.0
 
     def as_dict(self):
         return asdict(self)

@@ -335,6 +335,106 @@ def test_shear_wave_viscosity(tau):
     assert rate == pytest.approx(nu * k * k, rel=2e-2)
 
 
+# ------------------------------------------------ two relaxation times --
+# A relaxation time per species (the coupling-dependent relaxation time the
+# footnote of section "Numerical Results" leaves unexplored): species s relaxes
+# with tau_s around the common velocity u = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s).
+def species_momenta(f):
+    """j_s per species from populations [2, 9, ny, nx] (plain D2Q9 moments)."""
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=np.float64)
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=np.float64)
+    return np.einsum("i,siyx->syx", cx, f), np.einsum("i,siyx->syx", cy, f), f.sum(axis=1)
+
+
+def shear_wave_rate(tau_a, tau_b, rho_a, rho_b, L=64):
+    """Decay rate / k^2 of u_x = U sin(k y) in a uniform mixture at G = 0."""
+    k = 2 * math.pi / L
+    c = I.make_cell("ideal", nx=4, ny=L, tau=tau_a, tau_b=tau_b)
+    y = np.arange(L, dtype=np.float64)
+    ux = np.tile((1e-5 * np.sin(k * y))[:, None], (1, 4))
+    r = lb.Run(c, np.full((L, 4), rho_a), np.full((L, 4), rho_b), ux, np.zeros_like(ux))
+
+    def amp():
+        _, _, u, _ = r.fields()
+        return 2.0 / L * np.sum(u.mean(axis=1) * np.sin(k * y))
+
+    r.step(50)
+    a0 = amp()
+    r.step(400)
+    return -math.log(amp() / a0) / 400 / (k * k)
+
+
+def test_two_tau_equal_times_are_the_single_time_model_bitwise():
+    """tau_b = tau is the paper's model (tau_b = 0 means the same), bit for bit,
+    with interactions, walls and forcing."""
+    ra, rb = I.random_fields(24, 20, seed=31)
+    ux, uy = I.couette_velocity(24, 20, 0.01)
+    out = []
+    for tb in (0.0, 0.8):
+        c = I.make_cell("paper", nx=24, ny=20, g_ab=0.405, bc=1, u_wall=0.01, tau=0.8, tau_b=tb)
+        out.append(lb.Run(c, ra[0], rb[0], ux[0], uy[0]).step(30).f)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_two_tau_momentum_conserved_periodic():
+    """With tau_A != tau_B the collision changes the total momentum by
+    sum_s (rho_s u - j_s)/tau_s + sum_s F_s; the common velocity makes the first
+    sum vanish and the pair-antisymmetric forces make the second vanish, so P
+    stays constant although the species move at different velocities (a
+    barycentric u = j/rho, or tau_s swapped in the weights, breaks this)."""
+    c = I.make_cell("paper", nx=32, ny=32, g_ab=0.405, tau=0.7, tau_b=1.3)
+    ra, rb = I.random_fields(32, 32, seed=12)
+    r = lb.Run(c, ra[0], rb[0])
+    r.step(300)
+    m = ra.sum() + rb.sum()
+    assert abs(r.last["mom"][0]) / m < 1e-13 and abs(r.last["mom"][1]) / m < 1e-13
+    jx, jy, rho = species_momenta(r.f)
+    slip = np.abs(jx[0] / rho[0] - jx[1] / rho[1]).max()
+    assert slip > 1e-4  # the species do drift apart: the test is not vacuous
+
+
+def test_two_tau_uniform_state_stays_uniform():
+    c = I.make_cell("paper", nx=16, ny=12, g_ab=0.405, tau=0.7, tau_b=1.3)
+    r = lb.Run(c, np.full((12, 16), 0.6), np.full((12, 16), 0.55))
+    r.step(40)
+    ra, rb, ux, uy = r.fields()
+    assert np.ptp(ra) == 0.0 and np.ptp(rb) == 0.0
+    assert np.all(ux == 0.0) and np.all(uy == 0.0)
+
+
+@pytest.mark.parametrize("rho_a,rho_b", [(0.6, 0.0), (0.0, 0.6)], ids=["only_A", "only_B"])
+def test_two_tau_single_species_viscosity(rho_a, rho_b):
+    """A species alone shears with its own nu_s = (tau_s - 1/2)/3 whatever the
+    other's time (swapped times would give 0.3 instead of 0.1 and vice versa)."""
+    nu = shear_wave_rate(0.8, 1.4, rho_a, rho_b)
+    tau = 0.8 if rho_a > 0 else 1.4
+    assert nu == pytest.approx((tau - 0.5) / 3.0, rel=5e-3)
+
+
+@pytest.mark.parametrize("tau_a,tau_b,rho_a,rho_b", [(0.8, 1.4, 0.8, 0.4), (1.0, 0.7, 0.3, 0.9)])
+def test_two_tau_mixture_viscosity(tau_a, tau_b, rho_a, rho_b):
+    """Mixture with a common velocity: nu = (sum_s x_s tau_s - 1/2)/3, x_s =
+    rho_s/rho (Shan and Doolen 1995).  Swapping the times moves nu by 40 % and
+    23 % in these two cases."""
+    x = rho_a / (rho_a + rho_b)
+    assert shear_wave_rate(tau_a, tau_b, rho_a, rho_b) == pytest.approx(
+        (x * tau_a + (1 - x) * tau_b - 0.5) / 3.0, rel=5e-3)
+
+
+def test_two_tau_species_swap():
+    """Exchanging A and B together with their couplings and relaxation times
+    exchanges the populations (to round-off: the common velocity is evaluated
+    as (j_A + r j_B)/(rho_A + r rho_B) with r = tau_A/tau_B on one side and
+    1/r on the other)."""
+    ra, rb = I.random_fields(20, 18, seed=41)
+    a = I.make_cell("paper", nx=20, ny=18, g_ab=0.405, tau=0.75, tau_b=1.2)
+    b = I.make_cell("paper", nx=20, ny=18, g_ab=0.405, tau=1.2, tau_b=0.75,
+                    g_aa1=a.g_bb1, g_aa2=a.g_bb2, g_bb1=a.g_aa1, g_bb2=a.g_aa2)
+    fa = lb.Run(a, ra[0], rb[0]).step(60).f
+    fb = lb.Run(b, rb[0], ra[0]).step(60).f
+    assert np.abs(fa - fb[::-1]).max() <= 1e-13
+
+
 # -------------------------------------------------------- Herschel-Bulkley --
 @pytest.mark.parametrize("sy,A,beta", [(1.5e-4, 2e-2, 0.5), (1.5e-4, 5e-3, 0.25), (2e-5, 0.1, 1.3)])
 def test_hb_oracle_recovers_noiseless(sy, A, beta):

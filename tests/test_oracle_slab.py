@@ -41,6 +41,16 @@ def test_slabs_equal_whole_cell_bitwise(bc, f0, world):
     assert obs["pi_top"] == pytest.approx(o["pi_top"], rel=1e-12, abs=1e-18)
 
 
+def test_slabs_two_relaxation_times():
+    """The slab step restates the per-species relaxation times too."""
+    from oracle import slab
+    cell, f = case(1, seed=5)
+    cell.tau, cell.tau_b = 0.7, 1.3
+    ref, _ = whole(cell, f, 10)
+    got, _ = slab.run_in_process(cell, f, 10, 3)
+    assert np.array_equal(got, ref)
+
+
 def test_ragged_split():
     from oracle import slab
     assert slab.split_rows(26, 4) == [(0, 7), (7, 7), (14, 6), (20, 6)]
