@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--every", type=int, default=10, help="sampling interval of the FP64 reductions")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp16sr", "fp64"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "tiled"])
+    ap.add_argument("--tau-b", type=float, default=0.0,
+                    help="relaxation time of species B (0: tau = 1 for both, the paper's model); "
+                         "a time per species runs the common-velocity variant")
     ap.add_argument("--tile", default="", help="TXxTY for the tiled kernel (default: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -76,10 +79,10 @@ def dist_env():
     return rank_world()
 
 
-def workload_cells(nx, ny, n_cells, rank):
+def workload_cells(nx, ny, n_cells, rank, tau_b=0.0):
     from paper_1004_5058_gb300 import inputs as I
     speeds = I.log_spaced(1e-4, 1e-2, n_cells) if n_cells > 1 else [1e-3]
-    return [I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=u) for u in speeds]
+    return [I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=u, tau_b=tau_b) for u in speeds]
 
 
 def workload_fields(nx, ny, cells, seed):
@@ -182,6 +185,7 @@ def workload_config(args):
             "cells": n_cells, "nx": nx, "ny": ny, "lattice_steps_per_step": chunk,
             "sampling_every": args.every, "precision": args.precision,
             "couplings": "paper footnote, G_AB=0.405", "u_wall": "1e-4..1e-2 log",
+            "tau": "1 (both species)" if args.tau_b == 0 else "A 1, B %g (common-velocity variant)" % args.tau_b,
             "l2": "inputs larger than L2 (%.2f GB populations, ping-pong)" % (bytes_pop / 1e9)}
 
 
@@ -189,7 +193,7 @@ def cpu_baseline(args, seconds):
     """The FP64 oracle, as it stands, on this host's cores: one cell of the
     workload, as many time steps as fit in about `seconds`."""
     from oracle import lb as orc
-    cells = workload_cells(args.nx, args.ny, args.cells, 0)
+    cells = workload_cells(args.nx, args.ny, args.cells, 0, args.tau_b)
     cell = cells[len(cells) // 2]
     ra, rb, ux, uy = workload_fields(args.nx, args.ny, [cell], seed=1004)
     run = orc.Run(cell, ra[0], rb[0], ux[0], uy[0])
@@ -247,7 +251,7 @@ def run_reference(args):
     K, W = args.steps, args.warmup
     per_step = max(1.0, min(args.cpu_seconds, 60.0 / max(1, K + W)))
     from oracle import lb as orc
-    cells = workload_cells(args.nx, args.ny, args.cells, 0)
+    cells = workload_cells(args.nx, args.ny, args.cells, 0, args.tau_b)
     cell = cells[len(cells) // 2]
     ra, rb, ux, uy = workload_fields(args.nx, args.ny, [cell], seed=1004)
     run = orc.Run(cell, ra[0], rb[0], ux[0], uy[0])
@@ -300,7 +304,7 @@ def run_ours(args):
     from paper_1004_5058_gb300.dist import max_over_ranks
 
     nx, ny, n_cells, chunk = args.nx, args.ny, args.cells, args.chunk
-    cells = workload_cells(nx, ny, n_cells, rank)
+    cells = workload_cells(nx, ny, n_cells, rank, args.tau_b)
     ra, rb, ux, uy = workload_fields(nx, ny, cells, seed=1004 + rank)
     lat = Lattice(cells, args.precision)
     lat.init_fields(ra, rb, ux, uy)

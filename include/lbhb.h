@@ -80,7 +80,17 @@ typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_GENERIC = 1, LB_KERNEL_TILED = 2 } 
  *            section "Numerical Results" (force density; each species receives
  *            rho_s / rho of it); 0 for none
  *   rho_bar_a, rho_bar_b  shift reference of LB_FP16_SHIFTED storage
- *   bc       lb_bc */
+ *   bc       lb_bc
+ *   tau_b    relaxation time of species B (> 1/2), or 0 for tau.  The paper runs
+ *            one time for both species (tau = 1) and names a coupling-dependent
+ *            one as unexplored (footnote of section "Numerical Results").  With
+ *            tau_b != tau, tau is species A's, each species relaxes with its own
+ *            time and is shifted by tau_s F_s / rho_s, and u in Eq. (be) is the
+ *            common velocity (j_A/tau_A + j_B/tau_B) / (rho_A/tau_A + rho_B/tau_B)
+ *            of Shan and Doolen (J. Stat. Phys. 81, 1995), which keeps the
+ *            collision from creating momentum; tau_b = tau gives the one-time
+ *            model bit for bit.  Last field, so callers that fill the fields
+ *            before it and zero the rest get the paper's model. */
 typedef struct {
     int nx, ny;
     double tau, rho0;
@@ -89,6 +99,7 @@ typedef struct {
     double f0;
     double rho_bar_a, rho_bar_b;
     int bc;
+    double tau_b;
 } lb_cell_params;
 
 /* Creates a handle for n_cells cells (n_cells >= 1; nx >= 5, ny >= 5; same nx, ny,
@@ -187,10 +198,11 @@ long long lb_steps_done(const lb_handle* h);
  * equals the run continued after lb_save bit for bit.  A file that is not a
  * checkpoint, is truncated or fails its checksum gives LB_ERR_INVALID and
  * leaves the handle without a loaded state.  Both calls are synchronous; the
- * file is binary in this machine's byte order (format version 1: a 128-byte
- * header, 14 float64 per cell, the float64 time sums, then the populations
+ * file is binary in this machine's byte order (format version 2: a 128-byte
+ * header, 15 float64 per cell, the float64 time sums, then the populations
  * [cell][s][i][y][x] without row padding, FNV-1a 64 checksum of the payload in
- * the header). */
+ * the header).  lb_load also reads version 1 files (14 float64 per cell, no
+ * tau_b: one relaxation time). */
 lb_status lb_save(lb_handle* h, const char* path);
 lb_status lb_load(lb_handle* h, const char* path);
 

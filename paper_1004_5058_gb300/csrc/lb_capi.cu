@@ -126,8 +126,13 @@ static void release(lb_handle* h)
 template <class C>
 static void fill(ParamSet<C>& d, const lb_cell_params& c)
 {
+    const double tau_b = c.tau_b == 0.0 ? c.tau : c.tau_b;
     d.tau = C(c.tau);
     d.omega = C(1.0 / c.tau);
+    d.tau_b = C(tau_b);
+    d.omega_b = C(1.0 / tau_b);
+    d.mix[0] = C(c.tau / tau_b);
+    d.mix[1] = C(tau_b / c.tau);
     d.rho0 = C(c.rho0);
     d.inv_rho0 = C(1.0 / c.rho0);
     d.gab_over_rho0 = C(c.g_ab / c.rho0);
@@ -247,11 +252,12 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
 }
 
 // ------------------------------------------------------------ checkpoints --
-// File layout (version 1, this machine's byte order):
+// File layout (version 2, this machine's byte order):
 //   header  128 bytes: magic "LBHBCKPT", u32 version, u32 header bytes, i32
 //           n_cells, nx, ny, bc, precision, element bytes, i64 t, start,
 //           every, n_samples, u64 payload bytes, u64 FNV-1a 64 of the payload
-//   payload 14 float64 per cell (lb_cell_params in declaration order), the
+//   payload 15 float64 per cell (lb_cell_params in declaration order; version
+//           1 files hold the first 14, without tau_b, and load as tau_b = 0), the
 //           time sums of the line profile [cell][ny] and of the wall momenta
 //           [cell][2] (float64), the populations [cell][s][i][y][x] in the
 //           storage precision without row padding
@@ -279,15 +285,19 @@ struct Fnv {
     }
 };
 
-void cell_to_doubles(const lb_cell_params& c, double v[14])
+constexpr int kCellDoubles = 15;  // per cell in version 2 (14 in version 1)
+
+void cell_to_doubles(const lb_cell_params& c, double v[kCellDoubles])
 {
-    const double a[14] = {(double)c.nx, (double)c.ny, c.tau, c.rho0, c.g_aa1, c.g_aa2, c.g_bb1,
-                          c.g_bb2, c.g_ab, c.u_wall, c.f0, c.rho_bar_a, c.rho_bar_b, (double)c.bc};
-    for (int k = 0; k < 14; ++k) v[k] = a[k];
+    const double a[kCellDoubles] = {(double)c.nx, (double)c.ny, c.tau, c.rho0, c.g_aa1, c.g_aa2, c.g_bb1,
+                                    c.g_bb2, c.g_ab, c.u_wall, c.f0, c.rho_bar_a, c.rho_bar_b, (double)c.bc,
+                                    c.tau_b};
+    for (int k = 0; k < kCellDoubles; ++k) v[k] = a[k];
 }
 
-// false if the integer fields are not small whole numbers
-bool cell_from_doubles(const double v[14], lb_cell_params* out)
+// false if the integer fields are not small whole numbers; v[14] (tau_b) is
+// read only from version 2 files (the caller passes 0 for version 1)
+bool cell_from_doubles(const double v[kCellDoubles], lb_cell_params* out)
 {
     for (int k : {0, 1, 13})
         if (!(v[k] >= 0.0 && v[k] <= 2147483647.0) || v[k] != std::floor(v[k])) return false;
@@ -306,6 +316,7 @@ bool cell_from_doubles(const double v[14], lb_cell_params* out)
     c.rho_bar_a = v[11];
     c.rho_bar_b = v[12];
     c.bc = (lb_bc)(int)v[13];
+    c.tau_b = v[14];
     return true;
 }
 
@@ -336,6 +347,10 @@ static bool cells_valid(const lb_cell_params* cells, int n_cells, char* why, siz
         }
         if (!(p.tau > 0.5) || !std::isfinite(p.tau)) {
             snprintf(why, n, "cell %d tau=%g must exceed 1/2", c, p.tau);
+            return false;
+        }
+        if (p.tau_b != 0.0 && (!(p.tau_b > 0.5) || !std::isfinite(p.tau_b))) {
+            snprintf(why, n, "cell %d tau_b=%g must exceed 1/2 (or be 0: tau)", c, p.tau_b);
             return false;
         }
         if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0)) {
@@ -939,7 +954,7 @@ lb_status lb_save(lb_handle* h, const char* path)
     CkptHeader hd;
     memset(&hd, 0, sizeof hd);
     memcpy(hd.magic, kMagic, 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.header_bytes = sizeof hd;
     hd.n_cells = h->n_cells;
     hd.nx = h->nx;
@@ -961,7 +976,7 @@ lb_status lb_save(lb_handle* h, const char* path)
         bytes += n;
     };
     for (int c = 0; c < h->n_cells; ++c) {
-        double v[14];
+        double v[kCellDoubles];
         cell_to_doubles(h->cells[c], v);
         put(v, sizeof v);
     }
@@ -998,7 +1013,7 @@ lb_status lb_load(lb_handle* h, const char* path)
     CkptHeader hd;
     if (fread(&hd, sizeof hd, 1, in.f) != 1 || memcmp(hd.magic, kMagic, 8) != 0)
         return fail(h, LB_ERR_INVALID, "lb_load: %s is not a checkpoint", path);
-    if (hd.version != 1 || hd.header_bytes != sizeof hd)
+    if ((hd.version != 1 && hd.version != 2) || hd.header_bytes != sizeof hd)
         return fail(h, LB_ERR_INVALID, "lb_load: checkpoint version %u not supported", hd.version);
     if (hd.n_cells != h->n_cells || hd.nx != h->nx || hd.ny != h->ny || hd.bc != h->bc ||
         hd.prec != (int32_t)h->prec || hd.elem != h->elem)
@@ -1024,9 +1039,10 @@ lb_status lb_load(lb_handle* h, const char* path)
     };
     std::vector<lb_cell_params> cells(h->n_cells);
     bool cells_ok = true;
+    const int per_cell = hd.version == 1 ? 14 : kCellDoubles;
     for (int c = 0; c < h->n_cells; ++c) {
-        double v[14];
-        get(v, sizeof v);
+        double v[kCellDoubles] = {};
+        get(v, sizeof(double) * per_cell);
         if (ok) cells_ok = cell_from_doubles(v, &cells[c]) && cells_ok;
     }
     std::vector<double> prof((size_t)h->n_cells * h->ny), wall((size_t)h->n_cells * 2);

@@ -48,7 +48,11 @@ __host__ __device__ constexpr double hs_w2(int k)
 // Per-cell parameters as stored on the device, in both compute precisions so
 // that FP32 kernels never touch the (slow) FP64 pipe for them.
 template <class C> struct ParamSet {
-    C tau, omega, rho0, inv_rho0, gab_over_rho0;
+    C tau, omega, rho0, inv_rho0, gab_over_rho0;  // tau, omega of species A
+    C tau_b, omega_b;  // species B (equal to tau, omega unless a time per species is set)
+    // weight of the other species' moments in the common velocity, seen from A and
+    // from B: mix[0] = tau_A / tau_B, mix[1] = tau_B / tau_A (both 1 for one time)
+    C mix[2];
     C g1[2], g2[2];  // G^a_ss, G^r_ss for s = A, B
     C u_wall;        // top wall +u_wall, bottom wall -u_wall (Couette)
     C rho_bar[2];    // FP16 shift reference
@@ -235,10 +239,12 @@ __device__ inline Sums<C> stencil_sums(const C d[12], const C e[4])
 //   F_s    = -psi_s (G^a S1 + G^r S2) - (G_AB/rho0) rho_s X       (Eq. (FFF))
 //   u_s    = u + tau F_s/rho_s = u - tau[(psi_s/rho_s)(G^a S1 + G^r S2) + (G_AB/rho0) X]
 //   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau, i = 1..8
+// (tau, omega: the species' own relaxation time and rate)
 //   f*_0s  = rho_s - sum_{i>=1} f*_is   (the same value in exact arithmetic)
 // f^eq_i = w_i rho_s (1 + 3 c_i.u_s + 4.5 (c_i.u_s)^2 - 1.5 u_s^2) is evaluated for
 // the pairs +-c_i together (even part + odd part).
-// u is the barycentric velocity j / (rho_A + rho_B) of both species.
+// u is the common velocity of both species: j / (rho_A + rho_B) for one
+// relaxation time (collide_site).
 // ax = F_x / rho is the Kolmogorov body force per unit total density: species s
 // receives rho_s ax of it (a share proportional to its density), which shifts
 // its equilibrium velocity by tau ax.
@@ -250,9 +256,9 @@ __device__ inline Sums<C> stencil_sums(const C d[12], const C e[4])
 // update is f*_i = f^eq_i exactly and f_i only enters through the moments.
 template <class C, bool UNIT = false>
 __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C uy, C ax, const Sums<C>& sm, C ga,
-                                       C gr, const ParamSet<C>& p, C fs[9], C* Fx, C* Fy)
+                                       C gr, C tau, C omega, const ParamSet<C>& p, C fs[9], C* Fx, C* Fy)
 {
-    const C tau = p.tau, omega = p.omega, gx = p.gab_over_rho0;
+    const C gx = p.gab_over_rho0;
     const C Gx = ga * sm.s1x + gr * sm.s2x;
     const C Gy = ga * sm.s1y + gr * sm.s2y;
     *Fx = -psi_s * Gx - gx * rho_s * sm.xx + rho_s * ax;
@@ -295,10 +301,10 @@ __device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C u
 // rounding) and so are the results; rho_s, psi_s, u and the forces are not scaled.
 template <class C, bool UNIT = false>
 __device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar, C psi_s, C ux, C uy, C ax,
-                                               const Sums<C>& sm, C ga, C gr, const ParamSet<C>& p, C gs[9],
-                                               C* Fx, C* Fy, C scale = C(1))
+                                               const Sums<C>& sm, C ga, C gr, C tau, C omega,
+                                               const ParamSet<C>& p, C gs[9], C* Fx, C* Fy, C scale = C(1))
 {
-    const C tau = p.tau, omega = p.omega, gx = p.gab_over_rho0;
+    const C gx = p.gab_over_rho0;
     const C Gx = ga * sm.s1x + gr * sm.s2x;
     const C Gy = ga * sm.s1y + gr * sm.s2y;
     *Fx = -psi_s * Gx - gx * rho_s * sm.xx + rho_s * ax;
@@ -342,25 +348,32 @@ template <class C> struct Collided {
     C Fx, Fy;
 };
 
-// Both species at one site: u = j / (rho_A + rho_B), then collide_species each.
+// Both species at one site: the common velocity u, then collide_species each.
+// With one relaxation time u = j / (rho_A + rho_B).  With a time per species u
+// is the Shan-Doolen common velocity (j_A/tau_A + j_B/tau_B) / (rho_A/tau_A +
+// rho_B/tau_B), taken as (j_A + r j_B) / (rho_A + r rho_B), r = tau_A/tau_B
+// (r = 1 gives the one-time velocity exactly), so that the collision conserves
+// the total momentum; the Kolmogorov force is still shared as rho_s / rho.
 template <class C>
 __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi[2],
                                     const Sums<C> sm[2], const ParamSet<C>& p, C fx_body, Collided<C>& out)
 {
-    const C jx = mom_x<C>(f[0]) + mom_x<C>(f[1]);
-    const C jy = mom_y<C>(f[0]) + mom_y<C>(f[1]);
-    const C inv_rho = fast_div<C>(C(1), rho[0] + rho[1]);
-    const C ux = jx * inv_rho, uy = jy * inv_rho;
-    const C ax = fx_body * inv_rho;
+    const C r = p.mix[0];
+    const C jx = mom_x<C>(f[0]) + r * mom_x<C>(f[1]);
+    const C jy = mom_y<C>(f[0]) + r * mom_y<C>(f[1]);
+    const C inv_rw = fast_div<C>(C(1), rho[0] + r * rho[1]);
+    const C ux = jx * inv_rw, uy = jy * inv_rw;
+    const C ax = r == C(1) ? fx_body * inv_rw : fx_body * fast_div<C>(C(1), rho[0] + rho[1]);
     C Fx[2], Fy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        if (p.omega == C(1))
-            collide_species<C, true>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p, out.fs[s],
-                                     &Fx[s], &Fy[s]);
+        const C tau = s ? p.tau_b : p.tau, omega = s ? p.omega_b : p.omega;
+        if (omega == C(1))
+            collide_species<C, true>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], tau, omega, p,
+                                     out.fs[s], &Fx[s], &Fy[s]);
         else
-            collide_species<C, false>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p, out.fs[s],
-                                      &Fx[s], &Fy[s]);
+            collide_species<C, false>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], tau, omega, p,
+                                      out.fs[s], &Fx[s], &Fy[s]);
     }
     out.Fx = Fx[0] + Fx[1];
     out.Fy = Fy[0] + Fy[1];

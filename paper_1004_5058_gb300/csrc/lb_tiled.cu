@@ -308,8 +308,6 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         // live in local memory)
         const ParamSet<C>& pg = params<C>(cells[cell]);
         ParamSet<C> p;
-        p.tau = pg.tau;
-        p.omega = pg.omega;
         p.rho0 = pg.rho0;
         p.inv_rho0 = pg.inv_rho0;
         p.gab_over_rho0 = pg.gab_over_rho0;
@@ -317,7 +315,12 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         p.f0 = pg.f0;
         p.two_over_ny = pg.two_over_ny;
         const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
-        const bool unit_omega = p.omega == C(1);  // tau = 1: f* = f^eq (uniform over the CTA)
+        // this lane's species relaxes with tau_s; mix weighs the partner species'
+        // moments in the common velocity (1, and one_time, for one relaxation time)
+        const C tau_s = sp ? pg.tau_b : pg.tau, omega_s = sp ? pg.omega_b : pg.omega;
+        const C mix = sp ? pg.mix[1] : pg.mix[0];
+        const bool one_time = pg.mix[0] == C(1);
+        const bool unit_omega = omega_s == C(1);  // tau_s = 1: f* = f^eq (uniform over each half-warp)
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
         // columns of this strip inside the lattice (the last strip of a width that
         // is not a multiple of TX is narrower; the TMA box reads zeros beyond it)
@@ -423,9 +426,10 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             C rho_s[2];
             Vec2<C>::ld(rho_ring + sp * SS + rr[2] * W + c0 + 2, rho_s[0], rho_s[1]);
             // window column of site o, offset dx: o + 2 + dx
-            C jx[2], jy[2], fs[2][9];
+            C jx[2], fs[2][9];  // jx: raw x-momentum of the site (observables)
             C Fx[2], Fy[2], inv_r[2];
             const C fx_body = body_force_x<C>(p, y);
+            const bool body_raw = !one_time && fx_body != C(0);  // the force needs the raw 1/rho
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
                 C dps[12], dro[4];
@@ -437,26 +441,31 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 }
                 const Sums<C> sm = stencil_sums<C>(dps, dro);
                 const C jx_s = mom_x<C>(f[o]), jy_s = mom_y<C>(f[o]);
-                jx[o] = (jx_s + __shfl_xor_sync(0xffffffffu, jx_s, 16)) * inv_scale;
-                jy[o] = (jy_s + __shfl_xor_sync(0xffffffffu, jy_s, 16)) * inv_scale;
-                const C rho_t = rho_s[o] + e[1][o + 2];
-                const C inv_rho = fast_div<C>(C(1), rho_t);
-                inv_r[o] = inv_rho;
-                const C ux = jx[o] * inv_rho, uy = jy[o] * inv_rho, ax = fx_body * inv_rho;
+                const C jx_p = __shfl_xor_sync(0xffffffffu, jx_s, 16), jy_p = __shfl_xor_sync(0xffffffffu, jy_s, 16);
+                // common velocity: (j_own + mix j_partner) / (rho_own + mix rho_partner)
+                const C jwx = (jx_s + mix * jx_p) * inv_scale, jwy = (jy_s + mix * jy_p) * inv_scale;
+                const C inv_rho = fast_div<C>(C(1), rho_s[o] + mix * e[1][o + 2]);
+                const C ux = jwx * inv_rho, uy = jwy * inv_rho;
+                C ax = fx_body * inv_rho;
+                if (body_raw) ax = fx_body * fast_div<C>(C(1), rho_s[o] + e[1][o + 2]);
+                if (SAMPLE) {
+                    jx[o] = one_time ? jwx : (jx_s + jx_p) * inv_scale;
+                    inv_r[o] = one_time ? inv_rho : fast_div<C>(C(1), rho_s[o] + e[1][o + 2]);
+                }
                 if (Store<T>::shifted) {
                     if (unit_omega)
                         collide_species_shifted<C, true>(f[o], rho_s[o], rho_bar, v[2][o + 2], ux, uy, ax, sm, ga, gr,
-                                                         p, fs[o], &Fx[o], &Fy[o], scale);
+                                                         tau_s, omega_s, p, fs[o], &Fx[o], &Fy[o], scale);
                     else
                         collide_species_shifted<C, false>(f[o], rho_s[o], rho_bar, v[2][o + 2], ux, uy, ax, sm, ga,
-                                                          gr, p, fs[o], &Fx[o], &Fy[o], scale);
+                                                          gr, tau_s, omega_s, p, fs[o], &Fx[o], &Fy[o], scale);
                 } else {
                     if (unit_omega)
-                        collide_species<C, true>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, p, fs[o], &Fx[o],
-                                                 &Fy[o]);
+                        collide_species<C, true>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, tau_s, omega_s,
+                                                 p, fs[o], &Fx[o], &Fy[o]);
                     else
-                        collide_species<C, false>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, p, fs[o],
-                                                  &Fx[o], &Fy[o]);
+                        collide_species<C, false>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, tau_s, omega_s,
+                                                  p, fs[o], &Fx[o], &Fy[o]);
                 }
             }
 

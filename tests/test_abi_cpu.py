@@ -34,7 +34,10 @@ def test_null_and_invalid_arguments_rejected_before_device_work(lib):
     cell = L.lb_cell_params(64, 64, 0.5, 0.83, -9, 8.1, -8, 7.1, 0.045, 0, 0, 0.6, 0.6, 0)
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID  # tau = 1/2
     assert b"tau" in lib.lb_last_error(None)
-    cell.tau, cell.nx = 1.0, 4
+    cell.tau, cell.tau_b = 1.0, 0.5
+    assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID  # tau_B = 1/2
+    assert b"tau_b" in lib.lb_last_error(None)
+    cell.tau_b, cell.nx = 0.0, 4
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID  # nx < 5
     cell.nx, cell.bc = 64, 7
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID

@@ -1,0 +1,193 @@
+"""GPU parity of the variant with a relaxation time per species (the
+coupling-dependent relaxation time the footnote of section "Numerical Results"
+leaves unexplored): each species relaxes with its own tau_s around the common
+velocity (j_A/tau_A + j_B/tau_B) / (rho_A/tau_A + rho_B/tau_B), against the FP64
+oracle on the same seeded inputs, through the C ABI.
+
+Tolerances are those of the one-time model (test_gpu_parity.py): the variant
+changes which numbers are combined, not the size of the rounding.  The pairs
+(tau_A, tau_B) = (1, 0.7) put the f* = f^eq path of species A and the general
+BGK update of species B into one warp; (0.8, 1.3) takes the general update for
+both.
+"""
+import struct
+
+import numpy as np
+import pytest
+
+from paper_1004_5058_gb300 import inputs as I
+from tests._util import max_abs, oracle_runs
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = ["generic", "tiled"]
+TAUS = [(1.0, 0.7), (0.8, 1.3)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def lattice(cells, prec, kernel):
+    from paper_1004_5058_gb300 import Lattice
+    lat = Lattice(cells, prec)
+    lat.set_kernel(kernel)
+    return lat
+
+
+def evolved(cell, steps, seed):
+    from oracle import lb as orc
+    ra, rb = I.random_fields(cell.nx, cell.ny, seed=seed)
+    ux = uy = None
+    if cell.bc == 1:
+        ux, uy = I.couette_velocity(cell.nx, cell.ny, cell.u_wall)
+        ux, uy = ux[0], uy[0]
+    return orc.Run(cell, ra[0], rb[0], ux, uy).step(steps).f.copy()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 2e-15), ("fp32", 4e-7), ("fp16", 2.0 ** -11), ("fp16sr", 2.0 ** -10)])
+@pytest.mark.parametrize("case", ["couette", "kolmogorov"])
+@pytest.mark.parametrize("taus", TAUS, ids=["1.0-0.7", "0.8-1.3"])
+def test_one_step_two_times(kernel, prec, tol, case, taus):
+    """One step from an evolved demixing state; the Kolmogorov case also takes
+    the body force's raw 1/rho (the common velocity uses weighted densities)."""
+    from oracle import lb as orc
+    bc = 1 if case == "couette" else 0
+    cell = I.make_cell("paper", nx=64, ny=48, g_ab=0.405, bc=bc, u_wall=0.02 if bc else 0.0,
+                       f0=0.0 if bc else I.kolmogorov_f0(0.05, 48), tau=taus[0], tau_b=taus[1])
+    f0 = evolved(cell, 300, seed=53)
+    with lattice([cell], prec, kernel) as lat:
+        lat.set_populations(f0[None])
+        start = lat.get_populations()[0]
+        lat.set_sampling(0, 1).step(1)
+        g1 = lat.get_populations()[0]
+        sigma, _, _ = lat.shear_stress()
+        ub, ns = lat.profile()
+    f1, obs, prof = orc.step(cell, start, want_profile=True)
+    if prec.startswith("fp16"):
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[None, :, None, None]
+        shift = w * np.array([cell.rho_bar_a, cell.rho_bar_b])[:, None, None, None]
+        gmag = np.maximum(np.abs(g1 - shift), np.abs(f1 - shift))
+        excess = np.abs(g1 - f1) - (tol * gmag + 5e-7)
+        assert excess.max() <= 0.0, (excess.max(), gmag.max())
+    else:
+        assert max_abs(g1, f1) <= tol
+    assert ns == 1
+    # the sampled profile uses the raw velocity (j + F/2)/rho, not the common one
+    otol = 1e-14 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(ub[0], prof / cell.nx, rtol=0, atol=otol)
+    if bc == 1:
+        assert abs(sigma[0] - 0.5 * (obs["pi_top"] - obs["pi_bot"]) / cell.nx) <= otol
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_1000_steps_two_times_conserve_momentum(kernel, prec, tol):
+    """64 x 64 periodic, footnote couplings, tau_A = 0.7, tau_B = 1.3: fields
+    against the oracle after 1000 steps; total momentum stays zero (the
+    common velocity), mass per species constant."""
+    cell = I.make_cell("paper", nx=64, ny=64, tau=0.7, tau_b=1.3)
+    ra, rb = I.random_fields(64, 64, seed=1004)
+    with lattice([cell], prec, kernel) as lat:
+        lat.init_fields(ra, rb).step(1000)
+        ga, gb, gu, gv = lat.fields()
+        mass, mom = lat.reductions()
+    (r,) = oracle_runs([cell], ra, rb, steps=1000)
+    oa, ob, ou, ov = r.fields()
+    assert max_abs(ga[0], oa) <= tol and max_abs(gb[0], ob) <= tol
+    assert max_abs(gu[0], ou) <= tol and max_abs(gv[0], ov) <= tol
+    m0 = (ra.sum(), rb.sum())
+    mtol = 1e-13 if prec == "fp64" else 1e-5
+    assert abs(mass[0, 0] - m0[0]) / m0[0] <= mtol and abs(mass[0, 1] - m0[1]) / m0[1] <= mtol
+    assert abs(mom[0]).max() / (m0[0] + m0[1]) <= (1e-13 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "fp64"])
+def test_equal_times_are_the_one_time_model_bitwise(kernel, prec):
+    """tau_b = tau runs the one-time arithmetic exactly (the weights are 1)."""
+    out = []
+    ra, rb = I.random_fields(64, 48, seed=7)
+    ux, uy = I.couette_velocity(64, 48, 0.01)
+    for tb in (0.0, 0.8):
+        cell = I.make_cell("paper", nx=64, ny=48, g_ab=0.405, bc=1, u_wall=0.01, tau=0.8, tau_b=tb)
+        with lattice([cell], prec, kernel) as lat:
+            lat.init_fields(ra, rb, ux, uy).set_sampling(10, 5).step(40)
+            out.append((lat.get_populations(), lat.shear_stress()))
+    assert np.array_equal(out[0][0], out[1][0])
+    for x, y in zip(out[0][1], out[1][1]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batch_mixing_one_and_two_times(kernel):
+    """Cells with one time and with two times in one launch, each against its
+    own oracle run (FP64), with stress and shear rate."""
+    nx, ny = 64, 32
+    spec = [(1e-3, 1.0, 0.0), (3e-3, 1.0, 0.7), (1e-2, 0.8, 1.3), (2e-2, 1.2, 1.2)]
+    cells = [I.make_cell("paper", nx=nx, ny=ny, bc=1, u_wall=u, g_ab=0.405, tau=ta, tau_b=tb)
+             for u, ta, tb in spec]
+    ra, rb = I.random_fields(nx, ny, n_cells=4, seed=19)
+    ux, uy = I.couette_velocity(nx, ny, [c.u_wall for c in cells], n_cells=4)
+    with lattice(cells, "fp64", kernel) as lat:
+        lat.init_fields(ra, rb, ux, uy).set_sampling(50, 10).step(120)
+        ga, gb, _, _ = lat.fields()
+        sigma, S, _ = lat.shear_stress()
+    for c, r in enumerate(oracle_runs(cells, ra, rb, ux, uy, steps=120, sampling=(50, 10))):
+        oa, ob, _, _ = r.fields()
+        assert max_abs(ga[c], oa) <= 1e-12 and max_abs(gb[c], ob) <= 1e-12
+        osig, oS, _, _ = r.shear()
+        assert sigma[c] == pytest.approx(osig, rel=1e-9, abs=1e-16)
+        assert S[c] == pytest.approx(oS, rel=1e-9, abs=1e-16)
+
+
+def fnv1a64(data: bytes) -> int:
+    h = 1469598103934665603
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_checkpoint_carries_tau_b_and_reads_version_1(tmp_path):
+    """A checkpoint holds tau_b: a handle created with one time continues with
+    the file's two.  A version-1 file (14 float64 per cell, written before
+    tau_b existed) still loads, and runs with one relaxation time."""
+    from paper_1004_5058_gb300 import Lattice
+    nx, ny = 64, 48
+    two = [I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=0.01, tau=0.8, tau_b=1.3)]
+    one = [I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=0.01, tau=0.8)]
+    ra, rb = I.random_fields(nx, ny, seed=23)
+    ux, uy = I.couette_velocity(nx, ny, 0.01)
+    path = tmp_path / "two.ckpt"
+    with Lattice(two, "fp32") as a:
+        a.init_fields(ra, rb, ux, uy).step(20)
+        f20 = a.get_populations()
+        a.save(path)
+        a.step(15)
+        fa = a.get_populations()
+    with Lattice(one, "fp32") as b:
+        b.load(path).step(15)
+        assert np.array_equal(b.get_populations(), fa)
+
+    # the same file as version 1: the cell records without tau_b
+    raw = path.read_bytes()
+    assert struct.unpack_from("<I", raw, 8)[0] == 2
+    n_cells = struct.unpack_from("<i", raw, 16)[0]
+    payload = raw[128:]
+    payload_v1 = b"".join(payload[c * 120:c * 120 + 112] for c in range(n_cells)) + payload[n_cells * 120:]
+    head = bytearray(raw[:128])
+    struct.pack_into("<I", head, 8, 1)
+    struct.pack_into("<QQ", head, 72, len(payload_v1), fnv1a64(payload_v1))
+    v1 = tmp_path / "v1.ckpt"
+    v1.write_bytes(bytes(head) + payload_v1)
+    with Lattice(two, "fp32") as c:
+        c.load(v1).step(15)
+        got = c.get_populations()
+    with Lattice(one, "fp32") as d:  # the step-20 state continued with one time
+        d.set_populations(f20).step(15)
+        ref = d.get_populations()
+    assert np.array_equal(got, ref)
+    assert not np.array_equal(got, fa)
