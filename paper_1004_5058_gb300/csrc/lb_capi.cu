@@ -147,6 +147,14 @@ static void fill(ParamSet<C>& d, const lb_cell_params& c)
     d.rho_bar[1] = C(c.rho_bar_b);
 }
 
+// true if no cell gives species B a relaxation time of its own
+static bool one_relaxation_time(const std::vector<lb_cell_params>& cells)
+{
+    for (const lb_cell_params& c : cells)
+        if (c.tau_b != 0.0 && c.tau_b != c.tau) return false;
+    return true;
+}
+
 static CellDev to_dev(const lb_cell_params& c)
 {
     CellDev d{};
@@ -244,6 +252,7 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
     const char* msg = nullptr;
     TiledPlan* p = tiled_create(h->g, (int)h->prec, h->elem, h->bc, h->f[0], h->f[1], tx, ty, &msg);
     if (!p) return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: %s", msg ? msg : "tiled plan failed");
+    tiled_set_one_time(p, one_relaxation_time(h->cells));
     if (h->plan) tiled_destroy(h->plan);
     h->plan = p;
     h->kernel = LB_KERNEL_TILED;
@@ -1073,6 +1082,8 @@ lb_status lb_load(lb_handle* h, const char* path)
     CK(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
     h->h_err[0] = 0;
     h->cells = cells;
+    if (h->plan) tiled_set_one_time(h->plan, one_relaxation_time(h->cells));
+    free_graphs(h);  // captured launches may name the other kernel family
     h->cur = 0;
     h->t = hd.t;
     h->start = hd.start;

@@ -28,6 +28,9 @@ void tiled_tiles(const TiledPlan* p, int* tx, int* ty);
 // Failure injection (tests): the next launch's CTA 0 leaves the copy of its row
 // `row` (counted over its work items) unissued, so the waits for it time out.
 void tiled_inject_skip(TiledPlan* p, uint32_t row);
+// Whether every cell has one relaxation time (the full-width kernels serve only
+// that case; cells with a time per species take the general kernels).
+void tiled_set_one_time(TiledPlan* p, bool one_time);
 
 // auxiliary kernels (lb_aux.cu)
 template <class T>

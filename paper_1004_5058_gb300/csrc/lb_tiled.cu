@@ -58,11 +58,13 @@ __host__ __device__ inline SlotGeom slot_geom(int tx, int elem)
 struct TiledPlan {
     Geom g;
     int elem, bc, tx, ty, depth;
-    int n_strips, n_seg, grid;
+    int n_strips, n_seg;
+    int grid[2];  // persistent CTAs of the full-width [0] and general [1] kernels
     size_t smem;
     CUtensorMap tm_main[2], tm_halo[2];
     void* f[2];
     uint32_t skip_row = ~0u;  // failure injection for the next launch (tests)
+    bool one_time = true;     // every cell has one relaxation time (the FULL kernels serve it)
 };
 
 // Row-slot ring depth: about three rows in flight beyond the three in use.
@@ -195,8 +197,9 @@ __device__ __noinline__ void profile_row_sums(const C* ub, int lane, double* __r
     if (t == 0 && (x0 >> 5) + grp < nbx) prof_part[((long long)cell * nbx + (x0 >> 5) + grp) * g.ny + y] = part;
 }
 
-// FULL: every strip is TX columns wide (nx a multiple of TX); otherwise the
-// last strip is narrower and its extra columns are masked.
+// FULL: every strip is TX columns wide (nx a multiple of TX) and every cell has
+// one relaxation time; otherwise the last strip may be narrower (its extra
+// columns masked) and the species may relax with times of their own.
 template <class T, int TX, bool SAMPLE, bool FULL>
 __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
                                                             const __grid_constant__ CUtensorMap tm_halo,
@@ -317,9 +320,9 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
         // this lane's species relaxes with tau_s; mix weighs the partner species'
         // moments in the common velocity (1, and one_time, for one relaxation time)
-        const C tau_s = sp ? pg.tau_b : pg.tau, omega_s = sp ? pg.omega_b : pg.omega;
-        const C mix = sp ? pg.mix[1] : pg.mix[0];
-        const bool one_time = pg.mix[0] == C(1);
+        const C tau_s = FULL || !sp ? pg.tau : pg.tau_b, omega_s = FULL || !sp ? pg.omega : pg.omega_b;
+        const C mix = FULL ? C(1) : (sp ? pg.mix[1] : pg.mix[0]);
+        const bool one_time = FULL || pg.mix[0] == C(1);
         const bool unit_omega = omega_s == C(1);  // tau_s = 1: f* = f^eq (uniform over each half-warp)
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
         // columns of this strip inside the lattice (the last strip of a width that
@@ -443,8 +446,17 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 const C jx_s = mom_x<C>(f[o]), jy_s = mom_y<C>(f[o]);
                 const C jx_p = __shfl_xor_sync(0xffffffffu, jx_s, 16), jy_p = __shfl_xor_sync(0xffffffffu, jy_s, 16);
                 // common velocity: (j_own + mix j_partner) / (rho_own + mix rho_partner)
-                const C jwx = (jx_s + mix * jx_p) * inv_scale, jwy = (jy_s + mix * jy_p) * inv_scale;
-                const C inv_rho = fast_div<C>(C(1), rho_s[o] + mix * e[1][o + 2]);
+                C jwx, jwy, rho_w;
+                if constexpr (FULL) {  // one relaxation time: the barycentric velocity
+                    jwx = (jx_s + jx_p) * inv_scale;
+                    jwy = (jy_s + jy_p) * inv_scale;
+                    rho_w = rho_s[o] + e[1][o + 2];
+                } else {
+                    jwx = (jx_s + mix * jx_p) * inv_scale;
+                    jwy = (jy_s + mix * jy_p) * inv_scale;
+                    rho_w = rho_s[o] + mix * e[1][o + 2];
+                }
+                const C inv_rho = fast_div<C>(C(1), rho_w);
                 const C ux = jwx * inv_rho, uy = jwy * inv_rho;
                 C ax = fx_body * inv_rho;
                 if (body_raw) ax = fx_body * fast_div<C>(C(1), rho_s[o] + e[1][o + 2]);
@@ -699,9 +711,16 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int occ = 1;
-    for (int s = 0; s < 2; ++s) {
-        const void* k = pick_any(prec, tile_x, s == 1, g.nx % tile_x == 0);
+    // occupancy of each family (sampled and plain kernels together): the
+    // full-width kernels (nx a multiple of the tile, one relaxation time) and
+    // the general ones; which family runs depends on the cells' relaxation
+    // times, which lb_load may change, so both are prepared
+    const bool full_ok = g.nx % tile_x == 0;
+    int occ[2] = {0, 0};  // [0] full-width, [1] general
+    for (int s = 0; s < 4; ++s) {
+        const int fam = (s & 2) ? 1 : 0;
+        if (fam == 0 && !full_ok) continue;
+        const void* k = pick_any(prec, tile_x, (s & 1) != 0, fam == 0);
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess) {
             cudaGetLastError();
             if (err_msg) *err_msg = "cudaFuncSetAttribute(max dynamic smem) failed";
@@ -716,19 +735,22 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
             delete p;
             return nullptr;
         }
-        occ = s == 0 ? o : std::min(occ, o);
+        occ[fam] = occ[fam] == 0 ? o : std::min(occ[fam], o);
     }
-    const long long slots = (long long)sms * occ;
+    const long long slots = (long long)sms * occ[full_ok ? 0 : 1];
     if (p->ty <= 0) p->ty = pick_segment_rows(g, tile_x, slots);
     p->n_seg = (g.ny + p->ty - 1) / p->ty;
     const long long items = (long long)p->n_strips * p->n_seg * g.n_cells;
-    p->grid = (int)std::min(items, slots);
+    p->grid[0] = full_ok ? (int)std::min(items, slots) : 0;
+    p->grid[1] = (int)std::min(items, (long long)sms * occ[1]);
     return p;
 }
 
 void tiled_destroy(TiledPlan* p) { delete p; }
 
 void tiled_inject_skip(TiledPlan* p, uint32_t row) { p->skip_row = row; }
+
+void tiled_set_one_time(TiledPlan* p, bool one_time) { p->one_time = one_time; }
 
 void tiled_tiles(const TiledPlan* p, int* tx, int* ty)
 {
@@ -741,7 +763,8 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
                               double* wall_part, unsigned* err, cudaStream_t st, int* n_launches)
 {
     T* dst = reinterpret_cast<T*>(p->f[1 - src]);
-    const void* k = pick<T>(p->tx, sample, p->g.nx % p->tx == 0);
+    const bool full = p->g.nx % p->tx == 0 && p->one_time;
+    const void* k = pick<T>(p->tx, sample, full);
     Geom g = p->g;
     int bc = p->bc, ty = p->ty, ns = p->n_strips, nseg = p->n_seg;
     uint32_t skip = p->skip_row;
@@ -749,7 +772,7 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
     void* args[] = {(void*)&p->tm_main[src], (void*)&p->tm_halo[src], (void*)&dst, (void*)&g, (void*)&bc,
                     (void*)&ty, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
                     (void*)&wall_part, (void*)&err, (void*)&skip};
-    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid), dim3(tiled_threads(p->tx)), args, p->smem, st);
+    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid[full ? 0 : 1]), dim3(tiled_threads(p->tx)), args, p->smem, st);
     *n_launches += 1;
     return e;
 }

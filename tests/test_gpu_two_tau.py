@@ -191,3 +191,26 @@ def test_checkpoint_carries_tau_b_and_reads_version_1(tmp_path):
         ref = d.get_populations()
     assert np.array_equal(got, ref)
     assert not np.array_equal(got, fa)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_two_times_narrow_last_strip(prec, tol):
+    """Two relaxation times with tiles that do not divide nx (80 = 64 + 16):
+    the general tiled kernel, against the oracle after 20 steps."""
+    nx, ny = 80, 40
+    cell = I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=0.01, tau=0.9, tau_b=1.2)
+    ra, rb = I.random_fields(nx, ny, seed=29)
+    ux, uy = I.couette_velocity(nx, ny, 0.01)
+    from paper_1004_5058_gb300 import Lattice
+    with Lattice([cell], prec) as lat:
+        lat.set_kernel("tiled", 64, 0)
+        assert lat.kernel()[:2] == ("tiled", 64)
+        lat.init_fields(ra, rb, ux, uy).set_sampling(5, 5).step(20)
+        ga, gb, gu, _ = lat.fields()
+        ub, ns = lat.profile()
+    (r,) = oracle_runs([cell], ra, rb, ux, uy, steps=20, sampling=(5, 5))
+    oa, ob, ou, _ = r.fields()
+    assert max_abs(ga[0], oa) <= tol and max_abs(gb[0], ob) <= tol and max_abs(gu[0], ou) <= tol
+    _, _, _, oub = r.shear()
+    assert ns == 3
+    np.testing.assert_allclose(ub[0], oub, rtol=0, atol=tol)
