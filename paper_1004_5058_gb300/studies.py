@@ -289,6 +289,38 @@ def surrogate_study(n_train: int = 600, n_test: int = 64, n_speeds: int = 16, L:
             "gain_queries_per_s": (4096 / t_serve) / (len(x) / t_data)}
 
 
+def two_time_flow_curve(L: int = 256, steps: int = 500000, every: int = 50, n_speeds: int = 16,
+                        u_lo: float = 1e-5, u_hi: float = 1e-2, tau_bs=(0.7, 1.0, 1.5), g_ab: float = 0.405,
+                        precision: str = "fp32", seed: int = 1004):
+    """The Couette flow curve with a relaxation time per species (the
+    coupling-dependent relaxation time the paper leaves unexplored): species A
+    keeps tau = 1, species B takes each tau_b in turn; cells = tau_b values x
+    wall speeds in one batch, the second half of the steps sampled, a
+    Herschel-Bulkley fit per tau_b.  The default 256^2 cells run 5e5 steps,
+    longer than the viscous time L^2/nu of every mixture here."""
+    speeds = I.log_spaced(u_lo, u_hi, n_speeds)
+    cells = [I.make_cell("paper", nx=L, ny=L, g_ab=g_ab, bc=1, u_wall=u, tau=1.0, tau_b=tb)
+             for tb in tau_bs for u in speeds]
+    ra, rb = I.random_fields(L, L, n_cells=len(cells), seed=seed)
+    ux, uy = I.couette_velocity(L, L, [c.u_wall for c in cells], n_cells=len(cells))
+    with Lattice(cells, precision) as lat:
+        lat.init_fields(ra, rb, ux, uy)
+        kern = lat.autotune()
+        lat.init_fields(ra, rb, ux, uy).set_sampling(steps // 2, every)
+        _, dt = _cuda_time(lambda: lat.step(steps).sync())
+        sigma, S, Sb = lat.shear_stress()
+    out = {"L": L, "steps": steps, "cells": len(cells), "precision": precision, "g_ab": g_ab, "kernel": kern,
+           "seconds": dt, "mlups": len(cells) * L * L * steps / dt / 1e6, "curves": {}}
+    for k, tb in enumerate(tau_bs):
+        sl = slice(k * n_speeds, (k + 1) * n_speeds)
+        s_, r_ = sigma[sl], S[sl]
+        ok = np.isfinite(r_) & (r_ > 0) & np.isfinite(s_) & (s_ > 0)
+        out["curves"][str(tb)] = {"u_wall": list(speeds), "sigma_xy": [float(v) for v in s_],
+                                  "shear_rate": [float(v) for v in r_], "shear_bulk": [float(v) for v in Sb[sl]],
+                                  "hb_fit": hb_fit(r_[ok], s_[ok]) if ok.sum() >= 3 else None}
+    return out
+
+
 def couette_flow_curve(n: int = 1024, n_speeds: int = 8, steps: int = 200000, every: int = 10, g_ab: float = 0.405,
                        precision: str = "fp32", seed: int = 1004):
     """The benchmark's configuration run to its end: n_speeds Couette cells of
@@ -319,7 +351,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
                                       "flow_curve_long", "couette_1024", "surrogate", "kolmogorov",
-                                      "kolmogorov_rho0"])
+                                      "kolmogorov_rho0", "two_time"])
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
@@ -335,6 +367,8 @@ def main():
         r = couette_flow_curve(n=128, steps=4000) if a.quick else couette_flow_curve()
     elif a.study == "flow_curve_long":  # the batched 64 x 512^2 cells for 1e6 steps (steady state)
         r = flow_curve(L=128, steps=4000, n_speeds=4) if a.quick else flow_curve(steps=1000000, every=100)
+    elif a.study == "two_time":  # relaxation time per species: flow curves for three tau_B
+        r = two_time_flow_curve(L=64, steps=4000, n_speeds=4) if a.quick else two_time_flow_curve()
     elif a.study == "surrogate":
         r = surrogate_study(n_train=48, n_test=12, n_speeds=8, L=32, steps=3000) if a.quick else surrogate_study()
     else:

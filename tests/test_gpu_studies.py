@@ -52,3 +52,14 @@ def test_surrogate_study_small():
     r = studies.surrogate_study(n_train=24, n_test=8, n_speeds=8, L=32, steps=2000, epochs=30, batch=64)
     assert r["train_points"] > 0 and 0.0 <= r["served_fraction"] <= 1.0
     assert r["network_queries_per_s"] > 0 and len(r["error_table_by_logS_bin"]) == 8
+
+
+def test_two_time_flow_curve_small():
+    """One batch over three tau_B values, one curve and fit slot per value; the
+    relaxation time of B changes the stresses."""
+    from paper_1004_5058_gb300 import studies
+    r = studies.two_time_flow_curve(L=64, steps=2000, every=10, n_speeds=4, tau_bs=(0.7, 1.0, 1.5))
+    assert set(r["curves"]) == {"0.7", "1.0", "1.5"} and r["mlups"] > 0
+    for c in r["curves"].values():
+        assert all(finite(v) for v in c["sigma_xy"]) and c["sigma_xy"][-1] > 0
+    assert r["curves"]["0.7"]["sigma_xy"][-1] != r["curves"]["1.5"]["sigma_xy"][-1]
