@@ -70,7 +70,8 @@ typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_GENERIC = 1, LB_KERNEL_TILED = 2 } 
 
 /* One lattice cell, in the paper's symbols.  All cells of a handle share nx, ny
  * and bc; the other fields may differ per cell (batched flow curves).
- *   tau      BGK relaxation time (Eq. (be)); must be > 1/2
+ *   tau      BGK relaxation time (Eq. (be)) of both species, or of species A
+ *            when tau_b is set; must be > 1/2
  *   rho0     reference density of psi(rho) = rho0 (1 - exp(-rho/rho0)) and of F^X
  *   g_aa1, g_bb1  G^a_AA, G^a_BB: belt-1 self couplings (negative attracts)
  *   g_aa2, g_bb2  G^r_AA, G^r_BB: two-belt self couplings (positive repels)
@@ -154,7 +155,8 @@ lb_status lb_shear_stress(lb_handle* h, double* sigma_xy, double* shear_rate,
 lb_status lb_get_profile(lb_handle* h, double* ubar, long long* n_samples);
 
 /* Current fields (host [n_cells][ny][nx], any pointer may be NULL):
- * rho_s = sum_i f_is and the paper's barycentric u = sum_s sum_i f_is c_i / rho.
+ * rho_s = sum_i f_is and the paper's barycentric u = sum_s sum_i f_is c_i / rho
+ * (also for cells whose species relax with times of their own).
  * Synchronous; reports LB_ERR_NONFINITE if any density is not finite or <= 0. */
 lb_status lb_get_fields(lb_handle* h, double* rho_a, double* rho_b, double* ux, double* uy);
 
