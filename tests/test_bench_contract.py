@@ -32,6 +32,13 @@ def test_reference_arm_line():
     assert d["config"]["workload"].startswith("couette batch: 2 cells of 64x64")
 
 
+def test_reference_arm_two_relaxation_times():
+    """--tau-b reaches the oracle's cells and the reported configuration."""
+    d = run_bench("--impl", "reference", "--steps", "1", "--warmup", "1", "--nx", "32", "--ny", "32",
+                  "--cells", "2", "--cpu-seconds", "0.3", "--tau-b", "0.7")
+    assert d["value"] > 0 and d["config"]["tau"].startswith("A 1, B 0.7")
+
+
 @pytest.mark.gpu
 def test_gpu_arm_line():
     d = run_bench("--steps", "3", "--warmup", "3", "--nx", "256", "--ny", "256", "--cells", "2", "--chunk", "20",
