@@ -114,14 +114,16 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(precision, nx, ny, n_cells):
+def committed_traffic(precision, nx, ny, n_cells, two_time=False):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    scaled to this workload's sites, if it was taken on the current sources."""
+    scaled to this workload's sites, if it was taken on the current sources.
+    Cells with a relaxation time per species run the general kernel, which has
+    its own entry ("<precision>_two_time"); without one the traffic is unknown."""
     p = os.path.join(ROOT, "profiles", "fused_step_dram.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(precision)
+    e = d.get(precision + ("_two_time" if two_time else ""))
     if not e or d.get("source_digest") != source_digest():
         return None
     per_site = float(e["dram_bytes_per_launch"]) / float(e["sites_per_launch"])
@@ -366,7 +368,8 @@ def run_ours(args):
     alg_bytes = BYTES_PER_SITE[args.precision] * sites
     peak, peak_kind = peaks()
     achieved = alg_bytes / (t_launch if kernels_per_step == 1 else t_launch * kernels_per_step) / 1e9
-    traffic = committed_traffic(args.precision, nx, ny, n_cells) if kernel == "tiled" else None
+    traffic = (committed_traffic(args.precision, nx, ny, n_cells, two_time=args.tau_b not in (0.0, 1.0))
+               if kernel == "tiled" else None)
 
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,

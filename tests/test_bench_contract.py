@@ -75,3 +75,7 @@ def test_traffic_record_matches_the_kernel_sources():
         alg = {"fp32": 144, "fp16": 72, "fp16sr": 72}[prec]
         assert 0.9 * alg < per_site < 1.1 * alg  # no wasted re-reads
     assert bench.committed_traffic("fp32", 1024, 1024, 8) == rec["fp32"]["dram_bytes_per_launch"]
+    # a relaxation time per species runs the general kernel: its own entry, or none
+    two = bench.committed_traffic("fp32", 1024, 1024, 8, two_time=True)
+    assert two == (rec["fp32_two_time"]["dram_bytes_per_launch"] if "fp32_two_time" in rec else None)
+    assert bench.committed_traffic("fp64", 1024, 1024, 8, two_time=True) is None
