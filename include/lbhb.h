@@ -10,6 +10,8 @@
  *   Eq. (FFF) F_s = F^a_s + F^r_s + F^X_s: attractive belt-1 self force, repulsive
  *             two-belt (24 neighbours) self force, belt-1 cross-species repulsion,
  *             on the pseudopotential psi(rho) = rho0 (1 - exp(-rho/rho0)).
+ * One relaxation time tau for both species, as in all the paper's runs, unless
+ * a cell sets tau_b (a time per species; see lb_cell_params).
  * Boundaries: periodic in x; in y periodic or Couette (halfway bounce-back walls
  * at y = -1/2 and y = ny - 1/2 moving at -u_wall and +u_wall in x; the paper
  * itself uses a fully periodic box, walls are an extension for shear-rate control).
