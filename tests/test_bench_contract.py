@@ -39,6 +39,25 @@ def test_reference_arm_two_relaxation_times():
     assert d["value"] > 0 and d["config"]["tau"].startswith("A 1, B 0.7")
 
 
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched like the multi-GPU bench (two ranks), the reference arm runs on
+    rank 0 only: one JSON line, every rank exits 0."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--nx", "32", "--ny", "32",
+           "--cells", "2", "--cpu-seconds", "0.3"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0
+
+
 @pytest.mark.gpu
 def test_gpu_arm_line():
     d = run_bench("--steps", "3", "--warmup", "3", "--nx", "256", "--ny", "256", "--cells", "2", "--chunk", "20",
