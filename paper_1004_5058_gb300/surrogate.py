@@ -16,7 +16,9 @@ Dataset recipe (one point per Couette cell):
   rho_s = 0.6 (1 +- 0.1 xi) and the linear Couette start; the time averages
   cover the second half of the run.  The label is 1 (yielded) when the bulk
   shear rate (least-squares slope of the central half of the profile) exceeds
-  a tenth of the nominal rate 2U/ny.
+  a tenth of the nominal rate 2U/ny.  All cells have one relaxation time tau
+  for both species (the paper's model): the network does not cover cells with
+  a relaxation time per species.
 """
 from __future__ import annotations
 
