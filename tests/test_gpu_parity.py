@@ -276,8 +276,10 @@ def test_one_step_kolmogorov_forcing(kernel, prec, tol):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_kolmogorov_flow_paper_start(kernel, prec, tol):
     """The paper's workload in small: fully periodic box, body force
-    F0 sin(2 pi y / L), the sinusoidal initial densities of the paper."""
-    L = 64
+    F0 sin(2 pi y / L), the sinusoidal initial densities of the paper
+    (k_in = 64 pi / L: L = 128 gives k_in = pi/2; at L = 64 the sine would vanish
+    on every lattice row)."""
+    L = 128
     cell = I.make_cell("paper", nx=L, ny=L, f0=I.kolmogorov_f0(0.02, L))
     ra, rb = I.sine_fields(L, L)
     with lattice([cell], prec, kernel) as lat:
