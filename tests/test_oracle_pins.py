@@ -506,6 +506,34 @@ def test_kolmogorov_tau1_exact_discrete_steady_state():
     assert abs(r.last["mom"][0]) < 1e-15 * ny * 4
 
 
+def test_kolmogorov_tau1_force_corrected_profile():
+    """The sampled line profile U_x(y) of section "Numerical Results" is taken
+    from the force-corrected velocity u = (j + (F_A + F_B)/2) / rho.  In the
+    exact discrete steady state of the test above (G = 0, tau = 1) the raw j/rho
+    has amplitude A = 3 lam Phi / (1 - cos k) and the body force adds F/(2 rho) =
+    (Phi/2) sin(k y) at every site, so the time-averaged profile is the pure sine
+    of amplitude A + Phi/2.  At ny = 32 the half-force term is 0.3 % of A: a
+    dropped, doubled or sign-flipped 1/2 misses by more than 1000 times the
+    tolerance."""
+    ny, nx, F0 = 32, 4, 1e-6
+    k = 2 * math.pi / ny
+    c = I.make_cell("ideal", nx=nx, ny=ny, tau=1.0, f0=F0)
+    r = lb.Run(c, np.full((ny, nx), 0.6), np.full((ny, nx), 0.6))
+    r.set_sampling(3000, 7)  # steady after ~20 decay times ny^2 / (nu k_1^2 ny^2) ~ 155 steps
+    r.step(4000)
+    _, _, _, ub = r.shear()
+    y = np.arange(ny)
+    lam = (2 + math.cos(k)) / 3
+    phi = F0 / 1.2
+    A = 3 * lam * phi / (1 - math.cos(k))
+    amp = 2.0 / ny * np.sum(ub * np.sin(k * y))
+    assert amp == pytest.approx(A + 0.5 * phi, rel=1e-6)
+    np.testing.assert_allclose(ub, amp * np.sin(k * y), rtol=0, atol=1e-6 * abs(amp))
+    # the raw barycentric profile of the same state has amplitude A (no force term)
+    _, _, u, _ = r.fields()
+    assert 2.0 / ny * np.sum(u.mean(axis=1) * np.sin(k * y)) == pytest.approx(A, rel=1e-6)
+
+
 @pytest.mark.parametrize("tau", [0.8, 1.4])
 def test_kolmogorov_laminar_amplitude(tau):
     """Peak speed of the laminar Kolmogorov flow u0 = F0 / (rho nu k^2), up to O(k^2)."""
