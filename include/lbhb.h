@@ -242,22 +242,29 @@ long long lb_kernel_launches(const lb_handle* h);
  *                LB_FP16_SHIFTED_SR are rejected (LB_ERR_UNSUPPORTED)
  *   sums         caller's device buffer [n_cells][4] float64, receives
  *                (sum rho_A, sum rho_B, sum j_x, sum j_y) per cell; a
- *                non-finite density makes its cell's sums non-finite
+ *                non-finite density makes its cell's sums non-finite.  Unlike
+ *                lb_reductions, this variant does not report a non-positive
+ *                density (it returns before the work is done): check the sums
  *   cuda_stream  stream of the current device (NULL: the legacy default stream)
+ * Before anything is enqueued both buffers are checked: each must be device
+ * (or managed) memory of the current device whose allocation holds the bytes
+ * the layout needs from the given pointer on (n_cells*18*ny*pitch elements;
+ * n_cells*4 doubles), else LB_ERR_INVALID; host memory, another device's
+ * memory and too small buffers are refused this way.
  * Work is enqueued and the call returns; read sums after the stream is done.
  * The partial sums live in one scratch array compiled into the library
  * (65536 doubles + an error word, 512 KiB on every GPU that loads the library,
- * held until exit): inputs needing more partial sums than that (4 per block of
- * up to 8192 sites, per cell) are rejected with LB_ERR_INVALID and a message,
- * e.g. more than 16 cells of 4096x4096.  The array is shared by all calls on a
- * device and keeps the last call's contents; calls that overlap on the GPU
- * (different streams or host threads) race on it and must be serialised by the
- * caller.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Allocates nothing (no cudaMalloc, cudaFree or
- * allocating library routine).  Errors: LB_ERR_INVALID (null or misaligned
- * pointer, bad size), LB_ERR_UNSUPPORTED, LB_ERR_CUDA; message in
- * lb_last_error(NULL). */
+ * held until exit).  A cell needs 4 * min(1024, ceil(nx*ny / 8192)) partial
+ * sums, and all cells together at most 65536, else LB_ERR_INVALID with a
+ * message: e.g. 16 cells of 4096x4096 fit, 17 do not.  The array is shared by
+ * all calls on a device and keeps the last call's contents; calls that overlap
+ * on the GPU (different streams or host threads) race on it and must be
+ * serialised by the caller.  Every call looks up the array's device address on
+ * the current device (cudaGetSymbolAddress); the first call on a device may
+ * load the library's device code, so make it before any stream capture.
+ * Allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * Errors: LB_ERR_INVALID (null, misaligned, host or too small buffer, bad
+ * size), LB_ERR_UNSUPPORTED, LB_ERR_CUDA; message in lb_last_error(NULL). */
 lb_status lb_reductions_noalloc(const void* populations, lb_precision prec, int nx, int ny, int pitch,
                                 int n_cells, double* sums, void* cuda_stream);
 

@@ -9,9 +9,10 @@
 // output as the caller's own device buffers and runs the same two reduction
 // kernels with their scratch (the per-block partial sums and the error word)
 // in a fixed-size array compiled into the library.
+#include <cudaTypedefs.h>
+
 #include <cstdint>
 #include <cstdio>
-#include <mutex>
 
 #include "lbhb.h"
 #include "lb_internal.h"
@@ -28,23 +29,16 @@ constexpr long long kScratchDoubles = kScratchPartials + 32;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array for the current device.  Host code may
-// not use the array's name as a device pointer, so the address is looked up
-// once per device with cudaGetSymbolAddress, with that device current.
-cudaError_t scratch_address(int dev, double** out)
+// Device address of the scratch array on the current device.  Host code may
+// not use the array's name as a device pointer; the address is looked up on
+// every call (a host-side table lookup once the module is loaded), so nothing
+// cached can outlive a device reset.
+cudaError_t scratch_address(double** out)
 {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 
@@ -54,6 +48,57 @@ lb_status fail(lb_status st, const char* msg)
     snprintf(buf, sizeof buf, "lb_reductions_noalloc: %s", msg);
     set_handleless_error(buf);
     return st;
+}
+
+PFN_cuMemGetAddressRange_v3020 address_range_fn()
+{
+    static PFN_cuMemGetAddressRange_v3020 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 3020, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuMemGetAddressRange_v3020)p;
+    }
+    return fn;
+}
+
+// A caller's buffer must be device (or managed) memory of the current device
+// whose allocation holds `bytes` bytes from `ptr` on; otherwise the kernels
+// would read or write outside it.  Nothing is launched before this holds.
+lb_status check_buffer(const void* ptr, size_t bytes, int dev, const char* name)
+{
+    char buf[256];
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(buf, sizeof buf, "%s: not a pointer the CUDA runtime knows", name);
+        return fail(LB_ERR_INVALID, buf);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        snprintf(buf, sizeof buf, "%s: host memory; a device buffer of the current device is required", name);
+        return fail(LB_ERR_INVALID, buf);
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) {
+        snprintf(buf, sizeof buf, "%s: memory of device %d, the current device is %d", name, a.device, dev);
+        return fail(LB_ERR_INVALID, buf);
+    }
+    auto range = address_range_fn();
+    if (!range) return fail(LB_ERR_CUDA, "cuMemGetAddressRange is not available");
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (range(&base, &size, (CUdeviceptr)(uintptr_t)ptr) != CUDA_SUCCESS) {
+        snprintf(buf, sizeof buf, "%s: the extent of its allocation cannot be established", name);
+        return fail(LB_ERR_INVALID, buf);
+    }
+    const uintptr_t p = (uintptr_t)ptr, end = (uintptr_t)base + size;
+    if (p < (uintptr_t)base || p > end || bytes > end - p) {
+        snprintf(buf, sizeof buf, "%s: %zu bytes needed from the pointer, its allocation holds %zu", name, bytes,
+                 (size_t)(p <= end ? end - p : 0));
+        return fail(LB_ERR_INVALID, buf);
+    }
+    return LB_OK;
 }
 
 }  // namespace
@@ -83,22 +128,28 @@ extern "C" lb_status lb_reductions_noalloc(const void* populations, lb_precision
                  n_cells, nx, ny, need, kScratchPartials);
         return fail(LB_ERR_INVALID, buf);
     }
+    // n_cells <= 16384 here, and g.plane < 2^62: the byte count needs no more than 2^61
+    if (g.plane > (1LL << 61) / (18LL * elem * n_cells)) return fail(LB_ERR_INVALID, "buffer size overflows");
+    const size_t pop_bytes = (size_t)n_cells * (size_t)g.cellstride * (size_t)elem;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(LB_ERR_CUDA, "no usable current device");
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, "no usable current device");
+    lb_status vs = check_buffer(populations, pop_bytes, dev, "populations");
+    if (vs != LB_OK) return vs;
+    vs = check_buffer(sums, (size_t)n_cells * 4 * sizeof(double), dev, "sums");
+    if (vs != LB_OK) return vs;
     double* scratch = nullptr;
-    e = scratch_address(dev, &scratch);
+    e = scratch_address(&scratch);
     if (e != cudaSuccess) return fail(LB_ERR_CUDA, cudaGetErrorString(e));
+    // the reduction kernels OR their non-finite/non-positive flag into this
+    // word; this variant does not read it back (the sums of a cell with a
+    // non-finite density are non-finite; a non-positive density is not flagged)
     unsigned* err = reinterpret_cast<unsigned*>(scratch + kScratchPartials);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    // the error word is the only scratch read before it is written
-    e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);
-    if (e == cudaSuccess) {
-        if (prec == LB_FP32)
-            e = launch_state_sums<float>(static_cast<const float*>(populations), g, nullptr, scratch, sums, err, st);
-        else
-            e = launch_state_sums<double>(static_cast<const double*>(populations), g, nullptr, scratch, sums, err, st);
-    }
+    if (prec == LB_FP32)
+        e = launch_state_sums<float>(static_cast<const float*>(populations), g, nullptr, scratch, sums, err, st);
+    else
+        e = launch_state_sums<double>(static_cast<const double*>(populations), g, nullptr, scratch, sums, err, st);
     if (e != cudaSuccess) return fail(LB_ERR_CUDA, cudaGetErrorString(e));
     return LB_OK;
 }

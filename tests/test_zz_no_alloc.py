@@ -83,3 +83,56 @@ def test_noalloc_rejects_what_it_cannot_do(env):
     assert lib.lb_reductions_noalloc(p, L.LB_FP16_SHIFTED_SR, 8, 8, 8, 1, o, None) == L.LB_ERR_UNSUPPORTED
     assert lib.lb_reductions_noalloc(None, L.LB_FP32, 8, 8, 8, 1, o, None) == L.LB_ERR_INVALID
     assert lib.lb_reductions_noalloc(p, L.LB_FP32, 8, 8, 4, 1, o, None) == L.LB_ERR_INVALID  # pitch < nx
+    # host memory, for either buffer: refused before anything is enqueued
+    host = np.zeros(18 * 64, dtype=np.float64)
+    hp = C.c_void_p(host.ctypes.data)
+    assert lib.lb_reductions_noalloc(hp, L.LB_FP32, 8, 8, 8, 1, o, None) == L.LB_ERR_INVALID
+    assert b"host memory" in lib.lb_last_error(None)
+    assert lib.lb_reductions_noalloc(p, L.LB_FP32, 8, 8, 8, 1, hp, None) == L.LB_ERR_INVALID
+    assert b"host memory" in lib.lb_last_error(None)
+
+
+def _cudart():
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            return C.CDLL(name)
+        except OSError:
+            pass
+    pytest.skip("CUDA runtime library not found for a plain cudaMalloc")
+
+
+def test_noalloc_checks_the_allocation_extent(env):
+    """Buffers from a plain cudaMalloc of a known size: a request that needs more
+    bytes than the allocation holds from the given pointer is refused before any
+    launch; one that fits runs."""
+    torch, L, lib = env
+    rt = _cudart()
+    rt.cudaMalloc.argtypes = [C.POINTER(C.c_void_p), C.c_size_t]
+    rt.cudaFree.argtypes = [C.c_void_p]
+    torch.cuda.synchronize()
+    pops, sums = C.c_void_p(), C.c_void_p()
+    nx = ny = 8
+    need = 18 * ny * nx * 4  # one FP32 cell
+    assert rt.cudaMalloc(C.byref(pops), need) == 0
+    assert rt.cudaMalloc(C.byref(sums), 4 * 8) == 0
+    try:
+        host = np.ones((18, ny, nx), dtype=np.float32)
+        rt.cudaMemcpy.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+        assert rt.cudaMemcpy(pops, C.c_void_p(host.ctypes.data), need, 1) == 0  # host to device
+        # a 1024 x 1024 cell needs 75 MB; the allocation holds 4.6 kB
+        assert lib.lb_reductions_noalloc(pops, L.LB_FP32, 1024, 1024, 1024, 1, sums, None) == L.LB_ERR_INVALID
+        assert b"allocation holds" in lib.lb_last_error(None)
+        # the same buffer read from 4 bytes past its start no longer holds one cell
+        late = C.c_void_p(pops.value + 4)
+        assert lib.lb_reductions_noalloc(late, L.LB_FP32, nx, ny, nx, 1, sums, None) == L.LB_ERR_INVALID
+        # two cells' sums do not fit a buffer of one cell's
+        assert lib.lb_reductions_noalloc(pops, L.LB_FP32, nx, ny // 2, nx, 2, sums, None) == L.LB_ERR_INVALID
+        # exactly one cell fits: every population is 1, so rho_s = 9 per site and j = 0
+        assert lib.lb_reductions_noalloc(pops, L.LB_FP32, nx, ny, nx, 1, sums, None) == L.LB_OK
+        assert rt.cudaDeviceSynchronize() == 0
+        out = np.zeros(4)
+        assert rt.cudaMemcpy(C.c_void_p(out.ctypes.data), sums, 32, 2) == 0  # device to host
+        np.testing.assert_array_equal(out, [9.0 * nx * ny, 9.0 * nx * ny, 0.0, 0.0])
+    finally:
+        rt.cudaFree(pops)
+        rt.cudaFree(sums)
