@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace lbhb {
 
@@ -180,12 +181,6 @@ __device__ inline double to_c(double v) { return v; }
 __device__ inline float to_c(__half v) { return __half2float(v); }
 __device__ inline float to_c(half_sr v) { return __half2float(v.h); }
 
-// Quotient for the collision: FP32 uses the fast division intrinsic (2 ulp),
-// FP64 the correctly rounded one.
-template <class C> __device__ inline C fast_div(C a, C b);
-template <> __device__ inline float fast_div<float>(float a, float b) { return __fdividef(a, b); }
-template <> __device__ inline double fast_div<double>(double a, double b) { return a / b; }
-
 // sin(pi x): the Kolmogorov profile sin(2 pi y / ny) is sin_pi(y * 2/ny).
 template <class C> __device__ inline C sin_pi(C x);
 template <> __device__ inline float sin_pi<float>(float x) { return sinpif(x); }
@@ -204,43 +199,171 @@ template <> __device__ inline double expm1_c<double>(double x) { return expm1(x)
 // psi(rho) = rho0 (1 - exp(-rho/rho0)) = -rho0 expm1(-rho/rho0)
 template <class C> __device__ inline C psi_of(C rho, C rho0, C inv_rho0) { return -rho0 * expm1_c<C>(-rho * inv_rho0); }
 
+// ------------------------------------------------------------ lane pairs --
+// The tiled kernel's threads update one species at two adjacent sites (x, x+1)
+// with identical arithmetic; P2<C> holds the pair.  For FP32 a pair is one
+// 64-bit operand of the packed FP32 instructions of sm_100 and later
+// (add/sub/mul/fma.rn.f32x2): one issued instruction yields both results, each
+// rounded as the scalar instruction would round it.  FP64 pairs are two scalar
+// operations.  The site arithmetic below is written once for a lane type V (a
+// scalar for the one-site-per-thread kernel, P2 for the tiled kernel), with the
+// multiply-adds explicit (vfma).
+template <class C> struct P2;
+
+template <> struct P2<float> {
+    float2 v;
+    P2() = default;
+    __device__ explicit P2(double s) : v(make_float2((float)s, (float)s)) {}
+    __device__ explicit P2(float s) : v(make_float2(s, s)) {}
+    __device__ P2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ explicit P2(float2 w) : v(w) {}
+    __device__ float a() const { return v.x; }
+    __device__ float b() const { return v.y; }
+};
+
+template <> struct P2<double> {
+    double x, y;
+    P2() = default;
+    __device__ explicit P2(double s) : x(s), y(s) {}
+    __device__ P2(double a, double b) : x(a), y(b) {}
+    __device__ double a() const { return x; }
+    __device__ double b() const { return y; }
+};
+
+namespace pk {
+__device__ __forceinline__ unsigned long long bits(float2 a)
+{
+    unsigned long long u;
+    memcpy(&u, &a, 8);
+    return u;
+}
+__device__ __forceinline__ float2 unbits(unsigned long long u)
+{
+    float2 a;
+    memcpy(&a, &u, 8);
+    return a;
+}
+}  // namespace pk
+
+__device__ __forceinline__ P2<float> operator+(P2<float> a, P2<float> b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk::bits(a.v)), "l"(pk::bits(b.v)));
+    return P2<float>(pk::unbits(d));
+}
+__device__ __forceinline__ P2<float> operator-(P2<float> a, P2<float> b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk::bits(a.v)), "l"(pk::bits(b.v)));
+    return P2<float>(pk::unbits(d));
+}
+__device__ __forceinline__ P2<float> operator*(P2<float> a, P2<float> b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk::bits(a.v)), "l"(pk::bits(b.v)));
+    return P2<float>(pk::unbits(d));
+}
+__device__ __forceinline__ P2<float> vfma(P2<float> a, P2<float> b, P2<float> c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk::bits(a.v)), "l"(pk::bits(b.v)), "l"(pk::bits(c.v)));
+    return P2<float>(pk::unbits(d));
+}
+__device__ __forceinline__ P2<double> operator+(P2<double> a, P2<double> b) { return P2<double>(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ P2<double> operator-(P2<double> a, P2<double> b) { return P2<double>(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ P2<double> operator*(P2<double> a, P2<double> b) { return P2<double>(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ P2<double> vfma(P2<double> a, P2<double> b, P2<double> c)
+{
+    return P2<double>(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Lane-wise helpers: reciprocal for the velocity (FP32 through the fast
+// division intrinsic, 2 ulp; FP64 correctly rounded), psi_s/rho_s with its limit
+// 1 at rho_s -> 0, and psi of the densities.
+__device__ __forceinline__ float lane_rcp(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double lane_rcp(double x) { return 1.0 / x; }
+template <class C> __device__ __forceinline__ P2<C> lane_rcp(P2<C> x) { return P2<C>(lane_rcp(x.a()), lane_rcp(x.b())); }
+
+__device__ __forceinline__ float lane_por(float psi, float rho) { return rho != 0.f ? __fdividef(psi, rho) : 1.f; }
+__device__ __forceinline__ double lane_por(double psi, double rho) { return rho != 0.0 ? psi / rho : 1.0; }
+template <class C> __device__ __forceinline__ P2<C> lane_por(P2<C> psi, P2<C> rho)
+{
+    return P2<C>(lane_por(psi.a(), rho.a()), lane_por(psi.b(), rho.b()));
+}
+
+// psi = -rho0 expm1(-rho/rho0) with the two products of a pair packed; the
+// arguments are -1/rho0 and -rho0 (negation is exact, so each lane equals psi_of)
+template <class C> __device__ __forceinline__ P2<C> lane_psi(P2<C> rho, P2<C> neg_inv_rho0, P2<C> neg_rho0)
+{
+    const P2<C> t = rho * neg_inv_rho0;
+    return P2<C>(expm1_c<C>(t.a()), expm1_c<C>(t.b())) * neg_rho0;
+}
+
+// Pairs of adjacent elements to and from shared or global memory, in the
+// compute type (FP16 storage converts both halves at once).
+template <class T> struct Pair;
+template <> struct Pair<float> {
+    __device__ static P2<float> ld(const float* p) { return P2<float>(*reinterpret_cast<const float2*>(p)); }
+    __device__ static void st(float* p, P2<float> v) { *reinterpret_cast<float2*>(p) = v.v; }
+};
+template <> struct Pair<double> {
+    __device__ static P2<double> ld(const double* p)
+    {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        return P2<double>(v.x, v.y);
+    }
+    __device__ static void st(double* p, P2<double> v) { *reinterpret_cast<double2*>(p) = make_double2(v.x, v.y); }
+};
+template <> struct Pair<__half> {
+    __device__ static P2<float> ld(const __half* p) { return P2<float>(__half22float2(*reinterpret_cast<const __half2*>(p))); }
+};
+template <> struct Pair<half_sr> {
+    __device__ static P2<float> ld(const half_sr* p)
+    {
+        return P2<float>(__half22float2(*reinterpret_cast<const __half2*>(p)));
+    }
+};
+
 // ----------------------------------------------------- per-site physics --
 // Interaction sums of Eq. (FFF) at one site for one species, from the
 // differences d_k = g(r + c_k) - g(r - c_k) over the half stencil:
 //   S1 = sum_{belt 1} w c psi_s(r+c),  S2 = sum_{belts 1+2} p c psi_s(r+c),
 //   X  = sum_{belt 1} w c rho_s'(r+c).
-template <class C> struct Sums {
-    C s1x, s1y, s2x, s2y, xx, xy;
+template <class V> struct Sums {
+    V s1x, s1y, s2x, s2y, xx, xy;
 };
 
-template <class C>
-__device__ inline Sums<C> stencil_sums(const C d[12], const C e[4])
+template <class V>
+__device__ inline Sums<V> stencil_sums(const V d[12], const V e[4])
 {
     // Terms grouped by weight (the half stencil is symmetric under x -> -x):
     //   belt 1: (1,0),(0,1) weight 1/9; (1,1),(-1,1) weight 1/36
     //   belts 1+2: |c|^2 = 1: 4/63, 2: 4/135, 4: 1/180, 5: 2/945, 8: 1/15120
-    const C p1 = C(hs_w2(0)), p2 = C(hs_w2(2)), p4 = C(hs_w2(4)), p5 = C(hs_w2(6)), p8 = C(hs_w2(10));
-    const C w1 = C(hs_w1(0)), w2 = C(hs_w1(2));
-    const C dm23 = d[2] - d[3], dp23 = d[2] + d[3];                           // (1,1), (-1,1)
-    const C dm67 = d[6] - d[7], dp67 = d[6] + d[7];                           // (2,1), (-2,1)
-    const C dm89 = d[8] - d[9], dp89 = d[8] + d[9];                           // (1,2), (-1,2)
-    const C dm1011 = d[10] - d[11], dp1011 = d[10] + d[11];                   // (2,2), (-2,2)
-    Sums<C> r;
-    r.s1x = w1 * d[0] + w2 * dm23;
-    r.s1y = w1 * d[1] + w2 * dp23;
-    r.s2x = p1 * d[0] + p2 * dm23 + (C(2) * p4) * d[4] + p5 * (C(2) * dm67 + dm89) + (C(2) * p8) * dm1011;
-    r.s2y = p1 * d[1] + p2 * dp23 + (C(2) * p4) * d[5] + p5 * (dp67 + C(2) * dp89) + (C(2) * p8) * dp1011;
-    r.xx = w1 * e[0] + w2 * (e[2] - e[3]);
-    r.xy = w1 * e[1] + w2 * (e[2] + e[3]);
+    const V p1 = V(hs_w2(0)), p2 = V(hs_w2(2)), p4x2 = V(2.0 * hs_w2(4)), p5 = V(hs_w2(6)), p8x2 = V(2.0 * hs_w2(10));
+    const V w1 = V(hs_w1(0)), w2 = V(hs_w1(2)), two = V(2.0);
+    const V dm23 = d[2] - d[3], dp23 = d[2] + d[3];          // (1,1), (-1,1)
+    const V dm67 = d[6] - d[7], dp67 = d[6] + d[7];          // (2,1), (-2,1)
+    const V dm89 = d[8] - d[9], dp89 = d[8] + d[9];          // (1,2), (-1,2)
+    const V dm1011 = d[10] - d[11], dp1011 = d[10] + d[11];  // (2,2), (-2,2)
+    Sums<V> r;
+    r.s1x = vfma(w2, dm23, w1 * d[0]);
+    r.s1y = vfma(w2, dp23, w1 * d[1]);
+    r.s2x = vfma(p8x2, dm1011, vfma(p5, vfma(two, dm67, dm89), vfma(p4x2, d[4], vfma(p2, dm23, p1 * d[0]))));
+    r.s2y = vfma(p8x2, dp1011, vfma(p5, vfma(two, dp89, dp67), vfma(p4x2, d[5], vfma(p2, dp23, p1 * d[1]))));
+    r.xx = vfma(w2, e[2] - e[3], w1 * e[0]);
+    r.xy = vfma(w2, e[2] + e[3], w1 * e[1]);
     return r;
 }
 
-// Shifted-velocity BGK collision of Eq. (be) for one species s at one site.
+// Shifted-velocity BGK collision of Eq. (be) for one species s at one site (or
+// a pair of sites).
 //   F_s    = -psi_s (G^a S1 + G^r S2) - (G_AB/rho0) rho_s X       (Eq. (FFF))
-//   u_s    = u + tau F_s/rho_s = u - tau[(psi_s/rho_s)(G^a S1 + G^r S2) + (G_AB/rho0) X]
+//   u_s    = u + tau F_s/rho_s = u + tau (a - (psi_s/rho_s)(G^a S1 + G^r S2) - (G_AB/rho0) X)
 //   f*_is  = f_is + omega (f^eq_is(rho_s, u_s) - f_is),  omega = 1/tau, i = 1..8
-// (tau, omega: the species' own relaxation time and rate)
-//   f*_0s  = rho_s - sum_{i>=1} f*_is   (the same value in exact arithmetic)
+// (tau, omega: the species' own relaxation time and rate; ntau = -tau)
+//   f*_0s  = f_0s + sum_{i>=1} (f_is - f*_is)   (the BGK value in exact arithmetic)
 // f^eq_i = w_i rho_s (1 + 3 c_i.u_s + 4.5 (c_i.u_s)^2 - 1.5 u_s^2) is evaluated for
 // the pairs +-c_i together (even part + odd part).
 // u is the common velocity of both species: j / (rho_A + rho_B) for one
@@ -249,97 +372,104 @@ __device__ inline Sums<C> stencil_sums(const C d[12], const C e[4])
 // receives rho_s ax of it (a share proportional to its density), which shifts
 // its equilibrium velocity by tau ax.
 // psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
-// vanishing species density.  Closing the rest population on rho_s keeps the
-// rounded weights (sum of float(w_i) = 1 + 7.5e-9) from biasing the mass.
+// vanishing species density.
+// The rest population closes the mass: each difference f_is - f*_is of nearby
+// values is exact (Sterbenz), so the stored populations sum to the loaded ones
+// up to the one rounding of f*_0s.  (Closing on the rounded sum rho_s instead
+// repeats that sum's rounding at every site of a near-uniform state, which
+// drifted the FP32 mass coherently by 4e-6 per 1000 steps.)
 // *Fx, *Fy receive F_s (for the force-corrected velocity of the observables).
 // UNIT: tau = 1 (omega = 1, the paper's choice for all its runs), where the BGK
 // update is f*_i = f^eq_i exactly and f_i only enters through the moments.
-template <class C, bool UNIT = false>
-__device__ inline void collide_species(const C f[9], C rho_s, C psi_s, C ux, C uy, C ax, const Sums<C>& sm, C ga,
-                                       C gr, C tau, C omega, const ParamSet<C>& p, C fs[9], C* Fx, C* Fy)
+template <class V, bool UNIT = false>
+__device__ inline void collide_species(const V f[9], V rho_s, V psi_s, V ux, V uy, V ax, const Sums<V>& sm, V ga,
+                                       V gr, V gx, V tau, V ntau, V omega, V fs[9], V* Fx, V* Fy)
 {
-    const C gx = p.gab_over_rho0;
-    const C Gx = ga * sm.s1x + gr * sm.s2x;
-    const C Gy = ga * sm.s1y + gr * sm.s2y;
-    *Fx = -psi_s * Gx - gx * rho_s * sm.xx + rho_s * ax;
-    *Fy = -psi_s * Gy - gx * rho_s * sm.xy;
-    const C por = rho_s != C(0) ? fast_div<C>(psi_s, rho_s) : C(1);
-    const C usx = ux - tau * (por * Gx + gx * sm.xx) + tau * ax;
-    const C usy = uy - tau * (por * Gy + gx * sm.xy);
+    const V Gx = vfma(gr, sm.s2x, ga * sm.s1x);
+    const V Gy = vfma(gr, sm.s2y, ga * sm.s1y);
+    *Fx = rho_s * (ax - gx * sm.xx) - psi_s * Gx;
+    *Fy = V(0.0) - vfma(psi_s, Gy, gx * rho_s * sm.xy);
+    const V por = lane_por(psi_s, rho_s);
+    const V hx = vfma(por, Gx, gx * sm.xx);
+    const V hy = vfma(por, Gy, gx * sm.xy);
+    const V usx = vfma(tau, ax - hx, ux);
+    const V usy = vfma(ntau, hy, uy);
     // f^eq of a pair +-c: w rho (1 - 1.5 u^2 + 4.5 (c.u)^2) +- 3 w rho (c.u)
-    const C base = C(1) - C(1.5) * (usx * usx + usy * usy);
-    const C wr1 = C(q_w(1)) * rho_s, wr5 = C(q_w(5)) * rho_s;
-    const C cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
+    const V base = vfma(V(-1.5), vfma(usx, usx, usy * usy), V(1.0));
+    const V wr1 = V(q_w(1)) * rho_s, wr5 = V(q_w(5)) * rho_s;
+    const V tr1 = V(3.0 * q_w(1)) * rho_s, tr5 = V(3.0 * q_w(5)) * rho_s;
+    const V cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
     const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
-    C moving = C(0);
+    V dsum = V(0.0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const C wr = k < 2 ? wr1 : wr5;
-        const C a = wr * (base + C(4.5) * cu[k] * cu[k]);
-        const C b = (C(3) * wr) * cu[k];
+        const V a = (k < 2 ? wr1 : wr5) * vfma(V(4.5) * cu[k], cu[k], base);
+        const V b = (k < 2 ? tr1 : tr5) * cu[k];
         const int i = lo[k], j = hi[k];
         if constexpr (UNIT) {
             fs[i] = a + b;
             fs[j] = a - b;
         } else {
-            fs[i] = f[i] + omega * ((a + b) - f[i]);
-            fs[j] = f[j] + omega * ((a - b) - f[j]);
+            fs[i] = vfma(omega, (a + b) - f[i], f[i]);
+            fs[j] = vfma(omega, (a - b) - f[j], f[j]);
         }
-        moving += fs[i] + fs[j];
+        const V dk = (f[i] - fs[i]) + (f[j] - fs[j]);
+        dsum = k == 0 ? dk : dsum + dk;
     }
-    fs[0] = rho_s - moving;
+    fs[0] = f[0] + dsum;
 }
 
 // The same collision for shifted populations g_i = f_i - w_i rho_bar (FP16
 // storage), computed on g directly: with dr = rho_s - rho_bar,
 //   g^eq_i = f^eq_i - w_i rho_bar = w_i (dr + rho_s (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)),
-//   g*_i = g_i + omega (g^eq_i - g_i),  g*_0 = dr - sum_{i>=1} g*_i,
+//   g*_i = g_i + omega (g^eq_i - g_i),  g*_0 = g_0 + sum_{i>=1} (g_i - g*_i),
 // so no population needs its shift added or removed, and the arithmetic works
 // on the small deviations.  Momenta of g equal those of f (opposite directions
 // carry equal weights).
 // With scale != 1 the populations are scale * g (FP16 storage with stochastic
 // rounding) and so are the results; rho_s, psi_s, u and the forces are not scaled.
-template <class C, bool UNIT = false>
-__device__ inline void collide_species_shifted(const C g[9], C rho_s, C rho_bar, C psi_s, C ux, C uy, C ax,
-                                               const Sums<C>& sm, C ga, C gr, C tau, C omega,
-                                               const ParamSet<C>& p, C gs[9], C* Fx, C* Fy, C scale = C(1))
+template <class V, bool UNIT = false>
+__device__ inline void collide_species_shifted(const V g[9], V rho_s, V rho_bar, V psi_s, V ux, V uy, V ax,
+                                               const Sums<V>& sm, V ga, V gr, V gx, V tau, V ntau, V omega,
+                                               V gs[9], V* Fx, V* Fy, V scale)
 {
-    const C gx = p.gab_over_rho0;
-    const C Gx = ga * sm.s1x + gr * sm.s2x;
-    const C Gy = ga * sm.s1y + gr * sm.s2y;
-    *Fx = -psi_s * Gx - gx * rho_s * sm.xx + rho_s * ax;
-    *Fy = -psi_s * Gy - gx * rho_s * sm.xy;
-    const C por = rho_s != C(0) ? fast_div<C>(psi_s, rho_s) : C(1);
-    const C usx = ux - tau * (por * Gx + gx * sm.xx) + tau * ax;
-    const C usy = uy - tau * (por * Gy + gx * sm.xy);
-    const C dr = (rho_s - rho_bar) * scale, rs = rho_s * scale;
-    const C usq = C(1.5) * (usx * usx + usy * usy);
-    const C w1 = C(q_w(1)), w5 = C(q_w(5));
-    const C cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
+    const V Gx = vfma(gr, sm.s2x, ga * sm.s1x);
+    const V Gy = vfma(gr, sm.s2y, ga * sm.s1y);
+    *Fx = rho_s * (ax - gx * sm.xx) - psi_s * Gx;
+    *Fy = V(0.0) - vfma(psi_s, Gy, gx * rho_s * sm.xy);
+    const V por = lane_por(psi_s, rho_s);
+    const V hx = vfma(por, Gx, gx * sm.xx);
+    const V hy = vfma(por, Gy, gx * sm.xy);
+    const V usx = vfma(tau, ax - hx, ux);
+    const V usy = vfma(ntau, hy, uy);
+    const V dr = (rho_s - rho_bar) * scale, rs = rho_s * scale;
+    const V nusq = V(-1.5) * vfma(usx, usx, usy * usy);
+    const V tr1 = V(3.0 * q_w(1)) * rs, tr5 = V(3.0 * q_w(5)) * rs;
+    const V cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
     const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
-    C moving = C(0);
+    V dsum = V(0.0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const C w = k < 2 ? w1 : w5;
-        const C a = w * (dr + rs * (C(4.5) * cu[k] * cu[k] - usq));
-        const C b = (C(3) * w * rs) * cu[k];
+        const V a = V(k < 2 ? q_w(1) : q_w(5)) * vfma(rs, vfma(V(4.5) * cu[k], cu[k], nusq), dr);
+        const V b = (k < 2 ? tr1 : tr5) * cu[k];
         const int i = lo[k], j = hi[k];
         if constexpr (UNIT) {
             gs[i] = a + b;
             gs[j] = a - b;
         } else {
-            gs[i] = g[i] + omega * ((a + b) - g[i]);
-            gs[j] = g[j] + omega * ((a - b) - g[j]);
+            gs[i] = vfma(omega, (a + b) - g[i], g[i]);
+            gs[j] = vfma(omega, (a - b) - g[j], g[j]);
         }
-        moving += gs[i] + gs[j];
+        const V dk = (g[i] - gs[i]) + (g[j] - gs[j]);
+        dsum = k == 0 ? dk : dsum + dk;
     }
-    gs[0] = dr - moving;
+    gs[0] = g[0] + dsum;
 }
 
 // Momentum of one species' populations, as differences of opposite directions
 // (a state at rest gives exactly zero).
-template <class C> __device__ inline C mom_x(const C f[9]) { return (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]); }
-template <class C> __device__ inline C mom_y(const C f[9]) { return (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]); }
+template <class V> __device__ inline V mom_x(const V f[9]) { return (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]); }
+template <class V> __device__ inline V mom_y(const V f[9]) { return (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]); }
 
 // Result of colliding one site: post-collision populations and the total
 // force (for the force-corrected velocity of the observables).
@@ -359,21 +489,21 @@ __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi
                                     const Sums<C> sm[2], const ParamSet<C>& p, C fx_body, Collided<C>& out)
 {
     const C r = p.mix[0];
-    const C jx = mom_x<C>(f[0]) + r * mom_x<C>(f[1]);
-    const C jy = mom_y<C>(f[0]) + r * mom_y<C>(f[1]);
-    const C inv_rw = fast_div<C>(C(1), rho[0] + r * rho[1]);
+    const C jx = vfma(r, mom_x<C>(f[1]), mom_x<C>(f[0]));
+    const C jy = vfma(r, mom_y<C>(f[1]), mom_y<C>(f[0]));
+    const C inv_rw = lane_rcp(vfma(r, rho[1], rho[0]));
     const C ux = jx * inv_rw, uy = jy * inv_rw;
-    const C ax = r == C(1) ? fx_body * inv_rw : fx_body * fast_div<C>(C(1), rho[0] + rho[1]);
+    const C ax = r == C(1) ? fx_body * inv_rw : fx_body * lane_rcp(rho[0] + rho[1]);
     C Fx[2], Fy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const C tau = s ? p.tau_b : p.tau, omega = s ? p.omega_b : p.omega;
         if (omega == C(1))
-            collide_species<C, true>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], tau, omega, p,
-                                     out.fs[s], &Fx[s], &Fy[s]);
+            collide_species<C, true>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p.gab_over_rho0,
+                                     tau, -tau, omega, out.fs[s], &Fx[s], &Fy[s]);
         else
-            collide_species<C, false>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], tau, omega, p,
-                                      out.fs[s], &Fx[s], &Fy[s]);
+            collide_species<C, false>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p.gab_over_rho0,
+                                      tau, -tau, omega, out.fs[s], &Fx[s], &Fy[s]);
     }
     out.Fx = Fx[0] + Fx[1];
     out.Fy = Fy[0] + Fy[1];

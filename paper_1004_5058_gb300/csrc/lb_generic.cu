@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
     const long long n = (long long)g.nx * g.ny;
     const C* rho_f = aux + (long long)cell * 4 * n;
     double uphys = 0.0, dpx_site = 0.0;
+    bool bad = false;  // watchdog: non-finite or non-positive density at this site
 
     if (active) {
         C f[2][9];
@@ -106,14 +107,16 @@ __global__ void __launch_bounds__(256) fused_generic_kernel(const T* __restrict_
                     Store<T>::st(fout, fidx(g, cell, s * 9 + i, ydd, xd), c.fs[s][i], sh, dz);
                 }
             }
+        const C rt = rho[0] + rho[1];
+        bad = !(rt > C(0)) || !isfinite((double)rho[0]) || !isfinite((double)rho[1]);
         if (SAMPLE) {
-            const C rt = rho[0] + rho[1];
             // force-corrected velocity (j + F/2)/rho
             const C jx = mom_x<C>(f[0]) + mom_x<C>(f[1]);
             uphys = (double)((jx + C(0.5) * c.Fx) / rt);
-            if (!(rt > C(0)) || !isfinite((double)rho[0]) || !isfinite((double)rho[1])) atomicOr(err, ERR_NONFINITE);
         }
     }
+    // every step, sampled or not: one flag per warp into the error word
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_NONFINITE);
     if (SAMPLE) {
         // FP64 warp sums: one warp = 32 consecutive columns of one row.
 #pragma unroll

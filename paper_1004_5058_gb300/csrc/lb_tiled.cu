@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <limits>
 #include <type_traits>
 
 #include "lb_internal.h"
@@ -146,6 +147,52 @@ __device__ inline void st_one(T* p, C v, Dither& d)
         *p = v;
 }
 
+// Element CI (0..5) of a window row of six columns held as three lane pairs.
+template <int CI, class C>
+__device__ __forceinline__ C win_at(const P2<C> (&row)[3])
+{
+    return (CI & 1) ? row[CI >> 1].b() : row[CI >> 1].a();
+}
+
+// g(r + c) - g(r - c) of Eq. (FFF) for both sites of a thread, c = (DX, DY):
+// site o sits at column 2 + o of window row MID.  Pairs at an even column
+// offset are the stored pairs (one packed subtraction); odd offsets straddle
+// two pairs (two scalar subtractions).
+template <int DX, int DY, int MID, int NR, class C>
+__device__ __forceinline__ P2<C> pair_diff(const P2<C> (&w)[NR][3])
+{
+    constexpr int cp = 2 + DX, cm = 2 - DX;
+    if constexpr ((DX & 1) == 0)
+        return w[MID + DY][cp / 2] - w[MID - DY][cm / 2];
+    else
+        return P2<C>(win_at<cp>(w[MID + DY]) - win_at<cm>(w[MID - DY]),
+                     win_at<cp + 1>(w[MID + DY]) - win_at<cm + 1>(w[MID - DY]));
+}
+
+// The half-stencil differences of psi (window rows k-2..k+2) and of the partner
+// density rho_s' (rows k-1..k+1, belt 1 only), in the order of hs_dx / hs_dy.
+template <class C>
+__device__ __forceinline__ void window_diffs(const P2<C> (&v)[5][3], const P2<C> (&e)[3][3], P2<C> d[12],
+                                             P2<C> de[4])
+{
+    d[0] = pair_diff<hs_dx(0), hs_dy(0), 2>(v);
+    d[1] = pair_diff<hs_dx(1), hs_dy(1), 2>(v);
+    d[2] = pair_diff<hs_dx(2), hs_dy(2), 2>(v);
+    d[3] = pair_diff<hs_dx(3), hs_dy(3), 2>(v);
+    d[4] = pair_diff<hs_dx(4), hs_dy(4), 2>(v);
+    d[5] = pair_diff<hs_dx(5), hs_dy(5), 2>(v);
+    d[6] = pair_diff<hs_dx(6), hs_dy(6), 2>(v);
+    d[7] = pair_diff<hs_dx(7), hs_dy(7), 2>(v);
+    d[8] = pair_diff<hs_dx(8), hs_dy(8), 2>(v);
+    d[9] = pair_diff<hs_dx(9), hs_dy(9), 2>(v);
+    d[10] = pair_diff<hs_dx(10), hs_dy(10), 2>(v);
+    d[11] = pair_diff<hs_dx(11), hs_dy(11), 2>(v);
+    de[0] = pair_diff<hs_dx(0), hs_dy(0), 1>(e);
+    de[1] = pair_diff<hs_dx(1), hs_dy(1), 1>(e);
+    de[2] = pair_diff<hs_dx(2), hs_dy(2), 1>(e);
+    de[3] = pair_diff<hs_dx(3), hs_dy(3), 1>(e);
+}
+
 // Threads per CTA: a thread per (species, column pair), TX threads, plus one
 // service warp that issues the TMA copies and computes the four halo columns
 // of psi/rho, so the column warps all do the same work between two barriers.
@@ -211,6 +258,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                                                             unsigned* __restrict__ err, uint32_t skip_row_arg)
 {
     using C = typename Store<T>::C;
+    using V = P2<C>;  // a lane pair: one species at the thread's two sites
     // stored populations are scale * g (scale 1 except for the dithered FP16 storage)
     constexpr C scale = C(Store<T>::scale), inv_scale = C(1) / scale;
     constexpr int E = (int)sizeof(T);
@@ -260,6 +308,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
     const long long items = per_cell * g.n_cells;
     uint32_t nrow = 0;  // global index of row 0 of the current item (rows consumed before it)
     bool aborted = false;
+    bool bad = false;  // watchdog: a non-finite or non-positive density seen in this item
 
     // Issue cursor (producer): the next row to load may belong to a later item
     // of this CTA, so the row pipeline does not drain between items.  Global
@@ -317,14 +366,21 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         p.u_wall = pg.u_wall;
         p.f0 = pg.f0;
         p.two_over_ny = pg.two_over_ny;
-        const C ga = sp ? pg.g1[1] : pg.g1[0], gr = sp ? pg.g2[1] : pg.g2[0];
         // this lane's species relaxes with tau_s; mix weighs the partner species'
         // moments in the common velocity (1, and one_time, for one relaxation time)
         const C tau_s = FULL || !sp ? pg.tau : pg.tau_b, omega_s = FULL || !sp ? pg.omega : pg.omega_b;
         const C mix = FULL ? C(1) : (sp ? pg.mix[1] : pg.mix[0]);
         const bool one_time = FULL || pg.mix[0] == C(1);
-        const bool unit_omega = omega_s == C(1);  // tau_s = 1: f* = f^eq (uniform over each half-warp)
+        // tau = 1 for both species: f* = f^eq.  Uniform over the item, so both
+        // half-warps take the same path (a cell with tau_A = 1 != tau_B runs the
+        // general update in both)
+        const bool unit_omega = FULL ? pg.omega == C(1) : (pg.omega == C(1) && pg.omega_b == C(1));
+        // the same values as lane pairs
+        const V ga = V(sp ? pg.g1[1] : pg.g1[0]), gr = V(sp ? pg.g2[1] : pg.g2[0]), gx = V(p.gab_over_rho0);
+        const V tau2 = V(tau_s), ntau2 = V(-tau_s), omega2 = V(omega_s), mix2 = V(mix);
+        const V neg_inv_rho0 = V(-p.inv_rho0), neg_rho0 = V(-p.rho0);
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
+        const V rho_bar2 = V(rho_bar);
         // columns of this strip inside the lattice (the last strip of a width that
         // is not a multiple of TX is narrower; the TMA box reads zeros beyond it)
         const int wv = FULL ? TX : min(TX, g.nx - x0);
@@ -334,7 +390,10 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p2 = x + 2 == g.nx ? 0 : x + 2;
         T* const dst_s = fout + (long long)cell * g.cellstride + (long long)sp * 9 * g.plane;
 
-        __syncthreads();  // rings of the previous item are no longer read
+        // rings of the previous item are no longer read; the watchdog flags of its
+        // rows are reported
+        if (__syncthreads_or(bad) && t == 0) atomicOr(err, ERR_NONFINITE);
+        bad = false;
 
         if (producer) issue_upto(nrow + D);  // rows of earlier items are all done
         auto wait_row = [&](int k) -> bool {
@@ -349,21 +408,17 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             if (!svc) {
                 if (!act) return;  // its ring positions belong to the halo or to nobody
                 const T* src = reinterpret_cast<const T*>(base) + sp * 9 * TX + c0;
-                C r0 = C(0), r1 = C(0);
+                V r = Pair<T>::ld(src);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    C a, b;
-                    Vec2<T>::ld(src + i * TX, a, b);
-                    r0 += a;
-                    r1 += b;
+                for (int i = 1; i < 9; ++i) r = r + Pair<T>::ld(src + i * TX);
+                if constexpr (Store<T>::shifted) {  // sum of the shifts w_i rho_bar is rho_bar
+                    if constexpr (Store<T>::scale != 1)
+                        r = vfma(r, V(inv_scale), rho_bar2);
+                    else
+                        r = r + rho_bar2;
                 }
-                if (Store<T>::shifted) {  // sum of the shifts w_i rho_bar is rho_bar
-                    r0 = r0 * inv_scale + rho_bar;
-                    r1 = r1 * inv_scale + rho_bar;
-                }
-                Vec2<C>::st(psi_ring + ring + c0 + 2, psi_of<C>(r0, p.rho0, p.inv_rho0),
-                            psi_of<C>(r1, p.rho0, p.inv_rho0));
-                Vec2<C>::st(rho_ring + ring + c0 + 2, r0, r1);
+                Pair<C>::st(psi_ring + ring + c0 + 2, lane_psi<C>(r, neg_inv_rho0, neg_rho0));
+                Pair<C>::st(rho_ring + ring + c0 + 2, r);
             } else if (lane < 8) {
                 // halo column h: 0,1 -> columns -2,-1 (left box); 2,3 -> TX, TX+1 (right box)
                 const int h = lane & 3;
@@ -408,77 +463,74 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             // ---- collide logical row k = j + 2 (lattice row y), sites x and x+1
             const int k = j + 2, y = y0 + j;
             const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT) + sp * 9 * TX + c0;
-            // populations as stored: f for FP32/FP64, the shifted g for FP16
-            C f[2][9];
+            // populations as stored: f for FP32/FP64, the shifted g for FP16; a
+            // lane pair per direction (sites x, x+1)
+            V f[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Vec2<T>::ld(fm + i * TX, f[0][i], f[1][i]);
-            // psi window rows k-2..k+2, columns c0-2..c0+3 (six, as three pairs);
-            // pair differences d_q = psi(r + c_q) - psi(r - c_q) of both sites
+            for (int i = 0; i < 9; ++i) f[i] = Pair<T>::ld(fm + i * TX);
+            // psi window rows k-2..k+2 and rho_s' window rows k-1..k+1, columns
+            // c0-2..c0+3 as three pairs; window column 2 + o is site o
             const C* ps = psi_ring + sp * SS + c0;  // ring column c0 + 2 + dx  <->  column c0 + dx
             const C* ro = rho_ring + (1 - sp) * SS + c0;
-            C v[5][6];
+            V v[5][3], e[3][3];
 #pragma unroll
             for (int d = 0; d < 5; ++d)
 #pragma unroll
-                for (int m = 0; m < 3; ++m) Vec2<C>::ld(ps + rr[d] * W + 2 * m, v[d][2 * m], v[d][2 * m + 1]);
-            C e[3][6];
+                for (int m = 0; m < 3; ++m) v[d][m] = Pair<C>::ld(ps + rr[d] * W + 2 * m);
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
-                for (int m = 0; m < 3; ++m) Vec2<C>::ld(ro + rr[d + 1] * W + 2 * m, e[d][2 * m], e[d][2 * m + 1]);
-            C rho_s[2];
-            Vec2<C>::ld(rho_ring + sp * SS + rr[2] * W + c0 + 2, rho_s[0], rho_s[1]);
-            // window column of site o, offset dx: o + 2 + dx
-            C jx[2], fs[2][9];  // jx: raw x-momentum of the site (observables)
-            C Fx[2], Fy[2], inv_r[2];
+                for (int m = 0; m < 3; ++m) e[d][m] = Pair<C>::ld(ro + rr[d + 1] * W + 2 * m);
+            const V rho_s = Pair<C>::ld(rho_ring + sp * SS + rr[2] * W + c0 + 2);
+            const V rho_p = e[1][1];  // the partner species' densities at the same two sites
+            // pair differences d_q = psi(r + c_q) - psi(r - c_q) of both sites
+            V dps[12], dro[4];
+            window_diffs(v, e, dps, dro);
+            const Sums<V> sm = stencil_sums<V>(dps, dro);
+            const V jx_s = mom_x<V>(f), jy_s = mom_y<V>(f);
+            const V jx_p(__shfl_xor_sync(0xffffffffu, jx_s.a(), 16), __shfl_xor_sync(0xffffffffu, jx_s.b(), 16));
+            const V jy_p(__shfl_xor_sync(0xffffffffu, jy_s.a(), 16), __shfl_xor_sync(0xffffffffu, jy_s.b(), 16));
+            // common velocity: (j_own + mix j_partner) / (rho_own + mix rho_partner)
+            V jwx, jwy, rho_w;
+            if constexpr (FULL) {  // one relaxation time: the barycentric velocity
+                jwx = jx_s + jx_p;
+                jwy = jy_s + jy_p;
+                rho_w = rho_s + rho_p;
+            } else {
+                jwx = vfma(mix2, jx_p, jx_s);
+                jwy = vfma(mix2, jy_p, jy_s);
+                rho_w = vfma(mix2, rho_p, rho_s);
+            }
+            if constexpr (Store<T>::scale != 1) {
+                jwx = jwx * V(inv_scale);
+                jwy = jwy * V(inv_scale);
+            }
+            const V inv_rho = lane_rcp(rho_w);
+            const V ux = jwx * inv_rho, uy = jwy * inv_rho;
             const C fx_body = body_force_x<C>(p, y);
             const bool body_raw = !one_time && fx_body != C(0);  // the force needs the raw 1/rho
-#pragma unroll
-            for (int o = 0; o < 2; ++o) {
-                C dps[12], dro[4];
-#pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    const int dx = hs_dx(q), dy = hs_dy(q);
-                    dps[q] = v[2 + dy][o + 2 + dx] - v[2 - dy][o + 2 - dx];
-                    if (q < 4) dro[q] = e[1 + dy][o + 2 + dx] - e[1 - dy][o + 2 - dx];
-                }
-                const Sums<C> sm = stencil_sums<C>(dps, dro);
-                const C jx_s = mom_x<C>(f[o]), jy_s = mom_y<C>(f[o]);
-                const C jx_p = __shfl_xor_sync(0xffffffffu, jx_s, 16), jy_p = __shfl_xor_sync(0xffffffffu, jy_s, 16);
-                // common velocity: (j_own + mix j_partner) / (rho_own + mix rho_partner)
-                C jwx, jwy, rho_w;
-                if constexpr (FULL) {  // one relaxation time: the barycentric velocity
-                    jwx = (jx_s + jx_p) * inv_scale;
-                    jwy = (jy_s + jy_p) * inv_scale;
-                    rho_w = rho_s[o] + e[1][o + 2];
-                } else {
-                    jwx = (jx_s + mix * jx_p) * inv_scale;
-                    jwy = (jy_s + mix * jy_p) * inv_scale;
-                    rho_w = rho_s[o] + mix * e[1][o + 2];
-                }
-                const C inv_rho = fast_div<C>(C(1), rho_w);
-                const C ux = jwx * inv_rho, uy = jwy * inv_rho;
-                C ax = fx_body * inv_rho;
-                if (body_raw) ax = fx_body * fast_div<C>(C(1), rho_s[o] + e[1][o + 2]);
-                if (SAMPLE) {
-                    jx[o] = one_time ? jwx : (jx_s + jx_p) * inv_scale;
-                    inv_r[o] = one_time ? inv_rho : fast_div<C>(C(1), rho_s[o] + e[1][o + 2]);
-                }
-                if (Store<T>::shifted) {
-                    if (unit_omega)
-                        collide_species_shifted<C, true>(f[o], rho_s[o], rho_bar, v[2][o + 2], ux, uy, ax, sm, ga, gr,
-                                                         tau_s, omega_s, p, fs[o], &Fx[o], &Fy[o], scale);
-                    else
-                        collide_species_shifted<C, false>(f[o], rho_s[o], rho_bar, v[2][o + 2], ux, uy, ax, sm, ga,
-                                                          gr, tau_s, omega_s, p, fs[o], &Fx[o], &Fy[o], scale);
-                } else {
-                    if (unit_omega)
-                        collide_species<C, true>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, tau_s, omega_s,
-                                                 p, fs[o], &Fx[o], &Fy[o]);
-                    else
-                        collide_species<C, false>(f[o], rho_s[o], v[2][o + 2], ux, uy, ax, sm, ga, gr, tau_s, omega_s,
-                                                  p, fs[o], &Fx[o], &Fy[o]);
-                }
+            const V rho_t = FULL ? rho_w : rho_s + rho_p;        // total density of each site
+            V ax = V(fx_body) * inv_rho;
+            if (body_raw) ax = V(fx_body) * lane_rcp(rho_t);
+            // watchdog: a non-finite or non-positive total density anywhere in the
+            // item is reported through the error word when the item ends
+            if (act) bad |= !(rho_t.a() > C(0) && rho_t.a() <= std::numeric_limits<C>::max() && rho_t.b() > C(0) &&
+                              rho_t.b() <= std::numeric_limits<C>::max());
+            V fs[9], Fx, Fy;
+            if constexpr (Store<T>::shifted) {
+                if (unit_omega)
+                    collide_species_shifted<V, true>(f, rho_s, rho_bar2, v[2][1], ux, uy, ax, sm, ga, gr, gx, tau2,
+                                                     ntau2, omega2, fs, &Fx, &Fy, V(scale));
+                else
+                    collide_species_shifted<V, false>(f, rho_s, rho_bar2, v[2][1], ux, uy, ax, sm, ga, gr, gx, tau2,
+                                                      ntau2, omega2, fs, &Fx, &Fy, V(scale));
+            } else {
+                if (unit_omega)
+                    collide_species<V, true>(f, rho_s, v[2][1], ux, uy, ax, sm, ga, gr, gx, tau2, ntau2, omega2, fs,
+                                             &Fx, &Fy);
+                else
+                    collide_species<V, false>(f, rho_s, v[2][1], ux, uy, ax, sm, ga, gr, gx, tau2, ntau2, omega2, fs,
+                                              &Fx, &Fy);
             }
 
             // stochastic rounding: one stream per thread and row, seeded from the
@@ -486,7 +538,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             Dither dz;
             if constexpr (Store<T>::dithered)
                 dz.seed(((uint32_t)cell * 0x9E3779B1u) ^ ((uint32_t)y << 15) ^ ((uint32_t)x << 1) ^ (uint32_t)sp,
-                        __float_as_uint(rho_s[0]) ^ (__float_as_uint(rho_s[1]) * 0x85EBCA6Bu));
+                        __float_as_uint(rho_s.a()) ^ (__float_as_uint(rho_s.b()) * 0x85EBCA6Bu));
             // push streaming; rows next to a Couette wall bounce back in place
             const bool wall_lo = bc == 1 && y == 0, wall_hi = bc == 1 && y == g.ny - 1;
             const int pl = (int)g.plane;  // < 2^31 / 18, checked on the host
@@ -502,10 +554,10 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                     for (int i = 0; i < 9; ++i) {
                         const int cy = q_cy(i), cx = q_cx(i);
                         if (cx == 0) {
-                            st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
+                            st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[i].a(), fs[i].b(), dz);
                         } else {
-                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
-                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[i].a(), dz);
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[i].b(), dz);
                         }
                     }
                 } else {
@@ -520,28 +572,34 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                             // is put back first; opposite directions carry equal weights,
                             // so the same shift is removed again)
                             const C sh = Store<T>::shifted ? C(q_w(i)) * rho_bar : C(0);
-                            const C ba = bounce<C>(i, fs[0][i] * inv_scale + sh, rho_s[0], uw, &dpa);
-                            const C bb = bounce<C>(i, fs[1][i] * inv_scale + sh, rho_s[1], uw, &dpb);
+                            const C ba = bounce<C>(i, fs[i].a() * inv_scale + sh, rho_s.a(), uw, &dpa);
+                            const C bb = bounce<C>(i, fs[i].b() * inv_scale + sh, rho_s.b(), uw, &dpb);
                             st_pair<T, C>(dst_s + q_opp(i) * pl + row3[1] + x, (ba - sh) * scale, (bb - sh) * scale, dz);
                             dpx_site += dpa + dpb;
                         } else if (cx == 0) {
-                            st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[0][i], fs[1][i], dz);
+                            st_pair<T, C>(dst_s + i * pl + row3[cy + 1] + x, fs[i].a(), fs[i].b(), dz);
                         } else {
-                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[0][i], dz);
-                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[1][i], dz);
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colA[cx + 1], fs[i].a(), dz);
+                            st_one<T, C>(dst_s + i * pl + row3[cy + 1] + colB[cx + 1], fs[i].b(), dz);
                         }
                     }
                 }
             }
             if (SAMPLE) {
+                // force-corrected velocity (j + F/2)/rho of the observables, from the
+                // raw barycentric momentum and density
+                V jxo = jwx, inv_r = inv_rho;
+                if (!one_time) {
+                    jxo = jx_s + jx_p;
+                    if constexpr (Store<T>::scale != 1) jxo = jxo * V(inv_scale);
+                    inv_r = lane_rcp(rho_t);
+                }
                 // one site per lane: species-A lanes take column x, species-B
                 // lanes column x+1; each lane sends its partner the force the
                 // partner's site needs, so one shuffle gives F_x of both species
-                const C fx_partner = __shfl_xor_sync(0xffffffffu, sp ? Fx[0] : Fx[1], 16);
-                const C Fx_t = (sp ? Fx[1] : Fx[0]) + fx_partner;
-                const C rho_t = sp ? rho_s[1] + e[1][3] : rho_s[0] + e[1][2];
-                const C up = ((sp ? jx[1] : jx[0]) + C(0.5) * Fx_t) * (sp ? inv_r[1] : inv_r[0]);
-                if (act && (!(rho_t > C(0)) || !isfinite(rho_t))) atomicOr(err, ERR_NONFINITE);
+                const C fx_partner = __shfl_xor_sync(0xffffffffu, sp ? Fx.a() : Fx.b(), 16);
+                const C Fx_t = (sp ? Fx.b() : Fx.a()) + fx_partner;
+                const C up = ((sp ? jxo.b() : jxo.a()) + C(0.5) * Fx_t) * (sp ? inv_r.b() : inv_r.a());
                 // the row sums of u_x are the service warp's (svc_profile, after the
                 // next barrier): sums carried as an unevaluated pair (error-free
                 // two-sum), then added in FP64, ~2^-48 relative
@@ -569,6 +627,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         }
         nrow += (uint32_t)R;
     }
+    if (__syncthreads_or(bad) && t == 0) atomicOr(err, ERR_NONFINITE);
 }
 
 // ------------------------------------------------------------- host side --

@@ -100,7 +100,9 @@ def test_1000_steps_two_times_conserve_momentum(kernel, prec, tol):
     assert max_abs(ga[0], oa) <= tol and max_abs(gb[0], ob) <= tol
     assert max_abs(gu[0], ou) <= tol and max_abs(gv[0], ov) <= tol
     m0 = (ra.sum(), rb.sum())
-    mtol = 1e-13 if prec == "fp64" else 1e-5
+    # FP32: the rest population closes on the loaded populations (one rounding per
+    # site and step, not coherent from site to site; see test_gpu_parity)
+    mtol = 1e-13 if prec == "fp64" else 2e-6
     assert abs(mass[0, 0] - m0[0]) / m0[0] <= mtol and abs(mass[0, 1] - m0[1]) / m0[1] <= mtol
     assert abs(mom[0]).max() / (m0[0] + m0[1]) <= (1e-13 if prec == "fp64" else 1e-6)
 
