@@ -183,6 +183,12 @@ lb_status lb_autotune(lb_handle* h, const char* cache_path);
 /* Reads the kernel family and tile in use (outputs nullable). */
 lb_status lb_get_kernel(const lb_handle* h, lb_kernel* kernel, int* tile_x, int* tile_y);
 
+/* Launch shape of the tiled kernel in use (outputs nullable): persistent CTAs of
+ * plain and of sampled steps (each as many as fit on the GPU, at most one per
+ * work item), threads and dynamic shared memory bytes per CTA.
+ * LB_ERR_UNSUPPORTED for the generic kernel. */
+lb_status lb_launch_shape(const lb_handle* h, int* ctas, int* ctas_sampled, int* threads, int* smem_bytes);
+
 /* Waits for all enqueued work of the handle; reports device errors. */
 lb_status lb_sync(lb_handle* h);
 
@@ -267,6 +273,77 @@ long long lb_kernel_launches(const lb_handle* h);
  * size), LB_ERR_UNSUPPORTED, LB_ERR_CUDA; message in lb_last_error(NULL). */
 lb_status lb_reductions_noalloc(const void* populations, lb_precision prec, int nx, int ny, int pitch,
                                 int n_cells, double* sums, void* cuda_stream);
+
+/* ---- One cell split into horizontal slabs (one handle, and possibly one GPU,
+ * per slab).  The paper runs single 512 x 512 lattices for 10^6 steps; larger
+ * cells than one GPU holds are split along y.  A slab owns rows [y0, y0 + rows)
+ * of each cell and keeps two ghost rows on each side: the interaction stencil of
+ * Eq. (FFF) reaches two rows out, and push streaming moves populations one row.
+ * Per time step the slabs trade two kinds of rows with their neighbours (the
+ * slab below holds the rows just below y0; in a periodic cell the first and last
+ * slabs are neighbours; across a Couette wall there is none):
+ *   before the step  each slab's first two and last two own rows, all 18
+ *                    populations, into the neighbours' ghost rows
+ *                    (lb_slab_get EDGE_LO / EDGE_HI, lb_slab_put EDGE_HI / EDGE_LO);
+ *   lb_step(h, 1)    the slab's own rows, exactly as the whole-cell step updates
+ *                    them, except the populations that stream in from the
+ *                    neighbours; those that stream out land in the ghost rows;
+ *   after the step   the c_y = -1 populations that left through the lower edge
+ *                    into the slab below's last row, the c_y = +1 ones that left
+ *                    through the upper edge into the slab above's first row
+ *                    (lb_slab_get FLOW_LO / FLOW_HI, lb_slab_put FLOW_HI / FLOW_LO).
+ * Done this way, the slabs' rows equal the whole-cell run's bit for bit. */
+typedef enum {
+    LB_SLAB_EDGE_LO = 0,  /* get: own rows 0, 1; put: the ghost rows below (the slab below's EDGE_HI) */
+    LB_SLAB_EDGE_HI = 1,  /* get: own rows rows-2, rows-1; put: the ghost rows above (the slab above's EDGE_LO) */
+    LB_SLAB_FLOW_LO = 2,  /* get: the c_y = -1 populations that left downwards; put: the c_y = +1 populations
+                             that came up into own row 0 (the slab below's FLOW_HI) */
+    LB_SLAB_FLOW_HI = 3   /* get: the c_y = +1 populations that left upwards; put: the c_y = -1 populations
+                             that came down into the last own row (the slab above's FLOW_LO) */
+} lb_slab_part;
+
+/* Creates a slab handle: rows [y0, y0 + rows) of each of the n_cells cells
+ * (cells[].ny is the whole cell's height; rows >= 2; y0 + rows <= ny; a
+ * periodic cell needs rows + 4 <= ny).  Like lb_create otherwise; the tiled
+ * kernel only (LB_ERR_UNSUPPORTED where its shape rules exclude the cell).
+ * On a slab handle every call that takes or returns fields, populations,
+ * profiles or sums works on the own rows ([n_cells][rows][nx] host arrays,
+ * [n_cells][2][9][rows][nx] populations); lb_step takes one step per call
+ * (n_steps 0 or 1, else LB_ERR_INVALID); lb_shear_stress, lb_save and lb_load
+ * give LB_ERR_UNSUPPORTED (the stress needs both walls: combine lb_get_profile
+ * and lb_wall_momentum over the slabs).  The ghost rows hold nothing until the
+ * first exchange: trade edges before the first step. */
+lb_status lb_create_slab(const lb_cell_params* cells, int n_cells, lb_precision prec, int y0, int rows,
+                         void* cuda_stream, lb_handle** out);
+
+/* First own row, own rows and the whole cell's height of a slab (outputs
+ * nullable; for a whole-cell handle 0, ny, ny and LB_ERR_UNSUPPORTED). */
+lb_status lb_slab_info(const lb_handle* h, int* y0, int* rows, int* ny_global);
+
+/* Size of a slab message, the same for get and put of a part:
+ * EDGE n_cells * 18 * 2 * nx elements, FLOW n_cells * 6 * nx elements, in the
+ * storage precision (2, 4 or 8 bytes).  Layout [cell][population][row][x], x
+ * dense; FLOW populations in the order 2, 5, 6 (or 4, 7, 8) of species A, then
+ * B. */
+lb_status lb_slab_message_bytes(const lb_handle* h, lb_slab_part part, size_t* bytes);
+
+/* Packs a message from the slab's current state into the caller's device buffer
+ * dst (lb_slab_get), or unpacks one into it (lb_slab_put), on the handle's
+ * stream; asynchronous, the copy is ordered with the handle's other work only.
+ * The buffer must be device memory of the handle's device holding
+ * lb_slab_message_bytes from the pointer on (else LB_ERR_INVALID before
+ * anything is enqueued).  Ownership stays with the caller; across devices the
+ * caller moves messages between buffers (peer copies, NCCL send/recv).
+ * LB_ERR_UNSUPPORTED on a whole-cell handle, LB_ERR_STATE before a state is
+ * loaded. */
+lb_status lb_slab_get(lb_handle* h, lb_slab_part part, void* dst);
+lb_status lb_slab_put(lb_handle* h, lb_slab_part part, const void* src);
+
+/* Time sums over the sampled steps of the x-momentum the walls delivered
+ * (sums [n_cells][2] = Pi_top, Pi_bot as in lb_shear_stress, zero for a wall a
+ * slab does not hold) and the number of sampled steps (nullable).
+ * Synchronous. */
+lb_status lb_wall_momentum(lb_handle* h, double* sums, long long* n_samples);
 
 /* Message for the last failing call on h; a static string when h is NULL. */
 const char* lb_last_error(const lb_handle* h);

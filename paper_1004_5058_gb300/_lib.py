@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "LB_OK", -1: "LB_ERR_INVALID", -2: "LB_ERR_CUDA", -3: "LB_ERR
 LB_BC_PERIODIC, LB_BC_COUETTE = 0, 1
 LB_FP32, LB_FP16_SHIFTED, LB_FP64, LB_FP16_SHIFTED_SR = 0, 1, 2, 3
 LB_KERNEL_AUTO, LB_KERNEL_GENERIC, LB_KERNEL_TILED = 0, 1, 2
+LB_SLAB_EDGE_LO, LB_SLAB_EDGE_HI, LB_SLAB_FLOW_LO, LB_SLAB_FLOW_HI = 0, 1, 2, 3
 
 # Every function the header declares, with its ctypes signature.
 _D = C.POINTER(C.c_double)
@@ -62,6 +63,15 @@ SIGNATURES = {
     "lb_hb_fit": (C.c_int, [_D, _D, C.c_int, C.c_double, C.c_double, _D]),
     "lb_reductions_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                         C.c_void_p]),
+    "lb_create_slab": (C.c_int, [C.POINTER(lb_cell_params), C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                 C.POINTER(_H)]),
+    "lb_slab_info": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lb_slab_message_bytes": (C.c_int, [_H, C.c_int, C.POINTER(C.c_size_t)]),
+    "lb_slab_get": (C.c_int, [_H, C.c_int, C.c_void_p]),
+    "lb_slab_put": (C.c_int, [_H, C.c_int, C.c_void_p]),
+    "lb_wall_momentum": (C.c_int, [_H, _D, C.POINTER(C.c_longlong)]),
+    "lb_launch_shape": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]),
     # include/lbhb_mlp.h
     "mlp_param_count": (C.c_longlong, []),
     "mlp_create": (C.c_int, [C.POINTER(mlp_config), C.c_void_p, C.POINTER(_H)]),

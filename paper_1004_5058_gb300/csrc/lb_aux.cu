@@ -176,7 +176,32 @@ __global__ void accumulate_kernel(const double* __restrict__ prof_part, const do
     }
 }
 
+// Slab messages: `planes` of rows [row0, row0 + nrows) of the population
+// buffer of every cell, packed as [cell][plane k][row r][x] (dense in x), in
+// the storage format (no conversion).
+template <class T>
+__global__ void slab_msg_kernel(T* __restrict__ f, T* __restrict__ msg, Geom g, SlabMsg m, int pack)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int k = blockIdx.y / m.nrows, r = blockIdx.y % m.nrows, cell = blockIdx.z;
+    const long long km = (((long long)cell * m.n_planes + k) * m.nrows + r) * g.nx + x;
+    const long long kf = fidx(g, cell, m.planes[k], m.row0 + r, x);
+    if (pack)
+        msg[km] = f[kf];
+    else
+        f[kf] = msg[km];
+}
+
 // ------------------------------------------------------------ launchers --
+template <class T>
+cudaError_t launch_slab_msg(T* f, T* msg, const Geom& g, const SlabMsg& m, bool pack, cudaStream_t st)
+{
+    dim3 blk(128), grd((g.nx + 127) / 128, m.n_planes * m.nrows, g.n_cells);
+    slab_msg_kernel<T><<<grd, blk, 0, st>>>(f, msg, g, m, pack ? 1 : 0);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_equilibrium(const double* src, T* f, const Geom& g, const CellDev* cells, cudaStream_t st)
 {
@@ -244,7 +269,8 @@ cudaError_t launch_accumulate(const double* prof_part, const double* wall_part, 
     template cudaError_t launch_fields<T>(const T*, double*, const Geom&, const CellDev*, unsigned*,          \
                                           cudaStream_t);                                                    \
     template cudaError_t launch_state_sums<T>(const T*, const Geom&, const CellDev*, double*, double*,       \
-                                              unsigned*, cudaStream_t);
+                                              unsigned*, cudaStream_t);                                     \
+    template cudaError_t launch_slab_msg<T>(T*, T*, const Geom&, const SlabMsg&, bool, cudaStream_t);
 LBHB_INST(float)
 LBHB_INST(double)
 LBHB_INST(__half)

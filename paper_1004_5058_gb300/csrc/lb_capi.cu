@@ -35,7 +35,11 @@ struct lb_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    Geom g{};
+    Geom g{};                          // the rows a step updates: ny = own rows (the whole cell, or a slab)
+    Geom gbuf{};                       // the whole population buffer (a slab adds two ghost rows each side)
+    RowMap rm{};
+    long long view_off = 0;            // elements from a buffer's start to row 0 of g
+    bool slab = false;
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     void* aux = nullptr;               // generic family: rho/psi field
@@ -175,6 +179,9 @@ static cudaError_t with_type(const lb_handle* h, F&& fn)
     }
 }
 
+// Buffer b at row 0 of the updated rows (the whole buffer for a whole cell).
+static void* fview(const lb_handle* h, int b) { return (char*)h->f[b] + h->view_off * h->elem; }
+
 static lb_status check_device_error(lb_handle* h)
 {
     unsigned e = 0;
@@ -219,11 +226,13 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
         const int txs[] = {128, 64, 32};
         for (int pass = 0; pass < 2; ++pass)
             for (int c : txs)
-                if ((pass == 1 || h->nx % c == 0) && tiled_supported(h->g, h->elem, c, 0) &&
+                if ((pass == 1 || h->nx % c == 0) && tiled_supported(h->gbuf, h->elem, c, 0) &&
                     select_kernel(h, LB_KERNEL_TILED, c, 0) == LB_OK)
                     return LB_OK;
         return select_kernel(h, LB_KERNEL_GENERIC, 0, 0);
     }
+    if (k == LB_KERNEL_GENERIC && h->slab)
+        return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: a slab runs the tiled kernel only");
     free_graphs(h);
     if (k == LB_KERNEL_GENERIC) {
         if (h->plan) {
@@ -244,13 +253,13 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
                 break;
             }
     }
-    if (!tiled_supported(h->g, h->elem, tx, ty))
+    if (!tiled_supported(h->gbuf, h->elem, tx, ty))
         return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: tiled kernel does not support nx=%d ny=%d tile %dx%d",
                     h->nx, h->ny, tx, ty);
     if (tiled_partials_nbx(h->g, tx) > h->nbx_alloc)
         return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: tile %d too narrow for the partial buffers", tx);
     const char* msg = nullptr;
-    TiledPlan* p = tiled_create(h->g, (int)h->prec, h->elem, h->bc, h->f[0], h->f[1], tx, ty, &msg);
+    TiledPlan* p = tiled_create(h->gbuf, h->rm, (int)h->prec, h->elem, h->bc, h->f[0], h->f[1], tx, ty, &msg);
     if (!p) return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: %s", msg ? msg : "tiled plan failed");
     tiled_set_one_time(p, one_relaxation_time(h->cells));
     if (h->plan) tiled_destroy(h->plan);
@@ -380,10 +389,10 @@ static bool cells_valid(const lb_cell_params* cells, int n_cells, char* why, siz
     return true;
 }
 
-extern "C" {
-
-lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec, void* cuda_stream,
-                    lb_handle** out)
+// A handle over the whole cells (rows < 0), or over rows [y0, y0 + rows) of
+// each cell with two ghost rows on each side (a slab).
+static lb_status create_handle(const lb_cell_params* cells, int n_cells, lb_precision prec, void* cuda_stream,
+                               int y0, int rows, lb_handle** out)
 {
     if (!out) return fail(nullptr, LB_ERR_INVALID, "lb_create: out is NULL");
     *out = nullptr;
@@ -393,12 +402,22 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
     char why[256];
     if (!cells_valid(cells, n_cells, why, sizeof why)) return fail(nullptr, LB_ERR_INVALID, "lb_create: %s", why);
     const lb_cell_params& c0 = cells[0];
+    const bool slab = rows >= 0;
+    if (slab) {
+        if (rows < 2 || y0 < 0 || (long long)y0 + rows > c0.ny)
+            return fail(nullptr, LB_ERR_INVALID, "lb_create_slab: rows [%d, %d) do not fit a cell of %d rows (and a "
+                        "slab needs at least 2)", y0, y0 + rows, c0.ny);
+        if (c0.bc == LB_BC_PERIODIC && rows + 4 > c0.ny)
+            return fail(nullptr, LB_ERR_INVALID, "lb_create_slab: a periodic cell of %d rows cannot hold a slab of "
+                        "%d rows and its four ghost rows", c0.ny, rows);
+    }
     lb_handle* h = new (std::nothrow) lb_handle();
     if (!h) return fail(nullptr, LB_ERR_NOMEM, "lb_create: out of host memory");
     h->n_cells = n_cells;
     h->nx = c0.nx;
-    h->ny = c0.ny;
+    h->ny = slab ? rows : c0.ny;  // the rows a step updates
     h->bc = c0.bc;
+    h->slab = slab;
     h->prec = prec;
     h->elem = prec == LB_FP64 ? 8 : (prec == LB_FP32 ? 4 : 2);
     h->cells.assign(cells, cells + n_cells);
@@ -417,13 +436,21 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
         h->own_stream = true;
     }
     const int align = 128 / h->elem;  // rows start on 128-byte boundaries
-    h->g.nx = h->nx;
+    h->gbuf.nx = h->nx;
+    h->gbuf.ny = slab ? rows + 4 : h->ny;
+    h->gbuf.pitch = (h->nx + align - 1) / align * align;
+    h->gbuf.n_cells = n_cells;
+    h->gbuf.plane = (long long)h->gbuf.ny * h->gbuf.pitch;
+    h->gbuf.cellstride = 18 * h->gbuf.plane;
+    h->g = h->gbuf;  // the updated rows as a view of the buffer: same strides, fewer rows
     h->g.ny = h->ny;
-    h->g.pitch = (h->nx + align - 1) / align * align;
-    h->g.n_cells = n_cells;
-    h->g.plane = (long long)h->ny * h->g.pitch;
-    h->g.cellstride = 18 * h->g.plane;
-    const size_t fbytes = (size_t)n_cells * h->g.cellstride * h->elem;
+    h->view_off = slab ? 2LL * h->gbuf.pitch : 0;
+    h->rm.ylo = slab ? 2 : 0;
+    h->rm.nown = h->ny;
+    h->rm.y0g = slab ? y0 : 0;
+    h->rm.nyg = c0.ny;
+    h->rm.slab = slab ? 1 : 0;
+    const size_t fbytes = (size_t)n_cells * h->gbuf.cellstride * h->elem;
     const size_t n = (size_t)h->nx * h->ny;
     const size_t cbytes = prec == LB_FP64 ? 8 : 4;
     h->nbx_alloc = std::max(generic_partials_nbx(h->g), tiled_partials_nbx(h->g, 32));
@@ -475,6 +502,21 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
     return LB_OK;
 }
 
+extern "C" {
+
+lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec, void* cuda_stream,
+                    lb_handle** out)
+{
+    return create_handle(cells, n_cells, prec, cuda_stream, 0, -1, out);
+}
+
+lb_status lb_create_slab(const lb_cell_params* cells, int n_cells, lb_precision prec, int y0, int rows,
+                         void* cuda_stream, lb_handle** out)
+{
+    if (rows < 0) return fail(nullptr, LB_ERR_INVALID, "lb_create_slab: rows < 0");
+    return create_handle(cells, n_cells, prec, cuda_stream, y0, rows, out);
+}
+
 lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b, const double* ux,
                          const double* uy)
 {
@@ -495,7 +537,7 @@ lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b,
     }
     CK(h, with_type(h, [&](auto* tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        return launch_equilibrium<T>(h->staging, (T*)h->f[0], h->g, h->d_cells, h->stream);
+        return launch_equilibrium<T>(h->staging, (T*)fview(h, 0), h->g, h->d_cells, h->stream);
     }));
     h->launches += 1;
     h->cur = 0;
@@ -519,7 +561,7 @@ lb_status lb_set_populations(lb_handle* h, const double* f)
     if (e == cudaSuccess)
         e = with_type(h, [&](auto* tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
-            return launch_import<T>(tmp, (T*)h->f[0], h->g, h->d_cells, h->stream);
+            return launch_import<T>(tmp, (T*)fview(h, 0), h->g, h->d_cells, h->stream);
         });
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
@@ -544,7 +586,7 @@ lb_status lb_get_populations(lb_handle* h, double* f)
     CK(h, cudaMalloc(&tmp, bytes));
     cudaError_t e = with_type(h, [&](auto* tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        return launch_export<T>((const T*)h->f[h->cur], tmp, h->g, h->d_cells, h->stream);
+        return launch_export<T>((const T*)fview(h, h->cur), tmp, h->g, h->d_cells, h->stream);
     });
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -630,6 +672,9 @@ lb_status lb_step(lb_handle* h, long long n_steps)
     Trace trace("lb_step");
     if (!h) return LB_ERR_INVALID;
     if (n_steps < 0) return fail(h, LB_ERR_INVALID, "lb_step: n_steps < 0");
+    if (h->slab && n_steps > 1)
+        return fail(h, LB_ERR_INVALID, "lb_step: a slab takes one step per call (its ghost rows and the populations "
+                    "that left it are traded between steps)");
     if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_step: no state loaded (call lb_init_fields)");
     if (h->faulted) return fail(h, LB_ERR_STATE, "lb_step: an earlier device error left the state invalid");
     CK(h, cudaSetDevice(h->device));
@@ -727,6 +772,9 @@ lb_status lb_shear_stress(lb_handle* h, double* sigma_xy, double* shear_rate, do
     Trace trace("lb_shear_stress");
     if (!h) return LB_ERR_INVALID;
     if (!sigma_xy || !shear_rate) return fail(h, LB_ERR_INVALID, "lb_shear_stress: outputs are NULL");
+    if (h->slab)
+        return fail(h, LB_ERR_UNSUPPORTED, "lb_shear_stress: a slab holds part of the cell (combine lb_get_profile "
+                    "and lb_wall_momentum over the slabs)");
     std::vector<double> prof, wall;
     lb_status st = read_acc(h, prof, wall);
     if (st != LB_OK) return st;
@@ -776,7 +824,7 @@ lb_status lb_get_fields(lb_handle* h, double* rho_a, double* rho_b, double* ux, 
     if (!h->staging) CK(h, cudaMalloc(&h->staging, sizeof(double) * 4 * n * h->n_cells));
     CK(h, with_type(h, [&](auto* tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        return launch_fields<T>((const T*)h->f[h->cur], h->staging, h->g, h->d_cells, h->d_err, h->stream);
+        return launch_fields<T>((const T*)fview(h, h->cur), h->staging, h->g, h->d_cells, h->d_err, h->stream);
     }));
     h->launches += 1;
     double* dst[4] = {rho_a, rho_b, ux, uy};
@@ -795,7 +843,7 @@ lb_status lb_reductions(lb_handle* h, double* mass_ab, double* momentum_xy)
     CK(h, cudaSetDevice(h->device));
     CK(h, with_type(h, [&](auto* tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        return launch_state_sums<T>((const T*)h->f[h->cur], h->g, h->d_cells, h->red_part, h->red_out, h->d_err,
+        return launch_state_sums<T>((const T*)fview(h, h->cur), h->g, h->d_cells, h->red_part, h->red_out, h->d_err,
                                     h->stream);
     }));
     h->launches += 2;
@@ -833,6 +881,14 @@ lb_status lb_get_kernel(const lb_handle* h, lb_kernel* kernel, int* tile_x, int*
     return LB_OK;
 }
 
+lb_status lb_launch_shape(const lb_handle* h, int* ctas, int* ctas_sampled, int* threads, int* smem_bytes)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (h->kernel != LB_KERNEL_TILED || !h->plan) return LB_ERR_UNSUPPORTED;
+    tiled_launch_shape(h->plan, ctas, ctas_sampled, threads, smem_bytes);
+    return LB_OK;
+}
+
 lb_status lb_autotune(lb_handle* h, const char* cache_path)
 {
     Trace trace("lb_autotune");
@@ -845,8 +901,8 @@ lb_status lb_autotune(lb_handle* h, const char* cache_path)
     for (char* c = devname; *c; ++c)
         if (*c == ' ') *c = '_';
     char key[512];
-    snprintf(key, sizeof key, "%s nx=%d ny=%d cells=%d prec=%d bc=%d", devname, h->nx, h->ny, h->n_cells,
-             (int)h->prec, h->bc);
+    snprintf(key, sizeof key, "%s nx=%d ny=%d cells=%d prec=%d bc=%d%s", devname, h->nx, h->ny, h->n_cells,
+             (int)h->prec, h->bc, h->slab ? " slab" : "");
     if (cache_path) {
         FILE* fp = fopen(cache_path, "r");
         if (fp) {
@@ -871,7 +927,7 @@ lb_status lb_autotune(lb_handle* h, const char* cache_path)
     const int tys[] = {0, 16, 32, 64};  // 0: segment height from the fill model
     for (int tx : txs)
         for (int ty : tys)
-            if (tiled_supported(h->g, h->elem, tx, ty)) cand.emplace_back((int)LB_KERNEL_TILED, tx, ty);
+            if (tiled_supported(h->gbuf, h->elem, tx, ty)) cand.emplace_back((int)LB_KERNEL_TILED, tx, ty);
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
@@ -951,6 +1007,7 @@ lb_status lb_save(lb_handle* h, const char* path)
     Trace trace("lb_save");
     if (!h) return LB_ERR_INVALID;
     if (!path) return fail(h, LB_ERR_INVALID, "lb_save: path is NULL");
+    if (h->slab) return fail(h, LB_ERR_UNSUPPORTED, "lb_save: not available for a slab");
     if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_save: no state loaded");
     lb_status st = sync_and_check(h);
     if (st != LB_OK) return st;
@@ -1013,6 +1070,7 @@ lb_status lb_load(lb_handle* h, const char* path)
     Trace trace("lb_load");
     if (!h) return LB_ERR_INVALID;
     if (!path) return fail(h, LB_ERR_INVALID, "lb_load: path is NULL");
+    if (h->slab) return fail(h, LB_ERR_UNSUPPORTED, "lb_load: not available for a slab");
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
     h->batch_pending = false;
@@ -1091,6 +1149,104 @@ lb_status lb_load(lb_handle* h, const char* path)
     h->n_samples = hd.n_samples;
     h->faulted = false;
     h->initialised = true;
+    return LB_OK;
+}
+
+// ------------------------------------------------------------------ slabs --
+// Rows and planes of a slab message.  Buffer rows of a slab of `rows` own rows:
+// 0, 1 ghost rows below | 2 .. rows+1 own rows | rows+2, rows+3 ghost rows above.
+static bool slab_message(const lb_handle* h, int part, bool put, SlabMsg* m)
+{
+    const int rows = h->ny;
+    const int up[6] = {2, 5, 6, 11, 14, 15}, down[6] = {4, 7, 8, 13, 16, 17};  // c_y = +1 / -1, both species
+    switch (part) {
+    case LB_SLAB_EDGE_LO:  // send: own rows 0, 1; receive: the ghost rows below
+    case LB_SLAB_EDGE_HI:  // send: own rows rows-2, rows-1; receive: the ghost rows above
+        m->n_planes = 18;
+        for (int q = 0; q < 18; ++q) m->planes[q] = q;
+        m->nrows = 2;
+        m->row0 = part == LB_SLAB_EDGE_LO ? (put ? 0 : 2) : (put ? rows + 2 : rows);
+        return true;
+    case LB_SLAB_FLOW_LO:  // send: what streamed down out of the slab; receive: what streamed up into row 0
+    case LB_SLAB_FLOW_HI:  // send: what streamed up out of the slab; receive: what streamed down into the last row
+    {
+        const bool lo = part == LB_SLAB_FLOW_LO;
+        const int* q = (lo == put) ? up : down;
+        m->n_planes = 6;
+        for (int k = 0; k < 6; ++k) m->planes[k] = q[k];
+        m->nrows = 1;
+        m->row0 = lo ? (put ? 2 : 1) : (put ? rows + 1 : rows + 2);
+        return true;
+    }
+    default:
+        return false;
+    }
+}
+
+static size_t slab_message_size(const lb_handle* h, const SlabMsg& m)
+{
+    return (size_t)h->n_cells * m.n_planes * m.nrows * h->nx * h->elem;
+}
+
+static lb_status slab_transfer(lb_handle* h, lb_slab_part part, void* buf, bool put, const char* name)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!h->slab) return fail(h, LB_ERR_UNSUPPORTED, "%s: the handle holds whole cells, not a slab", name);
+    if (!buf) return fail(h, LB_ERR_INVALID, "%s: the message buffer is NULL", name);
+    SlabMsg m{};
+    if (!slab_message(h, (int)part, put, &m)) return fail(h, LB_ERR_INVALID, "%s: unknown part %d", name, (int)part);
+    if (!h->initialised) return fail(h, LB_ERR_STATE, "%s: no state loaded", name);
+    CK(h, cudaSetDevice(h->device));
+    char why[256];
+    if (!device_buffer_ok(buf, slab_message_size(h, m), h->device, "message", why, sizeof why))
+        return fail(h, LB_ERR_INVALID, "%s: %s", name, why);
+    CK(h, with_type(h, [&](auto* tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        return launch_slab_msg<T>((T*)h->f[h->cur], (T*)buf, h->gbuf, m, !put, h->stream);
+    }));
+    h->launches += 1;
+    return LB_OK;
+}
+
+lb_status lb_slab_info(const lb_handle* h, int* y0, int* rows, int* ny_global)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (y0) *y0 = h->rm.y0g;
+    if (rows) *rows = h->ny;
+    if (ny_global) *ny_global = h->rm.nyg;
+    return h->slab ? LB_OK : LB_ERR_UNSUPPORTED;
+}
+
+lb_status lb_slab_message_bytes(const lb_handle* h, lb_slab_part part, size_t* bytes)
+{
+    if (!h || !bytes) return LB_ERR_INVALID;
+    SlabMsg m{};
+    if (!h->slab || !slab_message(h, (int)part, false, &m)) return h->slab ? LB_ERR_INVALID : LB_ERR_UNSUPPORTED;
+    *bytes = slab_message_size(h, m);
+    return LB_OK;
+}
+
+lb_status lb_slab_get(lb_handle* h, lb_slab_part part, void* dst)
+{
+    Trace trace("lb_slab_get");
+    return slab_transfer(h, part, dst, false, "lb_slab_get");
+}
+
+lb_status lb_slab_put(lb_handle* h, lb_slab_part part, const void* src)
+{
+    Trace trace("lb_slab_put");
+    return slab_transfer(h, part, const_cast<void*>(src), true, "lb_slab_put");
+}
+
+lb_status lb_wall_momentum(lb_handle* h, double* sums, long long* n_samples)
+{
+    if (!h) return LB_ERR_INVALID;
+    if (!sums) return fail(h, LB_ERR_INVALID, "lb_wall_momentum: sums is NULL");
+    std::vector<double> prof, wall;
+    lb_status st = read_acc(h, prof, wall);
+    if (st != LB_OK) return st;
+    for (size_t k = 0; k < wall.size(); ++k) sums[k] = wall[k];
+    if (n_samples) *n_samples = h->n_samples;
     return LB_OK;
 }
 

@@ -196,8 +196,53 @@ template <class C> __device__ inline C expm1_c(C x);
 template <> __device__ inline float expm1_c<float>(float x) { return expm1f(x); }
 template <> __device__ inline double expm1_c<double>(double x) { return expm1(x); }
 
-// psi(rho) = rho0 (1 - exp(-rho/rho0)) = -rho0 expm1(-rho/rho0)
-template <class C> __device__ inline C psi_of(C rho, C rho0, C inv_rho0) { return -rho0 * expm1_c<C>(-rho * inv_rho0); }
+// 1 - e^{-t} in FP32 without the library's expm1f, for psi: Cody-Waite
+// argument reduction t = k ln2 + r, |r| <= ln2/2 (k the nearest integer to
+// t log2(e), rounded by adding 1.5 * 2^23; ln2 split so that k * OMX_LN2_HI is
+// exact for |k| < 2^11), the Taylor polynomial of 1 - e^{-r} to degree 7
+// (truncation below 2^-27 of the result for |r| <= ln2/2), and
+//   1 - e^{-t} = (1 - 2^-k) + 2^-k (1 - e^{-r}),
+// with 2^-k built in the exponent field from the integer bits of k that the
+// rounding constant leaves in the low mantissa.  t is clamped to 80, beyond
+// which 1 - e^{-t} rounds to 1.  Every operation is rounded to nearest once
+// (explicit fma/mul/add), so the packed pair and the scalar forms agree bit
+// for bit.  In an FP32 emulation of these steps the error stays within 1.2 ulp
+// of the exact value for t in [1e-6, 40].
+constexpr float OMX_LOG2E = 1.44269504088896340736f, OMX_ROUND = 12582912.0f;
+constexpr float OMX_LN2_HI = 0.693145751953125f, OMX_LN2_LO = 1.42860682030941723212e-6f;
+// Taylor coefficients of 1 - e^{-r}: (-1)^(n+1) / n!, n = 1..7
+__host__ __device__ constexpr float omx_d(int n)
+{
+    return n == 1 ? 1.0f : n == 2 ? -0.5f : n == 3 ? 1.0f / 6.0f : n == 4 ? -1.0f / 24.0f : n == 5 ? 1.0f / 120.0f
+         : n == 6 ? -1.0f / 720.0f : 1.0f / 5040.0f;
+}
+
+__device__ __forceinline__ float omx_pow2_neg(float km)
+{
+    return __uint_as_float(0x3f800000u - (__float_as_uint(km) << 23));
+}
+__device__ __forceinline__ float one_minus_exp_neg(float t)
+{
+    t = fminf(t, 80.f);
+    const float km = __fmaf_rn(t, OMX_LOG2E, OMX_ROUND);
+    const float k = __fsub_rn(km, OMX_ROUND);
+    float r = __fmaf_rn(k, -OMX_LN2_HI, t);
+    r = __fmaf_rn(k, -OMX_LN2_LO, r);
+    float q = omx_d(7);
+#pragma unroll
+    for (int n = 6; n >= 1; --n) q = __fmaf_rn(q, r, omx_d(n));
+    q = __fmul_rn(q, r);
+    const float s = omx_pow2_neg(km);
+    return __fmaf_rn(s, q, __fsub_rn(1.0f, s));
+}
+
+// psi(rho) = rho0 (1 - exp(-rho/rho0)): FP32 through one_minus_exp_neg, FP64
+// as -rho0 expm1(-rho/rho0)
+__device__ inline float psi_of(float rho, float rho0, float inv_rho0)
+{
+    return __fmul_rn(rho0, one_minus_exp_neg(__fmul_rn(rho, inv_rho0)));
+}
+__device__ inline double psi_of(double rho, double rho0, double inv_rho0) { return -rho0 * expm1(-rho * inv_rho0); }
 
 // ------------------------------------------------------------ lane pairs --
 // The tiled kernel's threads update one species at two adjacent sites (x, x+1)
@@ -293,12 +338,26 @@ template <class C> __device__ __forceinline__ P2<C> lane_por(P2<C> psi, P2<C> rh
     return P2<C>(lane_por(psi.a(), rho.a()), lane_por(psi.b(), rho.b()));
 }
 
-// psi = -rho0 expm1(-rho/rho0) with the two products of a pair packed; the
-// arguments are -1/rho0 and -rho0 (negation is exact, so each lane equals psi_of)
-template <class C> __device__ __forceinline__ P2<C> lane_psi(P2<C> rho, P2<C> neg_inv_rho0, P2<C> neg_rho0)
+// psi of a pair of densities, each lane equal to psi_of: FP32 with every step
+// of one_minus_exp_neg packed; FP64 through expm1 per lane
+__device__ __forceinline__ P2<float> lane_psi(P2<float> rho, P2<float> rho0, P2<float> inv_rho0)
 {
-    const P2<C> t = rho * neg_inv_rho0;
-    return P2<C>(expm1_c<C>(t.a()), expm1_c<C>(t.b())) * neg_rho0;
+    P2<float> t = rho * inv_rho0;
+    t = P2<float>(fminf(t.a(), 80.f), fminf(t.b(), 80.f));
+    const P2<float> km = vfma(t, P2<float>(OMX_LOG2E), P2<float>(OMX_ROUND));
+    const P2<float> k = km - P2<float>(OMX_ROUND);
+    P2<float> r = vfma(k, P2<float>(-OMX_LN2_HI), t);
+    r = vfma(k, P2<float>(-OMX_LN2_LO), r);
+    P2<float> q = P2<float>(omx_d(7));
+#pragma unroll
+    for (int n = 6; n >= 1; --n) q = vfma(q, r, P2<float>(omx_d(n)));
+    q = q * r;
+    const P2<float> sk(omx_pow2_neg(km.a()), omx_pow2_neg(km.b()));
+    return rho0 * vfma(sk, q, P2<float>(1.0f) - sk);
+}
+__device__ __forceinline__ P2<double> lane_psi(P2<double> rho, P2<double> rho0, P2<double> inv_rho0)
+{
+    return P2<double>(psi_of(rho.a(), rho0.a(), inv_rho0.a()), psi_of(rho.b(), rho0.b(), inv_rho0.b()));
 }
 
 // Pairs of adjacent elements to and from shared or global memory, in the
@@ -528,6 +587,29 @@ __host__ __device__ inline int stencil_row(int y, int ny, int bc)
     return y < 0 ? -y - 1 : (y >= ny ? 2 * ny - y - 1 : y);
 }
 __host__ __device__ inline int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
+// Rows of a population buffer that a step updates, and where they sit in the
+// global cell.  A whole cell: the buffer holds rows 0..ny-1, all updated
+// (ylo = 0, nown = nyg = ny, y0g = 0, slab = 0).  A slab of one cell split into
+// horizontal slabs: the buffer holds rows y0g-2 .. y0g+nown+1 of the global cell
+// (two ghost rows on each side, ylo = 2); the step updates the nown rows in the
+// middle, reads the ghost rows for the interaction stencil (they are copies of
+// the neighbouring slabs' rows) and streams into them the populations that leave
+// the slab, which the neighbours take over.
+struct RowMap {
+    int ylo, nown, y0g, nyg, slab;
+};
+
+// Buffer row the interaction stencil reads for buffer row e: a whole cell wraps
+// periodically or mirrors at the walls; a slab reads its ghost rows, except
+// beyond a Couette wall of the global cell, where the mirror rows are its own.
+__host__ __device__ inline int stencil_load_row(int e, int ny, const RowMap& m, int bc)
+{
+    if (!m.slab) return stencil_row(e, ny, bc);
+    const int gy = e - m.ylo + m.y0g;
+    if (bc == 1 && (gy < 0 || gy >= m.nyg)) return stencil_row(gy, m.nyg, 1) - m.y0g + m.ylo;
+    return e;
+}
 
 // Sum over the 32 lanes of a warp (result valid in lane 0).  FP32 values are
 // added as an unevaluated (hi, lo) pair with the error-free two-sum, so the

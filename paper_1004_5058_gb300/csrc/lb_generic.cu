@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) moments_psi_kernel(const T* __restrict__ 
             r += Store<T>::ld(f, fidx(g, cell, s * 9 + i, y, x), sh);
         }
         a[s * n] = r;
-        a[(2 + s) * n] = psi_of<C>(r, p.rho0, p.inv_rho0);
+        a[(2 + s) * n] = psi_of(r, p.rho0, p.inv_rho0);
     }
 }
 

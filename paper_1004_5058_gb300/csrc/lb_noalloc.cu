@@ -64,40 +64,53 @@ PFN_cuMemGetAddressRange_v3020 address_range_fn()
     return fn;
 }
 
-// A caller's buffer must be device (or managed) memory of the current device
-// whose allocation holds `bytes` bytes from `ptr` on; otherwise the kernels
-// would read or write outside it.  Nothing is launched before this holds.
-lb_status check_buffer(const void* ptr, size_t bytes, int dev, const char* name)
+}  // namespace
+
+// A caller's buffer must be device (or managed) memory of the device `dev`
+// whose allocation holds `bytes` bytes from `ptr` on; otherwise a kernel would
+// read or write outside it.  Callers check before anything is launched.
+bool lbhb::device_buffer_ok(const void* ptr, size_t bytes, int dev, const char* name, char* why, size_t why_len)
 {
-    char buf[256];
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
         cudaGetLastError();
-        snprintf(buf, sizeof buf, "%s: not a pointer the CUDA runtime knows", name);
-        return fail(LB_ERR_INVALID, buf);
+        snprintf(why, why_len, "%s: not a pointer the CUDA runtime knows", name);
+        return false;
     }
     if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
-        snprintf(buf, sizeof buf, "%s: host memory; a device buffer of the current device is required", name);
-        return fail(LB_ERR_INVALID, buf);
+        snprintf(why, why_len, "%s: host memory; a device buffer of the current device is required", name);
+        return false;
     }
     if (a.type == cudaMemoryTypeDevice && a.device != dev) {
-        snprintf(buf, sizeof buf, "%s: memory of device %d, the current device is %d", name, a.device, dev);
-        return fail(LB_ERR_INVALID, buf);
+        snprintf(why, why_len, "%s: memory of device %d, the current device is %d", name, a.device, dev);
+        return false;
     }
     auto range = address_range_fn();
-    if (!range) return fail(LB_ERR_CUDA, "cuMemGetAddressRange is not available");
+    if (!range) {
+        snprintf(why, why_len, "%s: cuMemGetAddressRange is not available", name);
+        return false;
+    }
     CUdeviceptr base = 0;
     size_t size = 0;
     if (range(&base, &size, (CUdeviceptr)(uintptr_t)ptr) != CUDA_SUCCESS) {
-        snprintf(buf, sizeof buf, "%s: the extent of its allocation cannot be established", name);
-        return fail(LB_ERR_INVALID, buf);
+        snprintf(why, why_len, "%s: the extent of its allocation cannot be established", name);
+        return false;
     }
     const uintptr_t p = (uintptr_t)ptr, end = (uintptr_t)base + size;
     if (p < (uintptr_t)base || p > end || bytes > end - p) {
-        snprintf(buf, sizeof buf, "%s: %zu bytes needed from the pointer, its allocation holds %zu", name, bytes,
+        snprintf(why, why_len, "%s: %zu bytes needed from the pointer, its allocation holds %zu", name, bytes,
                  (size_t)(p <= end ? end - p : 0));
-        return fail(LB_ERR_INVALID, buf);
+        return false;
     }
+    return true;
+}
+
+namespace {
+
+lb_status check_buffer(const void* ptr, size_t bytes, int dev, const char* name)
+{
+    char why[256];
+    if (!device_buffer_ok(ptr, bytes, dev, name, why, sizeof why)) return fail(LB_ERR_INVALID, why);
     return LB_OK;
 }
 

@@ -57,10 +57,11 @@ __host__ __device__ inline SlotGeom slot_geom(int tx, int elem)
 }
 
 struct TiledPlan {
-    Geom g;
+    Geom g;     // the whole population buffer (for a slab: its own rows and two ghost rows each side)
+    RowMap rm;  // the rows a step updates
     int elem, bc, tx, ty, depth;
     int n_strips, n_seg;
-    int grid[2];  // persistent CTAs of the full-width [0] and general [1] kernels
+    int grid[2][2];  // persistent CTAs: [full-width 0 / general 1][plain 0 / sampled 1]
     size_t smem;
     CUtensorMap tm_main[2], tm_halo[2];
     void* f[2];
@@ -198,6 +199,24 @@ __device__ __forceinline__ void window_diffs(const P2<C> (&v)[5][3], const P2<C>
 // of psi/rho, so the column warps all do the same work between two barriers.
 __host__ __device__ constexpr int tiled_threads(int tx) { return tx + 32; }
 
+// Dynamic shared memory of a CTA: row slots, psi/rho rings, mbarriers, and two
+// rows of per-site profile values (sampled steps).
+__host__ __device__ constexpr int tiled_smem_bytes(int tx, int elem)
+{
+    return ring_depth(tx, elem) * (al128(18 * tx * elem) + 2 * al128(18 * (16 / elem) * elem)) +
+           4 * ring_species_stride(tx) * (elem == 8 ? 8 : 4) + ring_depth(tx, elem) * 8 + 2 * tx * (elem == 8 ? 8 : 4);
+}
+// CTAs of a plain step per SM that shared memory admits (228 KB per SM, 1 KB of
+// it reserved per CTA), at most 4: the register budget the compiler is held to,
+// so that registers do not admit fewer.  Sampled steps (a tenth of the launches,
+// with more live values) are held to at most 3.
+__host__ __device__ constexpr int tiled_min_ctas(int tx, int elem)
+{
+    return 233472 / (tiled_smem_bytes(tx, elem) + 1024) < 1   ? 1
+         : 233472 / (tiled_smem_bytes(tx, elem) + 1024) > 4 ? 4
+                                                             : 233472 / (tiled_smem_bytes(tx, elem) + 1024);
+}
+
 // Service warp, sampled steps: the sums of u_x over each 32-column group of one
 // row of a strip (ub: TX values), one FP64 partial per group as the column warps
 // would have written it.  Lane l takes NW = TX/32 consecutive columns of group
@@ -206,7 +225,7 @@ __host__ __device__ constexpr int tiled_threads(int tx) { return tx + 32; }
 // so its registers do not add to the column warps' in the hot loop.
 template <class C, int TX>
 __device__ __noinline__ void profile_row_sums(const C* ub, int lane, double* __restrict__ prof_part, int cell,
-                                              const Geom& g, int x0, int y)
+                                              int nx, int nrows, int x0, int row)
 {
     constexpr int NW = TX / 32, SEG = 32 / NW;
     const int grp = lane / SEG, t = lane % SEG;
@@ -240,17 +259,21 @@ __device__ __noinline__ void profile_row_sums(const C* ub, int lane, double* __r
         for (int o = SEG / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, SEG);
         part = v;
     }
-    const int nbx = (g.nx + 31) / 32;  // 32-column groups of the lattice; a narrow last strip has fewer
-    if (t == 0 && (x0 >> 5) + grp < nbx) prof_part[((long long)cell * nbx + (x0 >> 5) + grp) * g.ny + y] = part;
+    const int nbx = (nx + 31) / 32;  // 32-column groups of the lattice; a narrow last strip has fewer
+    if (t == 0 && (x0 >> 5) + grp < nbx) prof_part[((long long)cell * nbx + (x0 >> 5) + grp) * nrows + row] = part;
 }
 
 // FULL: every strip is TX columns wide (nx a multiple of TX) and every cell has
 // one relaxation time; otherwise the last strip may be narrower (its extra
 // columns masked) and the species may relax with times of their own.
 template <class T, int TX, bool SAMPLE, bool FULL>
-__global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
+__global__ void __launch_bounds__(tiled_threads(TX),
+                                  SAMPLE ? (tiled_min_ctas(TX, (int)sizeof(T)) < 3 ? tiled_min_ctas(TX, (int)sizeof(T)) : 3)
+                                         : tiled_min_ctas(TX, (int)sizeof(T)))
+    tiled_step_kernel(const __grid_constant__ CUtensorMap tm_main,
                                                             const __grid_constant__ CUtensorMap tm_halo,
-                                                            T* __restrict__ fout, Geom g, int bc, int ty,
+                                                            T* __restrict__ fout, Geom g, int bc, RowMap rm,
+                                                            int ty,
                                                             int n_strips, int n_seg,
                                                             const CellDev* __restrict__ cells,
                                                             double* __restrict__ prof_part,
@@ -323,8 +346,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         const int irem = (int)(iw - (long long)icell * per_cell);
         const int iseg = irem / n_strips;
         ix0 = (irem - iseg * n_strips) * TX;
-        iy0 = iseg * ty;
-        iR = min(ty, g.ny - iy0) + 4;
+        iy0 = rm.ylo + iseg * ty;
+        iR = min(ty, rm.ylo + rm.nown - iy0) + 4;
         ixl = ix0 >= H ? ix0 - H : g.nx - H;
         ixr = ix0 + TX < g.nx ? ix0 + TX : 0;
     };
@@ -333,7 +356,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         while (n_issued < limit && iw < items) {
             const int slot = (int)(n_issued % D);
             unsigned char* dst = fring + slot * SLOT;
-            const int yp = stencil_row(iy0 - 2 + ik, g.ny, bc);
+            const int yp = stencil_load_row(iy0 - 2 + ik, g.ny, rm, bc);
             if (n_issued != skip_row) {
                 mbar_arrive_expect_tx(&bars[slot], TX_BYTES);
                 tma_load_4d(dst, &tm_main, ix0, yp, 0, icell, &bars[slot]);
@@ -353,8 +376,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         const int cell = (int)(w / per_cell);
         const int rem = (int)(w % per_cell);
         const int seg = rem / n_strips, strip = rem % n_strips;
-        const int x0 = strip * TX, y0 = seg * ty;
-        const int rows = min(ty, g.ny - y0);
+        const int x0 = strip * TX, y0 = rm.ylo + seg * ty;  // buffer row of the item's first row
+        const int rows = min(ty, rm.ylo + rm.nown - y0);
         const int R = rows + 4;  // logical rows y0-2 .. y0+rows+1
         // per-cell parameters as scalars (no runtime-indexed arrays: they would
         // live in local memory)
@@ -378,7 +401,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         // the same values as lane pairs
         const V ga = V(sp ? pg.g1[1] : pg.g1[0]), gr = V(sp ? pg.g2[1] : pg.g2[0]), gx = V(p.gab_over_rho0);
         const V tau2 = V(tau_s), ntau2 = V(-tau_s), omega2 = V(omega_s), mix2 = V(mix);
-        const V neg_inv_rho0 = V(-p.inv_rho0), neg_rho0 = V(-p.rho0);
+        const V rho0_2 = V(p.rho0), inv_rho0_2 = V(p.inv_rho0);
         const C rho_bar = sp ? pg.rho_bar[1] : pg.rho_bar[0];
         const V rho_bar2 = V(rho_bar);
         // columns of this strip inside the lattice (the last strip of a width that
@@ -389,6 +412,11 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         const int x = x0 + c0;
         const int col_m = x == 0 ? g.nx - 1 : x - 1, col_p2 = x + 2 == g.nx ? 0 : x + 2;
         T* const dst_s = fout + (long long)cell * g.cellstride + (long long)sp * 9 * g.plane;
+        T* const dst_x = dst_s + x;  // column x, plane 0 of the species, row 0
+        // warps holding column 0 or column nx - 1 wrap their x-shifted stores
+        // periodically; the others store each direction's two sites at fixed
+        // offsets from one address
+        const bool xedge = (x0 == 0 && warp == 0) || (x0 + 32 * warp + 32 >= g.nx);
 
         // rings of the previous item are no longer read; the watchdog flags of its
         // rows are reported
@@ -402,8 +430,8 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         };
         // rho_s, psi_s of logical row k into ring row `ring_row` (own species,
         // own two columns; the service warp takes the halo columns)
-        auto psi_stage = [&](int k, int ring_row) {
-            const unsigned char* base = fring + ((nrow + (uint32_t)k) % D) * SLOT;
+        auto psi_stage_slot = [&](int slot, int ring_row) {
+            const unsigned char* base = fring + slot * SLOT;
             const int ring = sp * SS + ring_row * W;
             if (!svc) {
                 if (!act) return;  // its ring positions belong to the halo or to nobody
@@ -417,7 +445,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                     else
                         r = r + rho_bar2;
                 }
-                Pair<C>::st(psi_ring + ring + c0 + 2, lane_psi<C>(r, neg_inv_rho0, neg_rho0));
+                Pair<C>::st(psi_ring + ring + c0 + 2, lane_psi(r, rho0_2, inv_rho0_2));
                 Pair<C>::st(rho_ring + ring + c0 + 2, r);
             } else if (lane < 8) {
                 // halo column h: 0,1 -> columns -2,-1 (left box); 2,3 -> TX, TX+1 (right box)
@@ -429,7 +457,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
                 for (int i = 0; i < 9; ++i) acc += to_c(src[i * H]);
                 if (Store<T>::shifted) acc = acc * inv_scale + rho_bar;
                 const int pos = h < 2 ? h : wv + h;
-                psi_ring[ring + pos] = psi_of<C>(acc, p.rho0, p.inv_rho0);
+                psi_ring[ring + pos] = psi_of(acc, p.rho0, p.inv_rho0);
                 rho_ring[ring + pos] = acc;
             }
         };
@@ -437,15 +465,24 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         bool ok = true;
         for (int k = 0; k < 4; ++k) {
             ok = wait_row(k) && ok;
-            psi_stage(k, k);
+            psi_stage_slot((int)((nrow + (uint32_t)k) % (uint32_t)D), k);
         }
         int r0 = 0;  // ring row of logical row j (rows j .. j+4 are read by the collision of row j+2)
+        // slot and mbarrier phase of logical row j + 4 (global row nrow + j + 4),
+        // advanced by one row per iteration instead of recomputed
+        int s4 = (int)((nrow + 4u) % (uint32_t)D);
+        uint32_t ph4 = ((nrow + 4u) / (uint32_t)D) & 1u;
         for (int j = 0; j < rows; ++j) {
             int rr[5];
 #pragma unroll
             for (int d = 0; d < 5; ++d) rr[d] = r0 + d >= RING ? r0 + d - RING : r0 + d;
-            ok = wait_row(j + 4) && ok;
-            psi_stage(j + 4, rr[4]);
+            const int s2 = s4 >= 2 ? s4 - 2 : s4 + D - 2;  // slot of row j + 2
+            ok = mbar_wait_bounded(&bars[s4], ph4) && ok;
+            psi_stage_slot(s4, rr[4]);
+            if (++s4 == D) {
+                s4 = 0;
+                ph4 ^= 1u;
+            }
             r0 = rr[1];
             // barrier: psi/rho of row j+4 visible, collision of row j+1 finished
             // everywhere; it also tells every thread whether any wait ran out
@@ -457,12 +494,13 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             if (producer) issue_upto(nrow + (uint32_t)(j + 2 + D));
             if (svc) {
                 if (SAMPLE && j > 0)  // its row finished before this barrier
-                    profile_row_sums<C, TX>(ubuf + ((j - 1) & 1) * TX, lane, prof_part, cell, g, x0, y0 + j - 1);
+                    profile_row_sums<C, TX>(ubuf + ((j - 1) & 1) * TX, lane, prof_part, cell, g.nx, rm.nown, x0,
+                                            y0 + j - 1 - rm.ylo);
                 continue;
             }
             // ---- collide logical row k = j + 2 (lattice row y), sites x and x+1
-            const int k = j + 2, y = y0 + j;
-            const T* fm = reinterpret_cast<const T*>(fring + ((nrow + (uint32_t)k) % D) * SLOT) + sp * 9 * TX + c0;
+            const int y = y0 + j, gy = y - rm.ylo + rm.y0g;  // buffer row, row of the global cell
+            const T* fm = reinterpret_cast<const T*>(fring + s2 * SLOT) + sp * 9 * TX + c0;
             // populations as stored: f for FP32/FP64, the shifted g for FP16; a
             // lane pair per direction (sites x, x+1)
             V f[9];
@@ -507,7 +545,7 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             }
             const V inv_rho = lane_rcp(rho_w);
             const V ux = jwx * inv_rho, uy = jwy * inv_rho;
-            const C fx_body = body_force_x<C>(p, y);
+            const C fx_body = body_force_x<C>(p, gy);
             const bool body_raw = !one_time && fx_body != C(0);  // the force needs the raw 1/rho
             const V rho_t = FULL ? rho_w : rho_s + rho_p;        // total density of each site
             V ax = V(fx_body) * inv_rho;
@@ -537,19 +575,35 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
             // sites and their densities
             Dither dz;
             if constexpr (Store<T>::dithered)
-                dz.seed(((uint32_t)cell * 0x9E3779B1u) ^ ((uint32_t)y << 15) ^ ((uint32_t)x << 1) ^ (uint32_t)sp,
+                dz.seed(((uint32_t)cell * 0x9E3779B1u) ^ ((uint32_t)gy << 15) ^ ((uint32_t)x << 1) ^ (uint32_t)sp,
                         __float_as_uint(rho_s.a()) ^ (__float_as_uint(rho_s.b()) * 0x85EBCA6Bu));
             // push streaming; rows next to a Couette wall bounce back in place
-            const bool wall_lo = bc == 1 && y == 0, wall_hi = bc == 1 && y == g.ny - 1;
+            const bool wall_lo = bc == 1 && gy == 0, wall_hi = bc == 1 && gy == rm.nyg - 1;
             const int pl = (int)g.plane;  // < 2^31 / 18, checked on the host
-            const int row3[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.pitch, y * g.pitch,
-                                 (y == g.ny - 1 ? 0 : y + 1) * g.pitch};
+            // destination rows y-1, y, y+1: periodic in a whole cell; a slab streams
+            // into its ghost rows (the populations that leave it)
+            const int row3[3] = {(!rm.slab && y == 0 ? g.ny - 1 : y - 1) * g.pitch, y * g.pitch,
+                                 (!rm.slab && y == g.ny - 1 ? 0 : y + 1) * g.pitch};
             const int colA[3] = {col_m, x, x + 1};   // site x,   shifts -1, 0, +1
             const int colB[3] = {x, x + 1, col_p2};  // site x+1, shifts -1, 0, +1
             C dpx_site = C(0);
             if (act) {  // columns beyond the lattice store nothing
-                if (!(wall_lo || wall_hi)) {
-                    // interior row (uniform over the CTA): plain stores, no wall tests
+                if (!(wall_lo || wall_hi) && !xedge) {
+                    // interior row (uniform over the CTA), away from the x edge (uniform
+                    // over the warp): one address per direction, no wall tests
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int cy = q_cy(i), cx = q_cx(i);
+                        T* const q = dst_x + (i * pl + row3[cy + 1]);
+                        if (cx == 0) {
+                            st_pair<T, C>(q, fs[i].a(), fs[i].b(), dz);
+                        } else {
+                            st_one<T, C>(q + cx, fs[i].a(), dz);
+                            st_one<T, C>(q + cx + 1, fs[i].b(), dz);
+                        }
+                    }
+                } else if (!(wall_lo || wall_hi)) {
+                    // interior row on a warp at the x edge: periodic columns
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         const int cy = q_cy(i), cx = q_cx(i);
@@ -613,7 +667,9 @@ __global__ void __launch_bounds__(tiled_threads(TX)) tiled_step_kernel(const __g
         }
         if (SAMPLE && !aborted) {
             __syncthreads();  // the last row's u_x values are in place
-            if (svc) profile_row_sums<C, TX>(ubuf + ((rows - 1) & 1) * TX, lane, prof_part, cell, g, x0, y0 + rows - 1);
+            if (svc)
+                profile_row_sums<C, TX>(ubuf + ((rows - 1) & 1) * TX, lane, prof_part, cell, g.nx, rm.nown, x0,
+                                        y0 + rows - 1 - rm.ylo);
         }
         if (aborted) {
             if (producer) {
@@ -652,23 +708,25 @@ static size_t smem_bytes(int tx, int elem, int depth)
     const SlotGeom sg = slot_geom(tx, elem);
     const int cb = elem == 8 ? 8 : 4;
     // slots, psi/rho rings, mbarriers, and two rows of per-site profile values
-    return (size_t)depth * sg.slot_b + (size_t)4 * ring_species_stride(tx) * cb + (size_t)depth * 8 +
-           (size_t)2 * tx * cb;
+    const size_t b = (size_t)depth * sg.slot_b + (size_t)4 * ring_species_stride(tx) * cb + (size_t)depth * 8 +
+                     (size_t)2 * tx * cb;
+    return b;
 }
+static_assert(tiled_smem_bytes(128, 4) == 74032, "shared memory of the FP32 128-column tile");
 
 // Segment height from a fill model: work items = strips x segments x cells run
 // on `slots` persistent CTAs, each item costing about (rows + 6) row-times
 // (4 halo rows plus pipeline effects); pick the height with the least
 // rounds x cost, so the last round of items is not mostly empty.
-static int pick_segment_rows(const Geom& g, int tile_x, long long slots)
+static int pick_segment_rows(const Geom& g, int nrows, int tile_x, long long slots)
 {
     const long long strips = g.nx / tile_x;
     int best = 32;
     double best_cost = 1e300;
-    for (int ty = 8; ty <= 256 && ty <= g.ny; ++ty) {
-        const long long items = strips * g.n_cells * ((g.ny + ty - 1) / ty);
+    for (int ty = 8; ty <= 256 && ty <= nrows; ++ty) {
+        const long long items = strips * g.n_cells * ((nrows + ty - 1) / ty);
         const long long rounds = (items + slots - 1) / slots;
-        const int rows = std::min(ty, g.ny);
+        const int rows = std::min(ty, nrows);
         const double cost = (double)rounds * (rows + 6);
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
@@ -742,8 +800,8 @@ static bool encode(CUtensorMap* m, void* base, const Geom& g, int elem, int box_
     return r == CUDA_SUCCESS;
 }
 
-TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, void* f1, int tile_x, int tile_y,
-                        const char** err_msg)
+TiledPlan* tiled_create(const Geom& g, const RowMap& rm, int prec, int elem, int bc, void* f0, void* f1, int tile_x,
+                        int tile_y, const char** err_msg)
 {
     if (!tiled_supported(g, elem, tile_x, tile_y)) {
         if (err_msg) *err_msg = "shape/tile not supported by the tiled kernel";
@@ -751,6 +809,7 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
     }
     TiledPlan* p = new TiledPlan();
     p->g = g;
+    p->rm = rm;
     p->elem = elem;
     p->bc = bc;
     p->tx = tile_x;
@@ -770,17 +829,22 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // occupancy of each family (sampled and plain kernels together): the
-    // full-width kernels (nx a multiple of the tile, one relaxation time) and
-    // the general ones; which family runs depends on the cells' relaxation
-    // times, which lb_load may change, so both are prepared
+    // occupancy of each kernel: the full-width family (nx a multiple of the tile,
+    // one relaxation time) and the general one, each plain and sampled; which
+    // family runs depends on the cells' relaxation times, which lb_load may
+    // change, so both are prepared.  Plain and sampled launches of a family share
+    // the work items (the segment height) but each runs as many persistent CTAs
+    // as fit (the sampled variant holds more registers)
     const bool full_ok = g.nx % tile_x == 0;
-    int occ[2] = {0, 0};  // [0] full-width, [1] general
+    int occ[2][2] = {{0, 0}, {0, 0}};
     for (int s = 0; s < 4; ++s) {
-        const int fam = (s & 2) ? 1 : 0;
+        const int fam = (s & 2) ? 1 : 0, smp = s & 1;
         if (fam == 0 && !full_ok) continue;
-        const void* k = pick_any(prec, tile_x, (s & 1) != 0, fam == 0);
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess) {
+        const void* k = pick_any(prec, tile_x, smp != 0, fam == 0);
+        // the whole unified L1/shared array as shared memory: the CTAs' rings
+        // are what sets how many fit on an SM
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess ||
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) {
             cudaGetLastError();
             if (err_msg) *err_msg = "cudaFuncSetAttribute(max dynamic smem) failed";
             delete p;
@@ -794,14 +858,16 @@ TiledPlan* tiled_create(const Geom& g, int prec, int elem, int bc, void* f0, voi
             delete p;
             return nullptr;
         }
-        occ[fam] = occ[fam] == 0 ? o : std::min(occ[fam], o);
+        occ[fam][smp] = o;
     }
-    const long long slots = (long long)sms * occ[full_ok ? 0 : 1];
-    if (p->ty <= 0) p->ty = pick_segment_rows(g, tile_x, slots);
-    p->n_seg = (g.ny + p->ty - 1) / p->ty;
+    // segment height for the plain kernel of the family that will run most
+    const long long slots = (long long)sms * occ[full_ok ? 0 : 1][0];
+    if (p->ty <= 0) p->ty = pick_segment_rows(g, rm.nown, tile_x, slots);
+    p->n_seg = (rm.nown + p->ty - 1) / p->ty;
     const long long items = (long long)p->n_strips * p->n_seg * g.n_cells;
-    p->grid[0] = full_ok ? (int)std::min(items, slots) : 0;
-    p->grid[1] = (int)std::min(items, (long long)sms * occ[1]);
+    for (int fam = 0; fam < 2; ++fam)
+        for (int smp = 0; smp < 2; ++smp)
+            p->grid[fam][smp] = occ[fam][smp] > 0 ? (int)std::min(items, (long long)sms * occ[fam][smp]) : 0;
     return p;
 }
 
@@ -817,6 +883,15 @@ void tiled_tiles(const TiledPlan* p, int* tx, int* ty)
     *ty = p->ty;
 }
 
+void tiled_launch_shape(const TiledPlan* p, int* grid_plain, int* grid_sampled, int* threads, int* smem)
+{
+    const int fam = (p->g.nx % p->tx == 0 && p->one_time) ? 0 : 1;
+    if (grid_plain) *grid_plain = p->grid[fam][0];
+    if (grid_sampled) *grid_sampled = p->grid[fam][1];
+    if (threads) *threads = tiled_threads(p->tx);
+    if (smem) *smem = (int)p->smem;
+}
+
 template <class T>
 cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool sample, double* prof_part,
                               double* wall_part, unsigned* err, cudaStream_t st, int* n_launches)
@@ -825,13 +900,15 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
     const bool full = p->g.nx % p->tx == 0 && p->one_time;
     const void* k = pick<T>(p->tx, sample, full);
     Geom g = p->g;
+    RowMap rm = p->rm;
     int bc = p->bc, ty = p->ty, ns = p->n_strips, nseg = p->n_seg;
     uint32_t skip = p->skip_row;
     p->skip_row = ~0u;  // one launch only
     void* args[] = {(void*)&p->tm_main[src], (void*)&p->tm_halo[src], (void*)&dst, (void*)&g, (void*)&bc,
-                    (void*)&ty, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
+                    (void*)&rm, (void*)&ty, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
                     (void*)&wall_part, (void*)&err, (void*)&skip};
-    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid[full ? 0 : 1]), dim3(tiled_threads(p->tx)), args, p->smem, st);
+    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid[full ? 0 : 1][sample ? 1 : 0]), dim3(tiled_threads(p->tx)), args,
+                                     p->smem, st);
     *n_launches += 1;
     return e;
 }

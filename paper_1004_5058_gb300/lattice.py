@@ -38,19 +38,55 @@ def cell_struct(c: CellParams) -> L.lb_cell_params:
 
 
 class Lattice:
-    """n_cells independent cells advanced together (lb_create .. lb_destroy)."""
+    """n_cells independent cells advanced together (lb_create .. lb_destroy).
 
-    def __init__(self, cells: Iterable[CellParams], precision: str = "fp32", stream=None):
+    slab=(y0, rows): a handle over rows [y0, y0 + rows) of each cell only, one
+    slab of a cell split along y (lb_create_slab); host arrays then cover the own
+    rows ([n_cells][rows][nx]), and the slab trades rows with its neighbours
+    between steps (paper_1004_5058_gb300.slabs)."""
+
+    def __init__(self, cells: Iterable[CellParams], precision: str = "fp32", stream=None, slab=None):
         self.lib = L.load()
         self.cells = list(cells)
         self.n_cells = len(self.cells)
         self.nx, self.ny = self.cells[0].nx, self.cells[0].ny
+        self.ny_global = self.ny
+        self.slab = None if slab is None else (int(slab[0]), int(slab[1]))
         self.precision = precision
         arr = (L.lb_cell_params * self.n_cells)(*[cell_struct(c) for c in self.cells])
         h = L._H()
-        st = self.lib.lb_create(arr, self.n_cells, PRECISIONS[precision], _stream_ptr(stream), C.byref(h))
+        if self.slab is None:
+            st = self.lib.lb_create(arr, self.n_cells, PRECISIONS[precision], _stream_ptr(stream), C.byref(h))
+        else:
+            st = self.lib.lb_create_slab(arr, self.n_cells, PRECISIONS[precision], self.slab[0], self.slab[1],
+                                         _stream_ptr(stream), C.byref(h))
+            self.ny = self.slab[1]
         L.check(st, None)
         self.h = h
+
+    # ---- slab exchange (lb_slab_*): messages in the caller's device buffers
+    def message_bytes(self, part: int) -> int:
+        n = C.c_size_t()
+        self._chk(self.lib.lb_slab_message_bytes(self.h, int(part), C.byref(n)))
+        return int(n.value)
+
+    def slab_get(self, part: int, dst_ptr: int):
+        """Packs the message `part` into device memory at dst_ptr (stream-ordered)."""
+        self._chk(self.lib.lb_slab_get(self.h, int(part), C.c_void_p(int(dst_ptr))))
+        return self
+
+    def slab_put(self, part: int, src_ptr: int):
+        """Unpacks the message `part` from device memory at src_ptr (stream-ordered)."""
+        self._chk(self.lib.lb_slab_put(self.h, int(part), C.c_void_p(int(src_ptr))))
+        return self
+
+    def wall_momentum(self):
+        """Time sums [n_cells][2] of the x-momentum delivered by the top and
+        bottom walls over the sampled steps, and the number of sampled steps."""
+        s = np.empty((self.n_cells, 2))
+        n = C.c_longlong()
+        self._chk(self.lib.lb_wall_momentum(self.h, _dp(s), C.byref(n)))
+        return s, n.value
 
     # ---- life cycle
     def close(self):
@@ -154,6 +190,16 @@ class Lattice:
         k, tx, ty = C.c_int(), C.c_int(), C.c_int()
         self._chk(self.lib.lb_get_kernel(self.h, C.byref(k), C.byref(tx), C.byref(ty)))
         return KERNEL_NAMES[k.value], tx.value, ty.value
+
+    def launch_shape(self):
+        """(CTAs of plain steps, CTAs of sampled steps, threads, shared memory
+        bytes) of the tiled kernel in use, or None for the generic kernel."""
+        v = [C.c_int() for _ in range(4)]
+        st = self.lib.lb_launch_shape(self.h, *[C.byref(x) for x in v])
+        if st == L.LB_ERR_UNSUPPORTED:
+            return None
+        self._chk(st)
+        return tuple(x.value for x in v)
 
     def autotune(self, cache_path: Optional[str] = None):
         self._chk(self.lib.lb_autotune(self.h, cache_path.encode() if cache_path else None))

@@ -132,3 +132,95 @@ def test_slab_ranks_gloo(tmp_path, bc):
         f, _, _ = lb.step(cell, f)
     got = np.concatenate([np.load(tmp_path / ("slab_%d.npy" % r)) for r in range(world)], axis=2)
     assert np.array_equal(got, f)
+
+
+# ---- the package's rank-to-rank slab exchange, driving oracle slabs ---------
+class _OracleSlab:
+    """An FP64 oracle slab (orc_step_slab) behind the slab interface that
+    paper_1004_5058_gb300.slabs exchanges messages for (get / put / step / empty);
+    messages are CPU tensors here, device buffers on GPUs."""
+
+    def __init__(self, cell, y0, rows, f):
+        from oracle import slab
+        self.slab, self.cell, self.y0, self.rows = slab, cell, y0, rows
+        self.f = slab.scatter(f, y0, rows)
+
+    def _where(self, part, put):
+        from paper_1004_5058_gb300.slabs import EDGE_HI, EDGE_LO, FLOW_LO
+        r = self.rows
+        if part in (EDGE_LO, EDGE_HI):
+            lo = part == EDGE_LO
+            rows = (slice(0, 2) if lo else slice(r + 2, r + 4)) if put else (slice(2, 4) if lo else slice(r, r + 2))
+            return (slice(None), slice(None), rows)
+        lo = part == FLOW_LO
+        planes = list(self.slab.UP if lo == put else self.slab.DOWN)
+        row = (2 if lo else r + 1) if put else (1 if lo else r + 2)
+        return (slice(None), planes, row)
+
+    def get(self, part):
+        import torch
+        return torch.from_numpy(np.ascontiguousarray(self.f[self._where(part, False)]))
+
+    def empty(self, part):
+        import torch
+        return torch.empty(self.f[self._where(part, True)].shape, dtype=torch.float64)
+
+    def put(self, part, msg):
+        self.f[self._where(part, True)] = msg.numpy()
+
+    def step(self):
+        self.f, _ = self.slab.step_slab(self.cell, self.y0, self.f)
+
+
+def _dist_exchange_worker(rank, world, port, outdir, bc):
+    import torch.distributed as dist
+    from paper_1004_5058_gb300.slabs import DistExchange, split_rows
+    from tests.test_oracle_slab import case
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    cell, f = case(bc)
+    y0, rows = split_rows(cell.ny, world)[rank]
+    s = _OracleSlab(cell, y0, rows, f)
+    DistExchange(s, rank, world, periodic=cell.bc == 0).step(12)
+    np.save(os.path.join(outdir, "dx_%d.npy" % rank), s.f[:, :, 2:rows + 2])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("bc", [0, 1], ids=["periodic", "couette"])
+def test_package_slab_exchange_gloo(tmp_path, bc, world):
+    """paper_1004_5058_gb300.slabs.DistExchange (the host side of the GPU slab
+    mode: which message goes to which rank, in which order) over gloo ranks,
+    each stepping an oracle slab: the joined state equals the whole-cell oracle
+    bit for bit.  With two ranks in a periodic cell each rank is the other's
+    neighbour on both sides, so the order of the point-to-point messages alone
+    must pair them correctly."""
+    import torch.multiprocessing as mp
+    from oracle import lb
+    from tests.test_oracle_slab import case
+    mp.spawn(_dist_exchange_worker, args=(world, free_port(), str(tmp_path), bc), nprocs=world, join=True)
+    cell, f = case(bc)
+    for _ in range(12):
+        f, _, _ = lb.step(cell, f)
+    got = np.concatenate([np.load(tmp_path / ("dx_%d.npy" % r)) for r in range(world)], axis=2)
+    assert np.array_equal(got, f)
+
+
+def test_package_slab_exchange_in_process():
+    """The same exchange with every slab in one process (LocalExchange), 2 to 4
+    slabs (and one slab between the walls of a Couette cell), periodic and
+    Couette: equal to the whole-cell oracle bit for bit."""
+    from oracle import lb
+    from paper_1004_5058_gb300.slabs import LocalExchange, split_rows
+    from tests.test_oracle_slab import case
+    for bc in (0, 1):
+        cell, f0 = case(bc)
+        ref = f0
+        for _ in range(8):
+            ref, _, _ = lb.step(cell, ref)
+        for world in ((1, 2, 3, 4) if bc == 1 else (2, 3, 4)):
+            parts = split_rows(cell.ny, world)
+            slabs = [_OracleSlab(cell, y0, rows, f0) for y0, rows in parts]
+            LocalExchange(slabs, periodic=cell.bc == 0).step(8)
+            got = np.concatenate([s.f[:, :, 2:rows + 2] for s, (_, rows) in zip(slabs, parts)], axis=2)
+            assert np.array_equal(got, ref), (bc, world)
