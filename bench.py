@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--tile", default="", help="TXxTY for the tiled kernel (default: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bvp-steps", type=int, default=2000,
+                    help="time steps of the batched-vs-plain flow-curve leg (64 cells of 512^2); 0 skips it")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="only time the FP64 oracle on this host: 1 thread and all cores, at the parity (64^2), "
                          "bench (1024^2) and precision-study (4096^2) cell sizes; one JSON line, no GPU")
@@ -279,7 +281,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
         "warmup": W, "ms_per_step": 1e3 * tot_t / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args),
+        "config": dict(workload_config(args),
+                       timed="the FP64 oracle on the host cores: 1 cell of %dx%d (Couette U=%.3g) of this workload, "
+                             "FP64" % (args.nx, args.ny, cell.u_wall),
+                       timed_cells=1, timed_precision="fp64", timed_impl="oracle (CPU)"),
         "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
                          "sample": "1 cell of %dx%d, %d FP64 time steps in %.1f s over %d timed steps" %
                                    (args.nx, args.ny, tot_n, tot_t, K)},
@@ -287,6 +292,87 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_vs_plain(args, torch, Lattice, hb_fit):
+    """The batched flow-curve sweep against the plain single-cell runs, on the
+    64-cell shape of the batched flow curve: 64 Couette cells of 512 x 512 (16
+    wall speeds 1e-5 .. 1e-2 log-spaced x G_AB in {0.3, 0.35, 0.405, 0.45}), FP32
+    (or the bench's FP16 storage), a bounded number of steps with the second
+    half sampled.  Batched: one handle, tiles from the autotuner, graph-captured
+    chunks of one persistent launch per step.  Plain: the same cells one after
+    another, a handle each with the library's default tile, as a caller stepping
+    one cell at a time would run them.  Each side is timed from the state upload
+    (lb_init_fields) to the read-back of sigma and S (handle creation and
+    autotuning excluded): device time of the steps (CUDA events) and wall time of
+    the whole sweep; points/s = flow-curve points (cells) per wall second at this
+    step count.  sigma_max_rel_diff: the largest relative difference of the
+    cells' sigma_xy between the two (both are parity-checked against the FP64
+    oracle in the tests)."""
+    from paper_1004_5058_gb300 import inputs as I
+    L, steps, every = 512, args.bvp_steps, 20
+    speeds = I.log_spaced(1e-5, 1e-2, 16)
+    g_abs = (0.3, 0.35, 0.405, 0.45)
+    cells = [I.make_cell("paper", nx=L, ny=L, g_ab=g, bc=1, u_wall=u) for g in g_abs for u in speeds]
+    n = len(cells)
+    ra, rb = I.random_fields(L, L, n_cells=n, seed=2010)
+    ux, uy = I.couette_velocity(L, L, [c.u_wall for c in cells], n_cells=n)
+
+    def sweep(lat, sl):
+        st = torch.cuda.ExternalStream(lat.stream_ptr)
+        lat.init_fields(ra[sl], rb[sl], ux[sl], uy[sl]).set_sampling(steps // 2, every)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        lat.step(steps)
+        b.record(st)
+        sig, S, _ = lat.shear_stress()
+        return sig, S, a.elapsed_time(b) * 1e-3
+
+    cache_dir = os.path.join(ROOT, "paper_1004_5058_gb300", "_build")
+    cache = os.path.join(cache_dir, "autotune_cache.txt") if os.path.isdir(cache_dir) else None
+    with Lattice(cells, args.precision) as lat:
+        lat.init_fields(ra, rb, ux, uy)
+        lat.autotune(cache)
+        kern_b = lat.kernel()
+        sweep(lat, slice(0, n))  # the graphs of this step pattern, untimed
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sig_b, S_b, dev_b = sweep(lat, slice(0, n))
+        wall_b = time.perf_counter() - t0
+    lats = [Lattice([c], args.precision) for c in cells]
+    try:
+        kern_p = lats[0].kernel()
+        sig_p, S_p, dev_p = np.empty(n), np.empty(n), 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, lp in enumerate(lats):
+            s_, r_, d_ = sweep(lp, slice(c, c + 1))
+            sig_p[c], S_p[c], dev_p = s_[0], r_[0], dev_p + d_
+        wall_p = time.perf_counter() - t0
+    finally:
+        for lp in lats:
+            lp.close()
+    sites = n * L * L
+    rel = np.abs(sig_b - sig_p) / np.maximum(np.abs(sig_p), 1e-300)
+    fits = {}
+    for k, g in enumerate(g_abs):
+        sl = slice(16 * k, 16 * (k + 1))
+        ok = np.isfinite(S_b[sl]) & (S_b[sl] > 0) & np.isfinite(sig_b[sl])
+        fits[str(g)] = hb_fit(S_b[sl][ok], sig_b[sl][ok]) if ok.sum() >= 3 else None
+    return {
+        "workload": "64 Couette cells of 512x512: 16 wall speeds 1e-5..1e-2 x G_AB {0.3,0.35,0.405,0.45}, "
+                    "%s, %d time steps, second half sampled every %d" % (args.precision.upper(), steps, every),
+        "cells": n, "steps": steps,
+        "batched": {"mlups": sites * steps / dev_b / 1e6, "wall_s": wall_b, "points_per_s": n / wall_b,
+                    "kernel": list(kern_b)},
+        "plain": {"mlups": sites * steps / dev_p / 1e6, "wall_s": wall_p, "points_per_s": n / wall_p,
+                  "kernel": list(kern_p)},
+        "speedup_wall": wall_p / wall_b, "speedup_device": dev_p / dev_b,
+        "sigma_max_rel_diff": float(np.max(rel)), "sigma_bitwise_equal": bool(np.array_equal(sig_b, sig_p)),
+        "hb_fit_batched": fits,
+        "_wall_batched": wall_b,
+    }
 
 
 def run_ours(args):
@@ -317,6 +403,8 @@ def run_ours(args):
         cache_dir = os.path.join(ROOT, "paper_1004_5058_gb300", "_build")  # the library's build folder
         lat.autotune(os.path.join(cache_dir, "autotune_cache.txt") if os.path.isdir(cache_dir) else None)
     kernel, tx, ty = lat.kernel()
+    shape = lat.launch_shape()
+    launch_shape = None if shape is None else dict(zip(("ctas", "ctas_sampled", "threads", "smem_bytes"), shape))
     stream = torch.cuda.ExternalStream(lat.stream_ptr)
     lat.set_sampling(0, args.every)
 
@@ -351,20 +439,32 @@ def run_ours(args):
     value = sites * chunk * args.steps * world / (ms * 1e-3) / 1e6
     sigma, S, Sb = lat.shear_stress()
 
-    # roofline: fused kernel alone (sampling off), CUDA events on the same stream
+    # roofline: fused kernel alone (sampling off), CUDA events on the same stream;
+    # the same number of steps is run once untimed first, so the CUDA graphs of
+    # the timed call exist already (capture is host work that would idle the GPU)
+    def timed_steps(n):
+        lat.step(n)
+        lat.sync()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        l0 = lat.kernel_launches
+        a.record(stream)
+        lat.step(n)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) * 1e-3 / n, (lat.kernel_launches - l0) / n
+
     lat.set_sampling(0, 0)
     n_roof = max(50, min(400, int(2e9 / (sites * BYTES_PER_SITE[args.precision]) * 20)))
-    lat.step(20)
-    lat.sync()
-    r0 = torch.cuda.Event(enable_timing=True)
-    r1 = torch.cuda.Event(enable_timing=True)
-    l0 = lat.kernel_launches
-    r0.record(stream)
-    lat.step(n_roof)
-    r1.record(stream)
-    r1.synchronize()
-    kernels_per_step = (lat.kernel_launches - l0) / n_roof
-    t_launch = r0.elapsed_time(r1) * 1e-3 / n_roof / kernels_per_step
+    t_plain, kernels_per_step = timed_steps(n_roof)
+    t_launch = t_plain / kernels_per_step
+    # sampled steps alone (every step sampled: the SAMPLE variant of the fused
+    # kernel plus the FP64 accumulation of its partial sums)
+    lat.set_sampling(0, 1)
+    n_samp = max(20, n_roof // 4)
+    t_sampled, launches_sampled = timed_steps(n_samp)
+    n_sampled_per_step = chunk // args.every if args.every > 0 else 0
+    predicted_ms = 1e3 * ((chunk - n_sampled_per_step) * t_plain + n_sampled_per_step * t_sampled)
     alg_bytes = BYTES_PER_SITE[args.precision] * sites
     peak, peak_kind = peaks()
     achieved = alg_bytes / (t_launch if kernels_per_step == 1 else t_launch * kernels_per_step) / 1e9
@@ -375,7 +475,11 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "%s copy bandwidth" % peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": t_launch * 1e3,
-                "bytes_per_site_update": BYTES_PER_SITE[args.precision]}
+                "bytes_per_site_update": BYTES_PER_SITE[args.precision],
+                "launches_timed": n_roof,
+                # the timed region reconciled from separately timed plain and sampled steps
+                "sampled_step_ms": t_sampled * 1e3, "sampled_step_launches": launches_sampled,
+                "predicted_ms_per_step": predicted_ms, "measured_ms_per_step": ms / args.steps}
     if args.precision == "fp64":
         gops = FP64_OPS_PER_SITE * sites / t_launch / 1e9
         sm_mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
@@ -419,20 +523,23 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "fp16sr": "f16-storage/f32",
                                        "fp64": "f64"}[args.precision],
         "data": "synthetic",
-        "config": dict(workload_config(args), kernel=kernel, tile=[tx, ty]),
+        "config": dict(workload_config(args), kernel=kernel, tile=[tx, ty], launch=launch_shape),
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lattice_steps_per_step": chunk},
-        # one flow-curve point = one Couette cell run for 2e5 time steps (the protocol of this
-        # workload), at the measured site-update rate
-        "flow_curve_points_per_s": value * 1e6 / (nx * ny * 2e5),
         "gpu_launches": int(launches),
         "clocks": clk,
         "flow_curve": {"sigma_xy": [float(v) for v in sigma], "shear_rate": [float(v) for v in S]},
     }
+    lat.close()
+    if args.bvp_steps > 0 and args.precision in ("fp32", "fp16", "fp16sr") and args.tau_b == 0.0:
+        bvp = batched_vs_plain(args, torch, Lattice, hb_fit)
+        bvp_s = max_over_ranks(bvp.pop("_wall_batched"), device="cuda")
+        bvp["batched"]["points_per_s_all_ranks"] = bvp["cells"] * world / bvp_s
+        line["batched_vs_plain"] = bvp
+        line["flow_curve_points_per_s"] = bvp["batched"]["points_per_s_all_ranks"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
-    lat.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -30,6 +30,9 @@ def test_reference_arm_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["config"]["workload"].startswith("couette batch: 2 cells of 64x64")
+    # the line says what the reference arm actually times: one cell, FP64, the oracle
+    assert d["config"]["timed_cells"] == 1 and d["config"]["timed_precision"] == "fp64"
+    assert "oracle" in d["config"]["timed"]
 
 
 def test_reference_arm_two_relaxation_times():
@@ -61,7 +64,7 @@ def test_reference_arm_under_torchrun_prints_once():
 @pytest.mark.gpu
 def test_gpu_arm_line():
     d = run_bench("--steps", "3", "--warmup", "3", "--nx", "256", "--ny", "256", "--cells", "2", "--chunk", "20",
-                  "--cpu-seconds", "0.5")
+                  "--cpu-seconds", "0.5", "--bvp-steps", "200")
     assert BASE_KEYS <= set(d) and "impl" not in d
     assert d["value"] > 0 and d["n_gpus"] == 1 and d["dtype"] == "f32" and d["data"] == "synthetic"
     rf = d["roofline"]
@@ -72,6 +75,14 @@ def test_gpu_arm_line():
     assert d["gpu_launches"] >= 3 * 20
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert set(d["clocks"] or {}) >= {"sm_mhz", "sm_max_mhz", "reasons"} or d["clocks"] is None
+    # plain and sampled steps timed apart, and the timed region predicted from them
+    assert rf["sampled_step_ms"] > 0 and rf["predicted_ms_per_step"] > 0 and rf["measured_ms_per_step"] > 0
+    # the batched flow-curve sweep against the same cells run one at a time
+    bvp = d["batched_vs_plain"]
+    assert bvp["cells"] == 64 and bvp["steps"] == 200
+    assert bvp["batched"]["points_per_s"] > 0 and bvp["plain"]["points_per_s"] > 0
+    assert bvp["sigma_max_rel_diff"] <= 1e-5  # same kernels: equal to rounding (bitwise when tiles agree)
+    assert d["flow_curve_points_per_s"] == bvp["batched"]["points_per_s_all_ranks"]
 
 
 def test_traffic_record_matches_the_kernel_sources():
