@@ -40,12 +40,13 @@ UNIT = "MLUPS"
 BYTES_PER_SITE = {"fp32": 144, "fp16": 72, "fp16sr": 72, "fp64": 288}
 FALLBACK_HBM_GBS = 6800.0
 # The FP64 step is bound by the FP64 pipe, not by HBM: its roofline counts the
-# FP64 pipe operations one site update issues (ncu counts of the fused kernel
-# at tau = 1, the workload's: dadd 124, dmul 60, dfma 126 per site; each occupies
-# the pipe once) against the pipe's rate, 152 SMs x 2 FP64 operations per clock
-# (the nominal 1.25 TFLOP/s of FMA at the 2070 MHz maximum SM clock), at the SM
-# clock sampled in the run.
-FP64_OPS_PER_SITE = 124 + 60 + 126
+# FP64 pipe operations one site update issues (ncu counts of the fused tiled
+# kernel at tau = 1, the workload's: dfma 124, dadd 122, dmul 60 per site; each
+# occupies the pipe once) against the pipe's rate, 152 SMs x 2 FP64 operations
+# per clock (the nominal 1.25 TFLOP/s of FMA at the 2070 MHz maximum SM clock),
+# at the SM clock sampled in the run.  The count is the tiled kernel's; for the
+# generic kernel pair the line reports no FP64 roofline.
+FP64_OPS_PER_SITE = 124 + 122 + 60
 FP64_OPS_PER_CLOCK, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 
 
@@ -481,10 +482,11 @@ def run_ours(args):
                 "sampled_step_ms": t_sampled * 1e3, "sampled_step_launches": launches_sampled,
                 "predicted_ms_per_step": predicted_ms, "measured_ms_per_step": ms / args.steps}
     if args.precision == "fp64":
-        gops = FP64_OPS_PER_SITE * sites / t_launch / 1e9
         sm_mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
         p64 = N_SM * FP64_OPS_PER_CLOCK * sm_mhz * 1e-3
-        roofline = {"bound": "alu", "achieved": gops, "peak": p64, "unit": "G FP64 op/s", "frac": gops / p64,
+        gops = FP64_OPS_PER_SITE * sites / t_plain / 1e9 if kernel == "tiled" else None
+        roofline = {"bound": "alu", "achieved": gops, "peak": p64, "unit": "G FP64 op/s",
+                    "frac": None if gops is None else gops / p64, "kernel": kernel,
                     "traffic": traffic,
                     "peak_source": "FP64 pipe: 152 SMs x 2 ops per clock at the sampled SM clock (%.0f MHz)" % sm_mhz,
                     "fp64_ops_per_site_update": FP64_OPS_PER_SITE, "mean_launch_ms": t_launch * 1e3,

@@ -321,6 +321,10 @@ __device__ __forceinline__ P2<double> vfma(P2<double> a, P2<double> b, P2<double
 {
     return P2<double>(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
 }
+// scalar type of a lane value
+template <class V> struct LaneScalar { using type = V; };
+template <class C> struct LaneScalar<P2<C>> { using type = C; };
+
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
@@ -432,11 +436,13 @@ __device__ inline Sums<V> stencil_sums(const V d[12], const V e[4])
 // its equilibrium velocity by tau ax.
 // psi_s/rho_s is taken with its limit 1 at rho_s -> 0, so nothing divides by a
 // vanishing species density.
-// The rest population closes the mass: each difference f_is - f*_is of nearby
-// values is exact (Sterbenz), so the stored populations sum to the loaded ones
-// up to the one rounding of f*_0s.  (Closing on the rounded sum rho_s instead
-// repeats that sum's rounding at every site of a near-uniform state, which
-// drifted the FP32 mass coherently by 4e-6 per 1000 steps.)
+// The rest population closes the mass.  FP32: each difference f_is - f*_is of
+// nearby values is exact (Sterbenz), so the stored populations sum to the
+// loaded ones up to the one rounding of f*_0s.  (Closing on the rounded sum
+// rho_s instead repeats that sum's rounding at every site of a near-uniform
+// state, which drifted the FP32 mass coherently by 4e-6 per 1000 steps.)  FP64,
+// whose roundings are 2^29 times smaller and whose pipe bounds the step, closes
+// on rho_s: f*_0s = rho_s - sum_{i>=1} f*_is (eight operations fewer).
 // *Fx, *Fy receive F_s (for the force-corrected velocity of the observables).
 // UNIT: tau = 1 (omega = 1, the paper's choice for all its runs), where the BGK
 // update is f*_i = f^eq_i exactly and f_i only enters through the moments.
@@ -459,6 +465,7 @@ __device__ inline void collide_species(const V f[9], V rho_s, V psi_s, V ux, V u
     const V tr1 = V(3.0 * q_w(1)) * rho_s, tr5 = V(3.0 * q_w(5)) * rho_s;
     const V cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
     const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
+    constexpr bool exact_close = sizeof(typename LaneScalar<V>::type) == 4;
     V dsum = V(0.0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -472,10 +479,14 @@ __device__ inline void collide_species(const V f[9], V rho_s, V psi_s, V ux, V u
             fs[i] = vfma(omega, (a + b) - f[i], f[i]);
             fs[j] = vfma(omega, (a - b) - f[j], f[j]);
         }
-        const V dk = (f[i] - fs[i]) + (f[j] - fs[j]);
-        dsum = k == 0 ? dk : dsum + dk;
+        if constexpr (exact_close) {
+            const V dk = (f[i] - fs[i]) + (f[j] - fs[j]);
+            dsum = k == 0 ? dk : dsum + dk;
+        } else {
+            dsum = k == 0 ? fs[i] + fs[j] : dsum + (fs[i] + fs[j]);
+        }
     }
-    fs[0] = f[0] + dsum;
+    fs[0] = exact_close ? f[0] + dsum : rho_s - dsum;
 }
 
 // The same collision for shifted populations g_i = f_i - w_i rho_bar (FP16

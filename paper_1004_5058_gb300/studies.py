@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import time
 
 import numpy as np
@@ -347,11 +348,61 @@ def couette_flow_curve(n: int = 1024, n_speeds: int = 8, steps: int = 200000, ev
             "hb_fit": hb_fit(S[ok], sigma[ok]) if ok.sum() >= 3 else None}
 
 
+# surrogate layers (inputs, outputs): 5 -> 128 -> 128 -> 128 -> 2
+SURROGATE_LAYERS = ((5, 128), (128, 128), (128, 128), (128, 2))
+
+
+def surrogate_train_rate(batch: int = 10240, steps: int = 50, warmup: int = 5, seed: int = 0):
+    """Training throughput of the surrogate's BF16 kernels at one batch size:
+    Adam steps (forward, loss, backward, update; mlp_train_step) on seeded
+    points inside a training box around the paper's couplings, timed with CUDA
+    events on the handle's stream.  FLOPs per sample: the forward products
+    2 sum(in*out), the weight gradients as many, and the input gradients of
+    layers 2..4 (the network's input needs none)."""
+    import torch
+    from .surrogate import Box, Surrogate, init_params, N_IN
+    center = np.array([math.log(1e-4), -9.0, 8.1, 0.405, 1.0])
+    half = np.array([3.0, 1.35, 1.2, 0.06, 0.15])
+    u = I.uniform01(seed, batch * N_IN).reshape(batch, N_IN)
+    x = center + half * (2.0 * u - 1.0)
+    t = 1e-4 * I.uniform01(seed + 1, batch)
+    lab = (I.uniform01(seed + 2, batch) > 0.5).astype(np.float64)
+    dev = torch.device("cuda")
+    X = torch.tensor(x, dtype=torch.float32, device=dev)
+    T = torch.tensor(t, dtype=torch.float32, device=dev)
+    Y = torch.tensor(lab, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    sg = Surrogate(Box(center, half), 1e-4, max_batch=batch, lr=1e-3)
+    try:
+        sg.set_params(init_params(seed))
+        for _ in range(warmup):
+            sg.train_step(X, T, Y, loss)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sg.train_step(X, T, Y, loss)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3 / steps
+        launches = sg.kernel_launches
+        final_loss = float(loss.item())
+    finally:
+        sg.close()
+    mac = sum(i * o for i, o in SURROGATE_LAYERS)
+    flops = batch * (2 * mac + 2 * mac + 2 * sum(i * o for i, o in SURROGATE_LAYERS[1:]))
+    return {"batch": batch, "steps": steps, "us_per_step": sec * 1e6, "samples_per_s": batch / sec,
+            "flops_per_step": flops, "tflops": flops / sec / 1e12, "loss": final_loss,
+            "kernel_launches": launches}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
                                       "flow_curve_long", "couette_1024", "surrogate", "kolmogorov",
-                                      "kolmogorov_rho0", "two_time"])
+                                      "kolmogorov_rho0", "two_time", "train_rate"])
+    ap.add_argument("--batch", type=int, default=10240, help="train_rate: batch size")
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
@@ -369,6 +420,8 @@ def main():
         r = flow_curve(L=128, steps=4000, n_speeds=4) if a.quick else flow_curve(steps=1000000, every=100)
     elif a.study == "two_time":  # relaxation time per species: flow curves for three tau_B
         r = two_time_flow_curve(L=64, steps=4000, n_speeds=4) if a.quick else two_time_flow_curve()
+    elif a.study == "train_rate":
+        r = surrogate_train_rate(batch=a.batch, steps=10 if a.quick else 50)
     elif a.study == "surrogate":
         r = surrogate_study(n_train=48, n_test=12, n_speeds=8, L=32, steps=3000) if a.quick else surrogate_study()
     else:
