@@ -493,10 +493,13 @@ static lb_status create_handle(const lb_cell_params* cells, int n_cells, lb_prec
         return LB_ERR_CUDA;
     }
     h->initialised = false;
-    if (select_kernel(h, LB_KERNEL_AUTO, 0, 0) != LB_OK) {
-        fail(nullptr, LB_ERR_CUDA, "lb_create: %s", h->last_error.c_str());
+    const lb_status ks = select_kernel(h, LB_KERNEL_AUTO, 0, 0);
+    if (ks != LB_OK) {
+        // a slab runs the tiled kernel only: a shape it does not take is unsupported
+        const lb_status st = ks == LB_ERR_UNSUPPORTED ? LB_ERR_UNSUPPORTED : LB_ERR_CUDA;
+        fail(nullptr, st, "%s: %s", slab ? "lb_create_slab" : "lb_create", h->last_error.c_str());
         release(h);
-        return LB_ERR_CUDA;
+        return st;
     }
     *out = h;
     return LB_OK;

@@ -43,7 +43,7 @@ __host__ __device__ constexpr LayerDef layer_def(int l)
            : l == 2 ? LayerDef{HID, HID, HID, HID, OFF_W3, OFF_B3}
                     : LayerDef{HID, HID, NOUT, NOUTP, OFF_W4, OFF_B4};
 }
-constexpr int KSPLIT = 512;  // batch rows per split-K partial of a weight gradient
+constexpr int KSPLIT = 256;  // batch rows per split-K partial of a weight gradient
 
 enum { EPI_TANH = 0, EPI_OUT = 1, EPI_DTANH = 2, EPI_PARTIAL = 3 };
 
@@ -239,16 +239,27 @@ __global__ void reduce_wgrad_kernel(const float* __restrict__ part, int S, int M
     grad[k] = s;
 }
 
-// grad_b[o] = sum over live batch rows of d[o][b] (transposed gradient rows), one warp per o.
-__global__ void bias_grad_kernel(const bf16* __restrict__ dt, int Bbuf, int B, int out, float* __restrict__ grad)
+// grad_b[o] = sum over live batch rows of d[o][b] (transposed gradient rows): a
+// block of BIAS_THREADS per output o, each thread a strided part of the batch,
+// then a fixed-shape tree (the same order every call).
+constexpr int BIAS_THREADS = 256;
+__global__ void __launch_bounds__(BIAS_THREADS) bias_grad_kernel(const bf16* __restrict__ dt, int Bbuf, int B,
+                                                                 float* __restrict__ grad)
 {
-    const int o = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-    if (o >= out) return;
+    const int o = blockIdx.x;
     float s = 0.f;
-    for (int b = lane; b < B; b += 32) s += __bfloat162float(dt[(long long)o * Bbuf + b]);
+    for (int b = threadIdx.x; b < B; b += BIAS_THREADS) s += __bfloat162float(dt[(long long)o * Bbuf + b]);
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1) s += __shfl_down_sync(0xffffffffu, s, w);
-    if (lane == 0) grad[o] = s;
+    __shared__ float warp_sum[BIAS_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < BIAS_THREADS / 32; ++k) t += warp_sum[k];
+        grad[o] = t;
+    }
 }
 
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
@@ -566,7 +577,7 @@ cudaError_t backward(mlp_handle* h, const float* target, const float* label, int
         const int S = (Br + KSPLIT - 1) / KSPLIT;
         reduce_wgrad_kernel<<<(L.out * L.in + 255) / 256, 256, 0, h->stream>>>(h->part, S, L.out_p, L.in_p, L.out,
                                                                                 L.in, h->G + L.offW);
-        bias_grad_kernel<<<(L.out + 7) / 8, 256, 0, h->stream>>>(h->Dt[l], bb, B, L.out, h->G + L.offB);
+        bias_grad_kernel<<<L.out, BIAS_THREADS, 0, h->stream>>>(h->Dt[l], bb, B, h->G + L.offB);
         h->launches += 2;
         if (l > 0) {
             // D_{l-1} = (D_l W_l) * (1 - h_{l-1}^2)

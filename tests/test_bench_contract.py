@@ -75,6 +75,9 @@ def test_gpu_arm_line():
     assert d["gpu_launches"] >= 3 * 20
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert set(d["clocks"] or {}) >= {"sm_mhz", "sm_max_mhz", "reasons"} or d["clocks"] is None
+    # the persistent grid the runtime gave the tiled kernel
+    launch = d["config"]["launch"]
+    assert launch["ctas"] > 0 and launch["ctas_sampled"] > 0 and launch["threads"] == d["config"]["tile"][0] + 32
     # plain and sampled steps timed apart, and the timed region predicted from them
     assert rf["sampled_step_ms"] > 0 and rf["predicted_ms_per_step"] > 0 and rf["measured_ms_per_step"] > 0
     # the batched flow-curve sweep against the same cells run one at a time

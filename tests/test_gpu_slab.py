@@ -104,6 +104,9 @@ def test_slab_errors():
     with pytest.raises(LBError) as e:  # a periodic cell of 40 rows cannot hold 37 rows + 4 ghosts
         Lattice([setup(0)[0]], "fp32", slab=(0, 37))
     assert e.value.status == LB_ERR_INVALID
+    with pytest.raises(LBError) as e:  # an odd width: the tiled kernel (a slab's only one) does not take it
+        Lattice([I.make_cell("paper", nx=63, ny=40, bc=1)], "fp32", slab=(0, 20))
+    assert e.value.status == LB_ERR_UNSUPPORTED
     with Lattice([cell], "fp32", slab=(10, 12)) as lat:
         y0, rows, nyg = C.c_int(), C.c_int(), C.c_int()
         assert lat.lib.lb_slab_info(lat.h, C.byref(y0), C.byref(rows), C.byref(nyg)) == 0
