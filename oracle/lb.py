@@ -20,7 +20,8 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("tau", C.c_double), ("rho0", C.c_double),
                 ("g_aa1", C.c_double), ("g_aa2", C.c_double), ("g_bb1", C.c_double),
                 ("g_bb2", C.c_double), ("g_ab", C.c_double), ("u_wall", C.c_double),
-                ("f0", C.c_double), ("bc", C.c_int), ("tau_b", C.c_double)]
+                ("f0", C.c_double), ("bc", C.c_int), ("tau_b", C.c_double),
+                ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double), ("s_nu", C.c_double)]
 
 
 class Obs(C.Structure):
@@ -62,7 +63,8 @@ def params(cell) -> Params:
     """Params from an inputs.CellParams (or any object with the same fields)."""
     return Params(cell.nx, cell.ny, cell.tau, cell.rho0, cell.g_aa1, cell.g_aa2, cell.g_bb1,
                   cell.g_bb2, cell.g_ab, cell.u_wall, getattr(cell, "f0", 0.0), cell.bc,
-                  getattr(cell, "tau_b", 0.0))
+                  getattr(cell, "tau_b", 0.0), getattr(cell, "s_e", 0.0), getattr(cell, "s_eps", 0.0),
+                  getattr(cell, "s_q", 0.0), getattr(cell, "s_nu", 0.0))
 
 
 def _f64(a, shape):

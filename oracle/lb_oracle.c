@@ -47,7 +47,17 @@
  *    tau_s F_s / rho_s, and u is the common velocity of the two relaxations,
  *    u = (sum_s j_s / tau_s) / (sum_s rho_s / tau_s) (Shan and Doolen, J. Stat.
  *    Phys. 81 (1995) 379), which equals j / rho when the times are equal and
- *    keeps the collision from creating momentum when they are not.
+ *    keeps the collision from creating momentum when they are not;
+ *  - a multiple-relaxation-time collision (the other form of a relaxation that
+ *    depends on more than one time; not in the paper): f* = f - M^-1 S M (f - f^eq)
+ *    with M the orthogonal D2Q9 moment basis of Lallemand and Luo (Phys. Rev. E
+ *    61 (2000) 6546) and S = diag(s_k).  f^eq is the paper's shifted equilibrium,
+ *    so the density and momentum moments relax with 1/tau_s (the rate at which
+ *    the shift tau_s F_s / rho_s adds F_s per step); the energy e, its square
+ *    eps, the energy flux q and the stress p relax with the cell's s_e, s_eps,
+ *    s_q, s_nu, each 0 meaning 1/tau_s.  With all four 0 the collision is the
+ *    paper's BGK one (taken on the BGK code path).  The shear viscosity is then
+ *    (1/s_nu - 1/2)/3, independent of the forcing time tau.
  *
  * Layout of a population array: [species s=0(A),1(B)][i=0..8][y][x], x fastest.
  * D2Q9 order: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
@@ -72,6 +82,8 @@ typedef struct {
     double f0;  /* Kolmogorov body force F_x(y) = f0 sin(2 pi y / ny) */
     int bc;     /* 0: periodic in x and y; 1: Couette (periodic x, walls in y) */
     double tau_b; /* relaxation time of species B; 0: tau (one time for both) */
+    /* multiple-relaxation-time rates of the e, eps, q and p moments; 0: 1/tau_s */
+    double s_e, s_eps, s_q, s_nu;
 } orc_params;
 
 /* Per-step observables of one sampled step (all FP64). */
@@ -181,6 +193,57 @@ void orc_equilibrium(const orc_params* p, const double* rho_a, const double* rho
 
 /* Moments: rho_s = sum_i f_is; j = sum_s sum_i f_is c_i, taken as differences of
  * opposite populations so that a state at rest gives exactly j = 0. */
+/* Row k of the orthogonal D2Q9 moment basis of Lallemand and Luo at velocity
+ * c_i: the moments rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy are the
+ * polynomials 1, 3c^2 - 4, (9c^4 - 21c^2 + 8)/2, c_x, (3c^2 - 5)c_x, c_y,
+ * (3c^2 - 5)c_y, c_x^2 - c_y^2, c_x c_y of c = c_i (c^2 = c_x^2 + c_y^2). */
+static double mrt_row(int k, int i)
+{
+    const double cx = CX[i], cy = CY[i], c2 = cx * cx + cy * cy;
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return 3.0 * c2 - 4.0;
+    case 2: return (9.0 * c2 * c2 - 21.0 * c2 + 8.0) / 2.0;
+    case 3: return cx;
+    case 4: return (3.0 * c2 - 5.0) * cx;
+    case 5: return cy;
+    case 6: return (3.0 * c2 - 5.0) * cy;
+    case 7: return cx * cx - cy * cy;
+    default: return cx * cy;
+    }
+}
+
+static int mrt_on(const orc_params* p) { return p->s_e != 0.0 || p->s_eps != 0.0 || p->s_q != 0.0 || p->s_nu != 0.0; }
+
+/* The relaxed populations of one species at one site: BGK, f - (f - f^eq)/tau,
+ * or, when the cell sets multiple-relaxation-time rates, f - M^-1 S M (f - f^eq)
+ * with M^-1 = M^T D^-1, D = diag(sum_i M_ki^2) (the rows of M are orthogonal). */
+static void relax(const orc_params* p, double tau, const double fi[9], const double feq[9], double out[9])
+{
+    if (!mrt_on(p)) {
+        for (int i = 0; i < 9; ++i) out[i] = fi[i] - (fi[i] - feq[i]) / tau;
+        return;
+    }
+    const double om = 1.0 / tau;
+    const double s[9] = {om, p->s_e != 0.0 ? p->s_e : om, p->s_eps != 0.0 ? p->s_eps : om, om,
+                         p->s_q != 0.0 ? p->s_q : om, om, p->s_q != 0.0 ? p->s_q : om,
+                         p->s_nu != 0.0 ? p->s_nu : om, p->s_nu != 0.0 ? p->s_nu : om};
+    double n[9];
+    for (int k = 0; k < 9; ++k) {
+        double m = 0.0, d = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            m += mrt_row(k, i) * (fi[i] - feq[i]);
+            d += mrt_row(k, i) * mrt_row(k, i);
+        }
+        n[k] = s[k] * m / d;
+    }
+    for (int i = 0; i < 9; ++i) {
+        double c = 0.0;
+        for (int k = 0; k < 9; ++k) c += mrt_row(k, i) * n[k];
+        out[i] = fi[i] - c;
+    }
+}
+
 /* Relaxation time of species s: tau for A; tau_b for B, or tau when tau_b is 0. */
 static double tau_of(const orc_params* p, int s)
 {
@@ -360,12 +423,14 @@ void orc_step(const orc_params* p, const double* f_in, double* f_out, orc_obs* o
                     us[a] = u[a] - tau * (por * G + (p->g_ab / rho0) * X[a]) + tau * body / rtot;
                 }
                 double usq = us[0] * us[0] + us[1] * us[1];
+                double fi[9], feq[9], fo[9];
                 for (int i = 0; i < 9; ++i) {
                     double cu = CX[i] * us[0] + CY[i] * us[1];
-                    double feq = W[i] * rs * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-                    double fi = f_in[FIDX(p, s, i, x, y)];
-                    fst[FIDX(p, s, i, x, y)] = fi - (fi - feq) / tau;
+                    feq[i] = W[i] * rs * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                    fi[i] = f_in[FIDX(p, s, i, x, y)];
                 }
+                relax(p, tau, fi, feq, fo);
+                for (int i = 0; i < 9; ++i) fst[FIDX(p, s, i, x, y)] = fo[i];
             }
             uphys[k] = (jj[k] + 0.5 * Ftot[0]) / rtot;
         }
@@ -537,12 +602,14 @@ int orc_step_slab(const orc_params* p, int y0, int rows, const double* f_in, dou
                     us[a] = u[a] - tau * (por * G + (p->g_ab / rho0) * X[a]) + tau * body / rtot;
                 }
                 double usq = us[0] * us[0] + us[1] * us[1];
+                double fi[9], feq[9], fo[9];
                 for (int i = 0; i < 9; ++i) {
                     double cu = CX[i] * us[0] + CY[i] * us[1];
-                    double feq = W[i] * rs * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-                    double fi = f_in[SIDX(p, nr, s, i, x, e)];
-                    fst[SIDX(p, nr, s, i, x, e)] = fi - (fi - feq) / tau;
+                    feq[i] = W[i] * rs * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                    fi[i] = f_in[SIDX(p, nr, s, i, x, e)];
                 }
+                relax(p, tau, fi, feq, fo);
+                for (int i = 0; i < 9; ++i) fst[SIDX(p, nr, s, i, x, e)] = fo[i];
             }
             uphys[k] = (jj[k] + 0.5 * Ftot[0]) / rtot;
         }

@@ -52,6 +52,11 @@ class CellParams:
     rho_bar_a/b: reference densities of the FP16 shifted storage f_i - w_i*rho_bar.
     tau_b: relaxation time of species B, 0 for tau (the paper uses one time,
     tau = 1, and leaves a coupling-dependent one unexplored); tau is species A's.
+    s_e, s_eps, s_q, s_nu: rates of a multiple-relaxation-time collision
+    (Lallemand and Luo's orthogonal D2Q9 moments e, eps, q_x/q_y, p_xx/p_xy; not
+    in the paper), each 0 for 1/tau_s; all 0 is the paper's BGK collision.  The
+    density and momentum moments always relax with 1/tau_s, so tau_s still sets
+    the force shift, and s_nu sets the shear viscosity (1/s_nu - 1/2)/3.
     """
     nx: int = 64
     ny: int = 64
@@ -68,6 +73,10 @@ class CellParams:
     rho_bar_b: float = 0.6
     bc: int = 0
     tau_b: float = 0.0
+    s_e: float = 0.0
+    s_eps: float = 0.0
+    s_q: float = 0.0
+    s_nu: float = 0.0
 
     def as_dict(self):
         return asdict(self)

@@ -548,3 +548,114 @@ def test_kolmogorov_laminar_amplitude(tau):
     y = np.arange(ny)
     amp = 2.0 / ny * np.sum(ub * np.sin(k * y))
     assert amp == pytest.approx(1e-3, rel=2e-2)
+
+
+# ------------------------------------------- multiple relaxation times --
+# A collision with one rate per group of moments (Lallemand and Luo, Phys. Rev.
+# E 61 (2000) 6546; a method variant, not in the paper): f* = f - M^-1 S M (f -
+# f^eq) with the paper's shifted f^eq; rho and j relax with 1/tau_s, the energy
+# e, its square eps, the flux q and the stress p with s_e, s_eps, s_q, s_nu.
+CX9 = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=np.float64)
+CY9 = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=np.float64)
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def gram_schmidt_moments():
+    """An orthogonal basis of the functions on the nine velocities, made here by
+    Gram-Schmidt (plain sum over the velocities as inner product) from the
+    monomials 1, c^2, c^4, c_x, c^2 c_x, c_y, c^2 c_y, c_x^2 - c_y^2, c_x c_y: the
+    moments rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy up to scale."""
+    c2 = CX9 ** 2 + CY9 ** 2
+    basis = []
+    for m in (np.ones(9), c2, c2 * c2, CX9, c2 * CX9, CY9, c2 * CY9, CX9 ** 2 - CY9 ** 2, CX9 * CY9):
+        v = m.astype(np.float64).copy()
+        for b in basis:
+            v -= (v @ b) / (b @ b) * b
+        basis.append(v)
+    return np.array(basis)
+
+
+def d2q9_feq(rho, ux, uy):
+    cu = CX9 * ux + CY9 * uy
+    return W9 * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy))
+
+
+def test_mrt_each_moment_relaxes_at_its_own_rate():
+    """A spatially uniform state has no force and streams onto itself, so rho_s
+    and j_s stay and each other moment's distance from equilibrium is multiplied
+    per step by 1 - its rate: e by 1 - s_e, eps by 1 - s_eps, q_x and q_y by
+    1 - s_q, p_xx and p_xy by 1 - s_nu.  The four factors differ (-0.3, 0.3,
+    -0.7, 0.1), so a moment row of the wrong shape, a wrong normalisation of
+    M^-1 or a rate given to the wrong moment fails."""
+    rates = dict(s_e=1.3, s_eps=0.7, s_q=1.7, s_nu=0.9)
+    factor = [None, 1 - 1.3, 1 - 0.7, None, 1 - 1.7, None, 1 - 1.7, 1 - 0.9, 1 - 0.9]
+    n = 4
+    c = I.make_cell("paper", nx=n, ny=n, g_ab=0.405, tau=0.8, tau_b=1.3, **rates)
+    B = gram_schmidt_moments()
+    ux, uy, rho = 0.03, -0.02, (0.7, 0.5)
+    delta = np.random.default_rng(7).standard_normal(9) * 1e-3
+    for k in (0, 3, 5):  # no change of rho or j: the equilibrium stays f^eq(rho_s, u)
+        delta -= (delta @ B[k]) / (B[k] @ B[k]) * B[k]
+    f = np.empty((2, 9, n, n))
+    for s in range(2):
+        f[s] = (d2q9_feq(rho[s], ux, uy) + rho[s] * delta)[:, None, None]
+    n0 = [B @ (f[s, :, 0, 0] - d2q9_feq(rho[s], ux, uy)) for s in range(2)]
+    for t in range(1, 7):
+        f, _, _ = lb.step(c, f)
+        assert np.all(f == f[:, :, :1, :1])  # uniform, bit for bit
+        for s in range(2):
+            got = B @ (f[s, :, 0, 0] - d2q9_feq(rho[s], ux, uy))
+            want = [0.0 if q is None else n0[s][k] * q ** t for k, q in enumerate(factor)]
+            np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+
+
+def test_mrt_with_every_rate_one_over_tau_is_bgk():
+    """Rates all equal to 1/tau take the multiple-relaxation-time code path and
+    must give the BGK collision: M^-1 (I/tau) M = I/tau."""
+    ra, rb = I.random_fields(24, 24, seed=4)
+    out = []
+    for rates in ({}, dict(s_e=1 / 0.8, s_eps=1 / 0.8, s_q=1 / 0.8, s_nu=1 / 0.8)):
+        c = I.make_cell("paper", nx=24, ny=24, g_ab=0.405, bc=1, u_wall=0.01, tau=0.8, **rates)
+        out.append(lb.Run(c, ra[0], rb[0]).step(30).f)
+    assert np.abs(out[0] - out[1]).max() <= 1e-13
+
+
+def test_mrt_conserves_mass_and_momentum_periodic():
+    """Interacting mixture, two relaxation times, all four rates set: species
+    masses and the total momentum stay (the interaction forces sum to zero and
+    j relaxes with 1/tau_s around the common velocity, as in the BGK model)."""
+    n = 32
+    c = I.make_cell("paper", nx=n, ny=n, g_ab=0.405, tau=0.8, tau_b=1.2, s_e=1.4, s_eps=1.1, s_q=1.6, s_nu=1.3)
+    ra, rb = I.random_fields(n, n, seed=3)
+    ux = 0.01 * np.sin(2 * np.pi * np.arange(n) / n)[:, None] * np.ones((1, n))
+    r = lb.Run(c, ra[0], rb[0], ux, np.zeros_like(ux))
+    jx0, jy0, m0 = species_momenta(r.f)
+    r.step(60)
+    jx1, jy1, m1 = species_momenta(r.f)
+    assert np.abs(m1.sum(axis=(1, 2)) / m0.sum(axis=(1, 2)) - 1).max() <= 1e-13
+    total = m0.sum()
+    assert abs(jx1.sum() - jx0.sum()) / total <= 1e-14 and abs(jy1.sum() - jy0.sum()) / total <= 1e-14
+    assert abs(jx1.sum(axis=(1, 2))[0] - jx0.sum(axis=(1, 2))[0]) / total > 1e-8  # the species do exchange momentum
+
+
+@pytest.mark.parametrize("tau,s_nu", [(1.0, 1.6), (0.8, 0.9)])
+def test_mrt_shear_viscosity_is_set_by_s_nu(tau, s_nu):
+    """A shear wave at G = 0 decays at nu k^2 with nu = (1/s_nu - 1/2)/3, not
+    (tau - 1/2)/3: the stress moments carry the viscosity."""
+    L = 64
+    k = 2 * math.pi / L
+    c = I.make_cell("ideal", nx=4, ny=L, tau=tau, s_nu=s_nu)
+    y = np.arange(L, dtype=np.float64)
+    ux = np.tile((1e-5 * np.sin(k * y))[:, None], (1, 4))
+    r = lb.Run(c, np.full((L, 4), 0.6), np.full((L, 4), 0.6), ux, np.zeros_like(ux))
+
+    def amp():
+        _, _, u, _ = r.fields()
+        return 2.0 / L * np.sum(u.mean(axis=1) * np.sin(k * y))
+
+    r.step(50)
+    a0, t0 = amp(), r.t
+    r.step(400)
+    rate = -math.log(amp() / a0) / (r.t - t0)
+    assert rate == pytest.approx((1 / s_nu - 0.5) / 3 * k * k, rel=2e-2)
+    assert abs(rate / ((tau - 0.5) / 3 * k * k) - 1) > 0.5
