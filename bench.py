@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--tau-b", type=float, default=0.0,
                     help="relaxation time of species B (0: tau = 1 for both, the paper's model); "
                          "a time per species runs the common-velocity variant")
+    ap.add_argument("--mrt", default="",
+                    help="s_e,s_eps,s_q,s_nu (e.g. 1.4,1.1,1.2,1.1): the multiple-relaxation-time collision with these rates "
+                         "(a method variant; default: the paper's BGK collision)")
     ap.add_argument("--tile", default="", help="TXxTY for the tiled kernel (default: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -82,10 +85,21 @@ def dist_env():
     return rank_world()
 
 
-def workload_cells(nx, ny, n_cells, rank, tau_b=0.0):
+def mrt_rates(spec):
+    """{s_e, s_eps, s_q, s_nu} from "a,b,c,d" ({} for an empty string: BGK)."""
+    if not spec:
+        return {}
+    v = [float(x) for x in spec.split(",")]
+    if len(v) != 4:
+        raise SystemExit("--mrt wants four rates s_e,s_eps,s_q,s_nu")
+    return dict(zip(("s_e", "s_eps", "s_q", "s_nu"), v))
+
+
+def workload_cells(nx, ny, n_cells, rank, tau_b=0.0, mrt=""):
     from paper_1004_5058_gb300 import inputs as I
     speeds = I.log_spaced(1e-4, 1e-2, n_cells) if n_cells > 1 else [1e-3]
-    return [I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=u, tau_b=tau_b) for u in speeds]
+    return [I.make_cell("paper", nx=nx, ny=ny, g_ab=0.405, bc=1, u_wall=u, tau_b=tau_b, **mrt_rates(mrt))
+            for u in speeds]
 
 
 def workload_fields(nx, ny, cells, seed):
@@ -117,16 +131,18 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(precision, nx, ny, n_cells, two_time=False):
+def committed_traffic(precision, nx, ny, n_cells, two_time=False, mrt=False):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     scaled to this workload's sites, if it was taken on the current sources.
-    Cells with a relaxation time per species run the general kernel, which has
-    its own entry ("<precision>_two_time"); without one the traffic is unknown."""
+    Cells with a relaxation time per species run the general kernel, and cells
+    with multiple relaxation times the MRT kernel; each has its own entry
+    ("<precision>_two_time", "<precision>_mrt"); without one the traffic is
+    unknown."""
     p = os.path.join(ROOT, "profiles", "fused_step_dram.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(precision + ("_two_time" if two_time else ""))
+    e = d.get(precision + ("_mrt" if mrt else "_two_time" if two_time else ""))
     if not e or d.get("source_digest") != source_digest():
         return None
     per_site = float(e["dram_bytes_per_launch"]) / float(e["sites_per_launch"])
@@ -191,6 +207,8 @@ def workload_config(args):
             "sampling_every": args.every, "precision": args.precision,
             "couplings": "paper footnote, G_AB=0.405", "u_wall": "1e-4..1e-2 log",
             "tau": "1 (both species)" if args.tau_b == 0 else "A 1, B %g (common-velocity variant)" % args.tau_b,
+            "collision": ("BGK (the paper's)" if not args.mrt else
+                          "multiple relaxation times s_e,s_eps,s_q,s_nu = %s (method variant)" % args.mrt),
             "l2": "inputs larger than L2 (%.2f GB populations, ping-pong)" % (bytes_pop / 1e9)}
 
 
@@ -198,7 +216,7 @@ def cpu_baseline(args, seconds):
     """The FP64 oracle, as it stands, on this host's cores: one cell of the
     workload, as many time steps as fit in about `seconds`."""
     from oracle import lb as orc
-    cells = workload_cells(args.nx, args.ny, args.cells, 0, args.tau_b)
+    cells = workload_cells(args.nx, args.ny, args.cells, 0, args.tau_b, args.mrt)
     cell = cells[len(cells) // 2]
     ra, rb, ux, uy = workload_fields(args.nx, args.ny, [cell], seed=1004)
     run = orc.Run(cell, ra[0], rb[0], ux[0], uy[0])
@@ -256,7 +274,7 @@ def run_reference(args):
     K, W = args.steps, args.warmup
     per_step = max(1.0, min(args.cpu_seconds, 60.0 / max(1, K + W)))
     from oracle import lb as orc
-    cells = workload_cells(args.nx, args.ny, args.cells, 0, args.tau_b)
+    cells = workload_cells(args.nx, args.ny, args.cells, 0, args.tau_b, args.mrt)
     cell = cells[len(cells) // 2]
     ra, rb, ux, uy = workload_fields(args.nx, args.ny, [cell], seed=1004)
     run = orc.Run(cell, ra[0], rb[0], ux[0], uy[0])
@@ -393,7 +411,7 @@ def run_ours(args):
     from paper_1004_5058_gb300.dist import max_over_ranks
 
     nx, ny, n_cells, chunk = args.nx, args.ny, args.cells, args.chunk
-    cells = workload_cells(nx, ny, n_cells, rank, args.tau_b)
+    cells = workload_cells(nx, ny, n_cells, rank, args.tau_b, args.mrt)
     ra, rb, ux, uy = workload_fields(nx, ny, cells, seed=1004 + rank)
     lat = Lattice(cells, args.precision)
     lat.init_fields(ra, rb, ux, uy)
@@ -469,8 +487,8 @@ def run_ours(args):
     alg_bytes = BYTES_PER_SITE[args.precision] * sites
     peak, peak_kind = peaks()
     achieved = alg_bytes / (t_launch if kernels_per_step == 1 else t_launch * kernels_per_step) / 1e9
-    traffic = (committed_traffic(args.precision, nx, ny, n_cells, two_time=args.tau_b not in (0.0, 1.0))
-               if kernel == "tiled" else None)
+    traffic = (committed_traffic(args.precision, nx, ny, n_cells, two_time=args.tau_b not in (0.0, 1.0),
+                                 mrt=bool(args.mrt)) if kernel == "tiled" else None)
 
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
@@ -484,7 +502,8 @@ def run_ours(args):
     if args.precision == "fp64":
         sm_mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
         p64 = N_SM * FP64_OPS_PER_CLOCK * sm_mhz * 1e-3
-        gops = FP64_OPS_PER_SITE * sites / t_plain / 1e9 if kernel == "tiled" else None
+        # the op count is the BGK kernel's (the MRT one adds its correction)
+        gops = FP64_OPS_PER_SITE * sites / t_plain / 1e9 if kernel == "tiled" and not args.mrt else None
         roofline = {"bound": "alu", "achieved": gops, "peak": p64, "unit": "G FP64 op/s",
                     "frac": None if gops is None else gops / p64, "kernel": kernel,
                     "traffic": traffic,
@@ -534,7 +553,7 @@ def run_ours(args):
         "flow_curve": {"sigma_xy": [float(v) for v in sigma], "shear_rate": [float(v) for v in S]},
     }
     lat.close()
-    if args.bvp_steps > 0 and args.precision in ("fp32", "fp16", "fp16sr") and args.tau_b == 0.0:
+    if args.bvp_steps > 0 and args.precision in ("fp32", "fp16", "fp16sr") and args.tau_b == 0.0 and not args.mrt:
         bvp = batched_vs_plain(args, torch, Lattice, hb_fit)
         bvp_s = max_over_ranks(bvp.pop("_wall_batched"), device="cuda")
         bvp["batched"]["points_per_s_all_ranks"] = bvp["cells"] * world / bvp_s

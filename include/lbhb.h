@@ -92,8 +92,21 @@ typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_GENERIC = 1, LB_KERNEL_TILED = 2 } 
  *            common velocity (j_A/tau_A + j_B/tau_B) / (rho_A/tau_A + rho_B/tau_B)
  *            of Shan and Doolen (J. Stat. Phys. 81, 1995), which keeps the
  *            collision from creating momentum; tau_b = tau gives the one-time
- *            model bit for bit.  Last field, so callers that fill the fields
- *            before it and zero the rest get the paper's model. */
+ *            model bit for bit.
+ *   s_e, s_eps, s_q, s_nu  rates of a multiple-relaxation-time collision, each
+ *            in (0, 2), or 0 for 1/tau_s (a method variant, not in the paper;
+ *            the same footnote's unexplored relaxation).  The collision becomes
+ *            f* = f - M^-1 S M (f - f^eq) on the orthogonal D2Q9 moments of
+ *            Lallemand and Luo (Phys. Rev. E 61, 2000): density and momentum
+ *            relax with 1/tau_s (so tau_s still sets the force shift tau_s F_s /
+ *            rho_s), the energy e with s_e, its square eps with s_eps, the energy
+ *            fluxes q_x, q_y with s_q and the stresses p_xx, p_xy with s_nu,
+ *            which sets the shear viscosity (1/s_nu - 1/2)/3.  With all four 0
+ *            the collision is the paper's BGK one.  A batch in which any cell
+ *            sets a rate runs every cell through the MRT update (cells without
+ *            rates then get the BGK result to rounding, not bit for bit).
+ * The fields after bc are last, so callers that fill the fields before them and
+ * zero the rest get the paper's model. */
 typedef struct {
     int nx, ny;
     double tau, rho0;
@@ -103,6 +116,7 @@ typedef struct {
     double rho_bar_a, rho_bar_b;
     int bc;
     double tau_b;
+    double s_e, s_eps, s_q, s_nu;
 } lb_cell_params;
 
 /* Creates a handle for n_cells cells (n_cells >= 1; nx >= 5, ny >= 5; same nx, ny,

@@ -29,7 +29,8 @@ class lb_cell_params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("tau", C.c_double), ("rho0", C.c_double),
                 ("g_aa1", C.c_double), ("g_aa2", C.c_double), ("g_bb1", C.c_double),
                 ("g_bb2", C.c_double), ("g_ab", C.c_double), ("u_wall", C.c_double), ("f0", C.c_double),
-                ("rho_bar_a", C.c_double), ("rho_bar_b", C.c_double), ("bc", C.c_int), ("tau_b", C.c_double)]
+                ("rho_bar_a", C.c_double), ("rho_bar_b", C.c_double), ("bc", C.c_int), ("tau_b", C.c_double),
+                ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double), ("s_nu", C.c_double)]
 
 
 class mlp_config(C.Structure):

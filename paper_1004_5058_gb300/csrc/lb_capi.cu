@@ -127,6 +127,9 @@ static void release(lb_handle* h)
     delete h;
 }
 
+// true if the cell sets a multiple-relaxation-time rate
+static bool has_mrt(const lb_cell_params& c) { return c.s_e != 0.0 || c.s_eps != 0.0 || c.s_q != 0.0 || c.s_nu != 0.0; }
+
 template <class C>
 static void fill(ParamSet<C>& d, const lb_cell_params& c)
 {
@@ -149,14 +152,25 @@ static void fill(ParamSet<C>& d, const lb_cell_params& c)
     d.two_over_ny = C(2.0 / c.ny);
     d.rho_bar[0] = C(c.rho_bar_a);
     d.rho_bar[1] = C(c.rho_bar_b);
+    // multiple relaxation times: (w - s_k)/D per species, s_k = w where unset
+    d.mrt = has_mrt(c) ? 1 : 0;
+    for (int s = 0; s < 2; ++s) {
+        const double w = 1.0 / (s ? tau_b : c.tau);
+        const double r[4] = {c.s_e, c.s_eps, c.s_q, c.s_nu}, norm[4] = {12.0, 12.0, 12.0, 4.0};
+        for (int k = 0; k < 4; ++k) d.mrt_h[s][k] = C(d.mrt ? (w - (r[k] != 0.0 ? r[k] : w)) / norm[k] : 0.0);
+    }
 }
 
-// true if no cell gives species B a relaxation time of its own
-static bool one_relaxation_time(const std::vector<lb_cell_params>& cells)
+// The batch's collision for the tiled kernels: MRT if any cell sets a rate,
+// else BGK with one relaxation time unless some cell gives species B its own
+static int collision_kind(const std::vector<lb_cell_params>& cells)
 {
-    for (const lb_cell_params& c : cells)
-        if (c.tau_b != 0.0 && c.tau_b != c.tau) return false;
-    return true;
+    int kind = TILED_BGK_ONE_TIME;
+    for (const lb_cell_params& c : cells) {
+        if (has_mrt(c)) return TILED_MRT;
+        if (c.tau_b != 0.0 && c.tau_b != c.tau) kind = TILED_BGK;
+    }
+    return kind;
 }
 
 static CellDev to_dev(const lb_cell_params& c)
@@ -261,7 +275,7 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
     const char* msg = nullptr;
     TiledPlan* p = tiled_create(h->gbuf, h->rm, (int)h->prec, h->elem, h->bc, h->f[0], h->f[1], tx, ty, &msg);
     if (!p) return fail(h, LB_ERR_UNSUPPORTED, "lb_set_kernel: %s", msg ? msg : "tiled plan failed");
-    tiled_set_one_time(p, one_relaxation_time(h->cells));
+    tiled_set_collision(p, collision_kind(h->cells));
     if (h->plan) tiled_destroy(h->plan);
     h->plan = p;
     h->kernel = LB_KERNEL_TILED;
@@ -270,12 +284,13 @@ static lb_status select_kernel(lb_handle* h, lb_kernel k, int tx, int ty)
 }
 
 // ------------------------------------------------------------ checkpoints --
-// File layout (version 2, this machine's byte order):
+// File layout (version 3, this machine's byte order):
 //   header  128 bytes: magic "LBHBCKPT", u32 version, u32 header bytes, i32
 //           n_cells, nx, ny, bc, precision, element bytes, i64 t, start,
 //           every, n_samples, u64 payload bytes, u64 FNV-1a 64 of the payload
-//   payload 15 float64 per cell (lb_cell_params in declaration order; version
-//           1 files hold the first 14, without tau_b, and load as tau_b = 0), the
+//   payload 19 float64 per cell (lb_cell_params in declaration order; version
+//           2 files hold the first 15, without the MRT rates, and load them as
+//           0; version 1 files the first 14, also without tau_b), the
 //           time sums of the line profile [cell][ny] and of the wall momenta
 //           [cell][2] (float64), the populations [cell][s][i][y][x] in the
 //           storage precision without row padding
@@ -303,18 +318,18 @@ struct Fnv {
     }
 };
 
-constexpr int kCellDoubles = 15;  // per cell in version 2 (14 in version 1)
+constexpr int kCellDoubles = 19;  // per cell in version 3 (15 in version 2, 14 in version 1)
 
 void cell_to_doubles(const lb_cell_params& c, double v[kCellDoubles])
 {
     const double a[kCellDoubles] = {(double)c.nx, (double)c.ny, c.tau, c.rho0, c.g_aa1, c.g_aa2, c.g_bb1,
                                     c.g_bb2, c.g_ab, c.u_wall, c.f0, c.rho_bar_a, c.rho_bar_b, (double)c.bc,
-                                    c.tau_b};
+                                    c.tau_b, c.s_e, c.s_eps, c.s_q, c.s_nu};
     for (int k = 0; k < kCellDoubles; ++k) v[k] = a[k];
 }
 
-// false if the integer fields are not small whole numbers; v[14] (tau_b) is
-// read only from version 2 files (the caller passes 0 for version 1)
+// false if the integer fields are not small whole numbers; fields a file's
+// version does not hold arrive as 0 (tau_b, the MRT rates)
 bool cell_from_doubles(const double v[kCellDoubles], lb_cell_params* out)
 {
     for (int k : {0, 1, 13})
@@ -335,6 +350,10 @@ bool cell_from_doubles(const double v[kCellDoubles], lb_cell_params* out)
     c.rho_bar_b = v[12];
     c.bc = (lb_bc)(int)v[13];
     c.tau_b = v[14];
+    c.s_e = v[15];
+    c.s_eps = v[16];
+    c.s_q = v[17];
+    c.s_nu = v[18];
     return true;
 }
 
@@ -371,6 +390,11 @@ static bool cells_valid(const lb_cell_params* cells, int n_cells, char* why, siz
             snprintf(why, n, "cell %d tau_b=%g must exceed 1/2 (or be 0: tau)", c, p.tau_b);
             return false;
         }
+        for (double r : {p.s_e, p.s_eps, p.s_q, p.s_nu})
+            if (r != 0.0 && !(r > 0.0 && r < 2.0)) {
+                snprintf(why, n, "cell %d: a multiple-relaxation-time rate %g is outside (0, 2) (0: 1/tau)", c, r);
+                return false;
+            }
         if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0)) {
             snprintf(why, n, "cell %d rho0=%g must be positive", c, p.rho0);
             return false;
@@ -1023,7 +1047,7 @@ lb_status lb_save(lb_handle* h, const char* path)
     CkptHeader hd;
     memset(&hd, 0, sizeof hd);
     memcpy(hd.magic, kMagic, 8);
-    hd.version = 2;
+    hd.version = 3;
     hd.header_bytes = sizeof hd;
     hd.n_cells = h->n_cells;
     hd.nx = h->nx;
@@ -1083,7 +1107,7 @@ lb_status lb_load(lb_handle* h, const char* path)
     CkptHeader hd;
     if (fread(&hd, sizeof hd, 1, in.f) != 1 || memcmp(hd.magic, kMagic, 8) != 0)
         return fail(h, LB_ERR_INVALID, "lb_load: %s is not a checkpoint", path);
-    if ((hd.version != 1 && hd.version != 2) || hd.header_bytes != sizeof hd)
+    if (hd.version < 1 || hd.version > 3 || hd.header_bytes != sizeof hd)
         return fail(h, LB_ERR_INVALID, "lb_load: checkpoint version %u not supported", hd.version);
     if (hd.n_cells != h->n_cells || hd.nx != h->nx || hd.ny != h->ny || hd.bc != h->bc ||
         hd.prec != (int32_t)h->prec || hd.elem != h->elem)
@@ -1109,7 +1133,7 @@ lb_status lb_load(lb_handle* h, const char* path)
     };
     std::vector<lb_cell_params> cells(h->n_cells);
     bool cells_ok = true;
-    const int per_cell = hd.version == 1 ? 14 : kCellDoubles;
+    const int per_cell = hd.version == 1 ? 14 : hd.version == 2 ? 15 : kCellDoubles;
     for (int c = 0; c < h->n_cells; ++c) {
         double v[kCellDoubles] = {};
         get(v, sizeof(double) * per_cell);
@@ -1143,7 +1167,7 @@ lb_status lb_load(lb_handle* h, const char* path)
     CK(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
     h->h_err[0] = 0;
     h->cells = cells;
-    if (h->plan) tiled_set_one_time(h->plan, one_relaxation_time(h->cells));
+    if (h->plan) tiled_set_collision(h->plan, collision_kind(h->cells));
     free_graphs(h);  // captured launches may name the other kernel family
     h->cur = 0;
     h->t = hd.t;

@@ -59,6 +59,11 @@ template <class C> struct ParamSet {
     C rho_bar[2];    // FP16 shift reference
     C f0;            // Kolmogorov body force F_x(y) = f0 sin(pi y two_over_ny)
     C two_over_ny;
+    // multiple-relaxation-time collision: per species s, (w - s_e)/12,
+    // (w - s_eps)/12, (w - s_q)/12, (w - s_nu)/4 with w = omega_s (mrt_delta);
+    // mrt != 0 if the cell sets any of the four rates
+    C mrt_h[2][4];
+    int mrt;
 };
 struct CellDev {
     ParamSet<double> d;
@@ -420,6 +425,40 @@ __device__ inline Sums<V> stencil_sums(const V d[12], const V e[4])
     return r;
 }
 
+// Multiple-relaxation-time correction of a BGK collision (the orthogonal D2Q9
+// moments rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy of Lallemand and Luo,
+// Phys. Rev. E 61 (2000) 6546; not in the paper).  The BGK result f + w d,
+// d_i = f^eq_i - f_i, relaxes every moment with w; adding
+//   -sum_k (s_k - w) n_k M_ki / D_k,   n_k = sum_i M_ki (f_i - f^eq_i),
+// over k = e, eps, q_x, q_y, p_xx, p_xy (norms D = 36, 36, 12, 12, 4, 4) gives
+// those moments their own rates s_k; rho and j keep w.  d_0 enters as
+// -(d_1 + ... + d_8) (f and f^eq carry the same density).  h = ((w - s_e)/12,
+// (w - s_eps)/12, (w - s_q)/12, (w - s_nu)/4).  fs[0] is left to the caller's
+// closure (the correction has no density).
+template <class V>
+__device__ inline void mrt_delta(const V d[9], const V h[4], V fs[9])
+{
+    const V s13 = d[1] + d[3], s24 = d[2] + d[4], s57 = d[5] + d[7], s68 = d[6] + d[8];
+    const V ax = s13 + s24, dg = s57 + s68;  // axis and diagonal sums
+    const V d13 = d[1] - d[3], d24 = d[2] - d[4], d57 = d[5] - d[7], d86 = d[8] - d[6];
+    const V ce = h[0] * vfma(V(2.0), dg, ax);               // e:   n = 3 (A + 2 Dg)
+    const V cp = V(0.0) - h[1] * vfma(V(2.0), ax, dg);      // eps: n = -3 (2 A + Dg)
+    const V cqx = h[2] * vfma(V(-2.0), d13, d57 + d86);     // q_x: -2 d13 + d57 + d86
+    const V cqy = h[2] * vfma(V(-2.0), d24, d57 - d86);     // q_y: -2 d24 + d57 - d86
+    const V cxx = h[3] * (s13 - s24), cxy = h[3] * (s57 - s68);  // p_xx, p_xy
+    const V P = vfma(V(2.0), cp, ce), Q = V(0.0) - vfma(V(2.0), ce, cp);
+    const V P1 = P - cxx, P2 = P + cxx, Q1 = Q - cxy, Q2 = Q + cxy;
+    const V qs = cqx + cqy, qd = cqx - cqy;
+    fs[1] = fs[1] + vfma(V(2.0), cqx, P1);
+    fs[3] = fs[3] + vfma(V(-2.0), cqx, P1);
+    fs[2] = fs[2] + vfma(V(2.0), cqy, P2);
+    fs[4] = fs[4] + vfma(V(-2.0), cqy, P2);
+    fs[5] = fs[5] + (Q1 - qs);
+    fs[7] = fs[7] + (Q1 + qs);
+    fs[6] = fs[6] + (Q2 + qd);
+    fs[8] = fs[8] + (Q2 - qd);
+}
+
 // Shifted-velocity BGK collision of Eq. (be) for one species s at one site (or
 // a pair of sites).
 //   F_s    = -psi_s (G^a S1 + G^r S2) - (G_AB/rho0) rho_s X       (Eq. (FFF))
@@ -446,10 +485,15 @@ __device__ inline Sums<V> stencil_sums(const V d[12], const V e[4])
 // *Fx, *Fy receive F_s (for the force-corrected velocity of the observables).
 // UNIT: tau = 1 (omega = 1, the paper's choice for all its runs), where the BGK
 // update is f*_i = f^eq_i exactly and f_i only enters through the moments.
-template <class V, bool UNIT = false>
+// MRT: the multiple-relaxation-time collision, the BGK one corrected by
+// mrt_delta with the species' coefficients h[4] (before the rest population
+// closes the mass).
+template <class V, bool UNIT = false, bool MRT = false>
 __device__ inline void collide_species(const V f[9], V rho_s, V psi_s, V ux, V uy, V ax, const Sums<V>& sm, V ga,
-                                       V gr, V gx, V tau, V ntau, V omega, V fs[9], V* Fx, V* Fy)
+                                       V gr, V gx, V tau, V ntau, V omega, V fs[9], V* Fx, V* Fy,
+                                       const V* h = nullptr)
 {
+    static_assert(!(UNIT && MRT), "the multiple-relaxation-time collision takes the general update");
     const V Gx = vfma(gr, sm.s2x, ga * sm.s1x);
     const V Gy = vfma(gr, sm.s2y, ga * sm.s1y);
     *Fx = rho_s * (ax - gx * sm.xx) - psi_s * Gx;
@@ -466,7 +510,16 @@ __device__ inline void collide_species(const V f[9], V rho_s, V psi_s, V ux, V u
     const V cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
     const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
     constexpr bool exact_close = sizeof(typename LaneScalar<V>::type) == 4;
-    V dsum = V(0.0);
+    V dsum = V(0.0), d[9];
+    auto close = [&](int k) {
+        const int i = lo[k], j = hi[k];
+        if constexpr (exact_close) {
+            const V dk = (f[i] - fs[i]) + (f[j] - fs[j]);
+            dsum = k == 0 ? dk : dsum + dk;
+        } else {
+            dsum = k == 0 ? fs[i] + fs[j] : dsum + (fs[i] + fs[j]);
+        }
+    };
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const V a = (k < 2 ? wr1 : wr5) * vfma(V(4.5) * cu[k], cu[k], base);
@@ -476,15 +529,17 @@ __device__ inline void collide_species(const V f[9], V rho_s, V psi_s, V ux, V u
             fs[i] = a + b;
             fs[j] = a - b;
         } else {
-            fs[i] = vfma(omega, (a + b) - f[i], f[i]);
-            fs[j] = vfma(omega, (a - b) - f[j], f[j]);
+            d[i] = (a + b) - f[i];
+            d[j] = (a - b) - f[j];
+            fs[i] = vfma(omega, d[i], f[i]);
+            fs[j] = vfma(omega, d[j], f[j]);
         }
-        if constexpr (exact_close) {
-            const V dk = (f[i] - fs[i]) + (f[j] - fs[j]);
-            dsum = k == 0 ? dk : dsum + dk;
-        } else {
-            dsum = k == 0 ? fs[i] + fs[j] : dsum + (fs[i] + fs[j]);
-        }
+        if constexpr (!MRT) close(k);
+    }
+    if constexpr (MRT) {
+        mrt_delta(d, h, fs);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) close(k);
     }
     fs[0] = exact_close ? f[0] + dsum : rho_s - dsum;
 }
@@ -498,11 +553,13 @@ __device__ inline void collide_species(const V f[9], V rho_s, V psi_s, V ux, V u
 // carry equal weights).
 // With scale != 1 the populations are scale * g (FP16 storage with stochastic
 // rounding) and so are the results; rho_s, psi_s, u and the forces are not scaled.
-template <class V, bool UNIT = false>
+// MRT as in collide_species (g - g^eq = f - f^eq, so the correction is the same).
+template <class V, bool UNIT = false, bool MRT = false>
 __device__ inline void collide_species_shifted(const V g[9], V rho_s, V rho_bar, V psi_s, V ux, V uy, V ax,
                                                const Sums<V>& sm, V ga, V gr, V gx, V tau, V ntau, V omega,
-                                               V gs[9], V* Fx, V* Fy, V scale)
+                                               V gs[9], V* Fx, V* Fy, V scale, const V* h = nullptr)
 {
+    static_assert(!(UNIT && MRT), "the multiple-relaxation-time collision takes the general update");
     const V Gx = vfma(gr, sm.s2x, ga * sm.s1x);
     const V Gy = vfma(gr, sm.s2y, ga * sm.s1y);
     *Fx = rho_s * (ax - gx * sm.xx) - psi_s * Gx;
@@ -517,7 +574,12 @@ __device__ inline void collide_species_shifted(const V g[9], V rho_s, V rho_bar,
     const V tr1 = V(3.0 * q_w(1)) * rs, tr5 = V(3.0 * q_w(5)) * rs;
     const V cu[4] = {usx, usy, usx + usy, usy - usx};  // c.u for i = 1, 2, 5, 6
     const int lo[4] = {1, 2, 5, 6}, hi[4] = {3, 4, 7, 8};
-    V dsum = V(0.0);
+    V dsum = V(0.0), d[9];
+    auto close = [&](int k) {
+        const int i = lo[k], j = hi[k];
+        const V dk = (g[i] - gs[i]) + (g[j] - gs[j]);
+        dsum = k == 0 ? dk : dsum + dk;
+    };
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const V a = V(k < 2 ? q_w(1) : q_w(5)) * vfma(rs, vfma(V(4.5) * cu[k], cu[k], nusq), dr);
@@ -527,11 +589,17 @@ __device__ inline void collide_species_shifted(const V g[9], V rho_s, V rho_bar,
             gs[i] = a + b;
             gs[j] = a - b;
         } else {
-            gs[i] = vfma(omega, (a + b) - g[i], g[i]);
-            gs[j] = vfma(omega, (a - b) - g[j], g[j]);
+            d[i] = (a + b) - g[i];
+            d[j] = (a - b) - g[j];
+            gs[i] = vfma(omega, d[i], g[i]);
+            gs[j] = vfma(omega, d[j], g[j]);
         }
-        const V dk = (g[i] - gs[i]) + (g[j] - gs[j]);
-        dsum = k == 0 ? dk : dsum + dk;
+        if constexpr (!MRT) close(k);
+    }
+    if constexpr (MRT) {
+        mrt_delta(d, h, gs);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) close(k);
     }
     gs[0] = g[0] + dsum;
 }
@@ -554,6 +622,7 @@ template <class C> struct Collided {
 // rho_B/tau_B), taken as (j_A + r j_B) / (rho_A + r rho_B), r = tau_A/tau_B
 // (r = 1 gives the one-time velocity exactly), so that the collision conserves
 // the total momentum; the Kolmogorov force is still shared as rho_s / rho.
+// A cell with multiple-relaxation-time rates (p.mrt) takes the MRT collision.
 template <class C>
 __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi[2],
                                     const Sums<C> sm[2], const ParamSet<C>& p, C fx_body, Collided<C>& out)
@@ -568,7 +637,11 @@ __device__ inline void collide_site(const C f[2][9], const C rho[2], const C psi
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const C tau = s ? p.tau_b : p.tau, omega = s ? p.omega_b : p.omega;
-        if (omega == C(1))
+        if (p.mrt)
+            collide_species<C, false, true>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s],
+                                            p.gab_over_rho0, tau, -tau, omega, out.fs[s], &Fx[s], &Fy[s],
+                                            p.mrt_h[s]);
+        else if (omega == C(1))
             collide_species<C, true>(f[s], rho[s], psi[s], ux, uy, ax, sm[s], p.g1[s], p.g2[s], p.gab_over_rho0,
                                      tau, -tau, omega, out.fs[s], &Fx[s], &Fy[s]);
         else

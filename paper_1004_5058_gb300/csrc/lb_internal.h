@@ -33,9 +33,12 @@ void tiled_launch_shape(const TiledPlan* p, int* grid_plain, int* grid_sampled, 
 // Failure injection (tests): the next launch's CTA 0 leaves the copy of its row
 // `row` (counted over its work items) unissued, so the waits for it time out.
 void tiled_inject_skip(TiledPlan* p, uint32_t row);
-// Whether every cell has one relaxation time (the full-width kernels serve only
-// that case; cells with a time per species take the general kernels).
-void tiled_set_one_time(TiledPlan* p, bool one_time);
+// The cells' collision: BGK with one relaxation time for every cell (the
+// full-width kernels serve only that case), BGK with a time per species in some
+// cell (the general kernels), or multiple relaxation times in some cell (the
+// MRT kernels, which then run every cell of the batch).
+enum { TILED_BGK_ONE_TIME = 0, TILED_BGK = 1, TILED_MRT = 2 };
+void tiled_set_collision(TiledPlan* p, int collision);
 
 // auxiliary kernels (lb_aux.cu)
 template <class T>

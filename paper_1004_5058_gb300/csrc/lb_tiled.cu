@@ -61,12 +61,12 @@ struct TiledPlan {
     RowMap rm;  // the rows a step updates
     int elem, bc, tx, ty, depth;
     int n_strips, n_seg;
-    int grid[2][2];  // persistent CTAs: [full-width 0 / general 1][plain 0 / sampled 1]
+    int grid[3][2];  // persistent CTAs: [kernel family FAM_*][plain 0 / sampled 1]
     size_t smem;
     CUtensorMap tm_main[2], tm_halo[2];
     void* f[2];
     uint32_t skip_row = ~0u;  // failure injection for the next launch (tests)
-    bool one_time = true;     // every cell has one relaxation time (the FULL kernels serve it)
+    int collision = TILED_BGK_ONE_TIME;  // the cells' collision (tiled_set_collision)
 };
 
 // Row-slot ring depth: about three rows in flight beyond the three in use.
@@ -263,10 +263,14 @@ __device__ __noinline__ void profile_row_sums(const C* ub, int lane, double* __r
     if (t == 0 && (x0 >> 5) + grp < nbx) prof_part[((long long)cell * nbx + (x0 >> 5) + grp) * nrows + row] = part;
 }
 
-// FULL: every strip is TX columns wide (nx a multiple of TX) and every cell has
-// one relaxation time; otherwise the last strip may be narrower (its extra
-// columns masked) and the species may relax with times of their own.
-template <class T, int TX, bool SAMPLE, bool FULL>
+// Kernel families (FAM):
+//   FAM_FULL  every strip is TX columns wide (nx a multiple of TX) and every cell
+//             has one relaxation time (BGK);
+//   FAM_GEN   the last strip may be narrower (its extra columns masked) and the
+//             species may relax with times of their own (BGK);
+//   FAM_MRT   as FAM_GEN, with the multiple-relaxation-time collision.
+constexpr int FAM_FULL = 0, FAM_GEN = 1, FAM_MRT = 2;
+template <class T, int TX, bool SAMPLE, int FAM>
 __global__ void __launch_bounds__(tiled_threads(TX),
                                   SAMPLE ? (tiled_min_ctas(TX, (int)sizeof(T)) < 3 ? tiled_min_ctas(TX, (int)sizeof(T)) : 3)
                                          : tiled_min_ctas(TX, (int)sizeof(T)))
@@ -282,6 +286,7 @@ __global__ void __launch_bounds__(tiled_threads(TX),
 {
     using C = typename Store<T>::C;
     using V = P2<C>;  // a lane pair: one species at the thread's two sites
+    constexpr bool FULL = FAM == FAM_FULL, MRT = FAM == FAM_MRT;
     // stored populations are scale * g (scale 1 except for the dithered FP16 storage)
     constexpr C scale = C(Store<T>::scale), inv_scale = C(1) / scale;
     constexpr int E = (int)sizeof(T);
@@ -398,6 +403,10 @@ __global__ void __launch_bounds__(tiled_threads(TX),
         // half-warps take the same path (a cell with tau_A = 1 != tau_B runs the
         // general update in both)
         const bool unit_omega = FULL ? pg.omega == C(1) : (pg.omega == C(1) && pg.omega_b == C(1));
+        // multiple-relaxation-time coefficients of this lane's species (mrt_delta)
+        V mh[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mh[q] = V(MRT ? (sp ? pg.mrt_h[1][q] : pg.mrt_h[0][q]) : C(0));
         // the same values as lane pairs
         const V ga = V(sp ? pg.g1[1] : pg.g1[0]), gr = V(sp ? pg.g2[1] : pg.g2[0]), gx = V(p.gab_over_rho0);
         const V tau2 = V(tau_s), ntau2 = V(-tau_s), omega2 = V(omega_s), mix2 = V(mix);
@@ -555,7 +564,13 @@ __global__ void __launch_bounds__(tiled_threads(TX),
             if (act) bad |= !(rho_t.a() > C(0) && rho_t.a() <= std::numeric_limits<C>::max() && rho_t.b() > C(0) &&
                               rho_t.b() <= std::numeric_limits<C>::max());
             V fs[9], Fx, Fy;
-            if constexpr (Store<T>::shifted) {
+            if constexpr (MRT && Store<T>::shifted) {
+                collide_species_shifted<V, false, true>(f, rho_s, rho_bar2, v[2][1], ux, uy, ax, sm, ga, gr, gx,
+                                                        tau2, ntau2, omega2, fs, &Fx, &Fy, V(scale), mh);
+            } else if constexpr (MRT) {
+                collide_species<V, false, true>(f, rho_s, v[2][1], ux, uy, ax, sm, ga, gr, gx, tau2, ntau2, omega2,
+                                                fs, &Fx, &Fy, mh);
+            } else if constexpr (Store<T>::shifted) {
                 if (unit_omega)
                     collide_species_shifted<V, true>(f, rho_s, rho_bar2, v[2][1], ux, uy, ax, sm, ga, gr, gx, tau2,
                                                      ntau2, omega2, fs, &Fx, &Fy, V(scale));
@@ -751,35 +766,48 @@ bool tiled_supported(const Geom& g, int elem, int tile_x, int tile_y)
 
 int tiled_partials_nbx(const Geom& g, int) { return (g.nx + 31) / 32; }
 
-template <class T, int TX>
-static const void* kernel_ptr(bool sample, bool full)
+template <class T, int TX, int FAM>
+static const void* kernel_ptr(bool sample)
 {
-    if (full)
-        return sample ? reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, true, true>)
-                      : reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, false, true>);
-    return sample ? reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, true, false>)
-                  : reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, false, false>);
+    return sample ? reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, true, FAM>)
+                  : reinterpret_cast<const void*>(&tiled_step_kernel<T, TX, false, FAM>);
+}
+
+template <class T, int TX>
+static const void* kernel_ptr(bool sample, int fam)
+{
+    return fam == FAM_FULL ? kernel_ptr<T, TX, FAM_FULL>(sample)
+         : fam == FAM_GEN  ? kernel_ptr<T, TX, FAM_GEN>(sample)
+                           : kernel_ptr<T, TX, FAM_MRT>(sample);
 }
 
 template <class T>
-static const void* pick(int tx, bool sample, bool full)
+static const void* pick(int tx, bool sample, int fam)
 {
     switch (tx) {
-    case 32: return kernel_ptr<T, 32>(sample, full);
-    case 64: return kernel_ptr<T, 64>(sample, full);
-    case 128: return kernel_ptr<T, 128>(sample, full);
-    default: return kernel_ptr<T, 256>(sample, full);
+    case 32: return kernel_ptr<T, 32>(sample, fam);
+    case 64: return kernel_ptr<T, 64>(sample, fam);
+    case 128: return kernel_ptr<T, 128>(sample, fam);
+    default: return kernel_ptr<T, 256>(sample, fam);
     }
 }
 
-static const void* pick_any(int prec, int tx, bool sample, bool full)
+static const void* pick_any(int prec, int tx, bool sample, int fam)
 {
     switch (prec) {
-    case LB_FP32: return pick<float>(tx, sample, full);
-    case LB_FP64: return pick<double>(tx, sample, full);
-    case LB_FP16_SHIFTED_SR: return pick<half_sr>(tx, sample, full);
-    default: return pick<__half>(tx, sample, full);
+    case LB_FP32: return pick<float>(tx, sample, fam);
+    case LB_FP64: return pick<double>(tx, sample, fam);
+    case LB_FP16_SHIFTED_SR: return pick<half_sr>(tx, sample, fam);
+    default: return pick<__half>(tx, sample, fam);
     }
+}
+
+// The family a launch runs: the full-width one when the strips are whole and
+// every cell has one relaxation time and BGK, else the general or MRT one.
+static int launch_family(const TiledPlan* p)
+{
+    if (p->collision == TILED_MRT) return FAM_MRT;
+    return p->g.nx % p->tx == 0 && p->collision == TILED_BGK_ONE_TIME ? FAM_FULL : FAM_GEN;
 }
 
 static bool encode(CUtensorMap* m, void* base, const Geom& g, int elem, int box_x)
@@ -830,17 +858,17 @@ TiledPlan* tiled_create(const Geom& g, const RowMap& rm, int prec, int elem, int
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // occupancy of each kernel: the full-width family (nx a multiple of the tile,
-    // one relaxation time) and the general one, each plain and sampled; which
-    // family runs depends on the cells' relaxation times, which lb_load may
-    // change, so both are prepared.  Plain and sampled launches of a family share
-    // the work items (the segment height) but each runs as many persistent CTAs
-    // as fit (the sampled variant holds more registers)
+    // one relaxation time), the general one and the MRT one, each plain and
+    // sampled; which family runs depends on the cells' collision, which lb_load
+    // may change, so all are prepared.  Plain and sampled launches of a family
+    // share the work items (the segment height) but each runs as many persistent
+    // CTAs as fit (the sampled variant holds more registers)
     const bool full_ok = g.nx % tile_x == 0;
-    int occ[2][2] = {{0, 0}, {0, 0}};
-    for (int s = 0; s < 4; ++s) {
-        const int fam = (s & 2) ? 1 : 0, smp = s & 1;
-        if (fam == 0 && !full_ok) continue;
-        const void* k = pick_any(prec, tile_x, smp != 0, fam == 0);
+    int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int s = 0; s < 6; ++s) {
+        const int fam = s >> 1, smp = s & 1;
+        if (fam == FAM_FULL && !full_ok) continue;
+        const void* k = pick_any(prec, tile_x, smp != 0, fam);
         // the whole unified L1/shared array as shared memory: the CTAs' rings
         // are what sets how many fit on an SM
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess ||
@@ -865,7 +893,7 @@ TiledPlan* tiled_create(const Geom& g, const RowMap& rm, int prec, int elem, int
     if (p->ty <= 0) p->ty = pick_segment_rows(g, rm.nown, tile_x, slots);
     p->n_seg = (rm.nown + p->ty - 1) / p->ty;
     const long long items = (long long)p->n_strips * p->n_seg * g.n_cells;
-    for (int fam = 0; fam < 2; ++fam)
+    for (int fam = 0; fam < 3; ++fam)
         for (int smp = 0; smp < 2; ++smp)
             p->grid[fam][smp] = occ[fam][smp] > 0 ? (int)std::min(items, (long long)sms * occ[fam][smp]) : 0;
     return p;
@@ -875,7 +903,7 @@ void tiled_destroy(TiledPlan* p) { delete p; }
 
 void tiled_inject_skip(TiledPlan* p, uint32_t row) { p->skip_row = row; }
 
-void tiled_set_one_time(TiledPlan* p, bool one_time) { p->one_time = one_time; }
+void tiled_set_collision(TiledPlan* p, int collision) { p->collision = collision; }
 
 void tiled_tiles(const TiledPlan* p, int* tx, int* ty)
 {
@@ -885,7 +913,7 @@ void tiled_tiles(const TiledPlan* p, int* tx, int* ty)
 
 void tiled_launch_shape(const TiledPlan* p, int* grid_plain, int* grid_sampled, int* threads, int* smem)
 {
-    const int fam = (p->g.nx % p->tx == 0 && p->one_time) ? 0 : 1;
+    const int fam = launch_family(p);
     if (grid_plain) *grid_plain = p->grid[fam][0];
     if (grid_sampled) *grid_sampled = p->grid[fam][1];
     if (threads) *threads = tiled_threads(p->tx);
@@ -897,8 +925,8 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
                               double* wall_part, unsigned* err, cudaStream_t st, int* n_launches)
 {
     T* dst = reinterpret_cast<T*>(p->f[1 - src]);
-    const bool full = p->g.nx % p->tx == 0 && p->one_time;
-    const void* k = pick<T>(p->tx, sample, full);
+    const int fam = launch_family(p);
+    const void* k = pick<T>(p->tx, sample, fam);
     Geom g = p->g;
     RowMap rm = p->rm;
     int bc = p->bc, ty = p->ty, ns = p->n_strips, nseg = p->n_seg;
@@ -907,7 +935,7 @@ cudaError_t launch_tiled_step(TiledPlan* p, int src, const CellDev* cells, bool 
     void* args[] = {(void*)&p->tm_main[src], (void*)&p->tm_halo[src], (void*)&dst, (void*)&g, (void*)&bc,
                     (void*)&rm, (void*)&ty, (void*)&ns, (void*)&nseg, (void*)&cells, (void*)&prof_part,
                     (void*)&wall_part, (void*)&err, (void*)&skip};
-    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid[full ? 0 : 1][sample ? 1 : 0]), dim3(tiled_threads(p->tx)), args,
+    cudaError_t e = cudaLaunchKernel(k, dim3(p->grid[fam][sample ? 1 : 0]), dim3(tiled_threads(p->tx)), args,
                                      p->smem, st);
     *n_launches += 1;
     return e;

@@ -34,7 +34,8 @@ def _stream_ptr(stream) -> Optional[int]:
 def cell_struct(c: CellParams) -> L.lb_cell_params:
     return L.lb_cell_params(c.nx, c.ny, c.tau, c.rho0, c.g_aa1, c.g_aa2, c.g_bb1, c.g_bb2, c.g_ab,
                             c.u_wall, getattr(c, "f0", 0.0), c.rho_bar_a, c.rho_bar_b, c.bc,
-                            getattr(c, "tau_b", 0.0))
+                            getattr(c, "tau_b", 0.0), getattr(c, "s_e", 0.0), getattr(c, "s_eps", 0.0),
+                            getattr(c, "s_q", 0.0), getattr(c, "s_nu", 0.0))
 
 
 class Lattice:

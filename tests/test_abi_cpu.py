@@ -37,7 +37,12 @@ def test_null_and_invalid_arguments_rejected_before_device_work(lib):
     cell.tau, cell.tau_b = 1.0, 0.5
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID  # tau_B = 1/2
     assert b"tau_b" in lib.lb_last_error(None)
-    cell.tau_b, cell.nx = 0.0, 4
+    cell.tau_b = 0.0
+    for rate in (2.0, -0.1, float("nan")):  # multiple-relaxation-time rates live in (0, 2); 0 is 1/tau
+        cell.s_q = rate
+        assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID
+        assert b"multiple-relaxation-time rate" in lib.lb_last_error(None)
+    cell.s_q, cell.nx = 0.0, 4
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID  # nx < 5
     cell.nx, cell.bc = 64, 7
     assert lib.lb_create(C.byref(cell), 1, 0, None, C.byref(h)) == L.LB_ERR_INVALID

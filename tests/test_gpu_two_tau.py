@@ -174,12 +174,13 @@ def test_checkpoint_carries_tau_b_and_reads_version_1(tmp_path):
         b.load(path).step(15)
         assert np.array_equal(b.get_populations(), fa)
 
-    # the same file as version 1: the cell records without tau_b
+    # the same file as version 1: the cell records without tau_b (and without
+    # the multiple-relaxation-time rates of version 3)
     raw = path.read_bytes()
-    assert struct.unpack_from("<I", raw, 8)[0] == 2
+    assert struct.unpack_from("<I", raw, 8)[0] == 3
     n_cells = struct.unpack_from("<i", raw, 16)[0]
     payload = raw[128:]
-    payload_v1 = b"".join(payload[c * 120:c * 120 + 112] for c in range(n_cells)) + payload[n_cells * 120:]
+    payload_v1 = b"".join(payload[c * 152:c * 152 + 112] for c in range(n_cells)) + payload[n_cells * 152:]
     head = bytearray(raw[:128])
     struct.pack_into("<I", head, 8, 1)
     struct.pack_into("<QQ", head, 72, len(payload_v1), fnv1a64(payload_v1))
