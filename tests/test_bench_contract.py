@@ -112,3 +112,8 @@ def test_traffic_record_matches_the_kernel_sources():
     two = bench.committed_traffic("fp32", 1024, 1024, 8, two_time=True)
     assert two == (rec["fp32_two_time"]["dram_bytes_per_launch"] if "fp32_two_time" in rec else None)
     assert bench.committed_traffic("fp64", 1024, 1024, 8, two_time=True) is None
+    # the multiple-relaxation-time kernel moves the same bytes
+    mrt = bench.committed_traffic("fp32", 1024, 1024, 8, mrt=True)
+    assert mrt == (rec["fp32_mrt"]["dram_bytes_per_launch"] if "fp32_mrt" in rec else None)
+    if mrt is not None:
+        assert 0.9 * 144 < mrt / (8 * 1024 * 1024) < 1.1 * 144
