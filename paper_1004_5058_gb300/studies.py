@@ -378,6 +378,46 @@ def two_time_flow_curve(L: int = 256, steps: int = 500000, every: int = 50, n_sp
     return out
 
 
+MRT_CONFIGS = (("BGK, G_AB 0.30", 0.30, {}), ("MRT s_nu 1.6, G_AB 0.30", 0.30, {"s_nu": 1.6}),
+               ("BGK, G_AB 0.405", 0.405, {}), ("MRT s_q 1.2, G_AB 0.405", 0.405, {"s_q": 1.2}))
+
+
+def mrt_flow_curve(L: int = 128, steps: int = 400000, every: int = 50, n_speeds: int = 16, u_lo: float = 1e-5,
+                   u_hi: float = 1e-2, configs=MRT_CONFIGS, precision: str = "fp32", seed: int = 1004):
+    """Couette flow curves with the multiple-relaxation-time collision (a method
+    variant) beside the paper's BGK one, all cells in one batch: per
+    configuration (label, G_AB, rates; tau = 1) n_speeds wall speeds, the second
+    half of the steps sampled.  Reports the Newtonian ratio sigma/S (rho nu),
+    the Herschel-Bulkley fit and the spread of rho_A (the demixing) per
+    configuration.  The default 128^2 cells run 4e5 steps, beyond the viscous
+    time L^2/nu of the least viscous configuration (nu = 1/24)."""
+    speeds = I.log_spaced(u_lo, u_hi, n_speeds)
+    cells = [I.make_cell("paper", nx=L, ny=L, g_ab=g, bc=1, u_wall=u, tau=1.0, **rates)
+             for _, g, rates in configs for u in speeds]
+    ra, rb = I.random_fields(L, L, n_cells=len(cells), seed=seed)
+    ux, uy = I.couette_velocity(L, L, [c.u_wall for c in cells], n_cells=len(cells))
+    with Lattice(cells, precision) as lat:
+        lat.init_fields(ra, rb, ux, uy)
+        kern = lat.autotune()
+        lat.init_fields(ra, rb, ux, uy).set_sampling(steps // 2, every)
+        _, dt = _cuda_time(lambda: lat.step(steps).sync())
+        sigma, S, Sb = lat.shear_stress()
+        rho_a = lat.fields()[0]
+    out = {"L": L, "steps": steps, "cells": len(cells), "precision": precision, "kernel": kern,
+           "seconds": dt, "mlups": len(cells) * L * L * steps / dt / 1e6, "curves": {}}
+    for k, (label, g, rates) in enumerate(configs):
+        sl = slice(k * n_speeds, (k + 1) * n_speeds)
+        s_, r_ = sigma[sl], S[sl]
+        ok = np.isfinite(r_) & (r_ > 0) & np.isfinite(s_) & (s_ > 0)
+        out["curves"][label] = {"g_ab": g, "rates": rates, "u_wall": list(speeds),
+                                "sigma_xy": [float(v) for v in s_], "shear_rate": [float(v) for v in r_],
+                                "shear_bulk": [float(v) for v in Sb[sl]],
+                                "sigma_over_S": [float(a / b) if b != 0 else None for a, b in zip(s_, r_)],
+                                "rho_a_std": [float(np.std(rho_a[c])) for c in range(sl.start, sl.stop)],
+                                "hb_fit": hb_fit(r_[ok], s_[ok]) if ok.sum() >= 3 else None}
+    return out
+
+
 def couette_flow_curve(n: int = 1024, n_speeds: int = 8, steps: int = 200000, every: int = 10, g_ab: float = 0.405,
                        precision: str = "fp32", seed: int = 1004):
     """The benchmark's configuration run to its end: n_speeds Couette cells of
@@ -457,7 +497,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
                                       "flow_curve_long", "couette_1024", "surrogate", "kolmogorov",
-                                      "kolmogorov_rho0", "two_time", "train_rate", "readings"])
+                                      "kolmogorov_rho0", "two_time", "train_rate", "readings", "mrt"])
     ap.add_argument("--batch", type=int, default=10240, help="train_rate: batch size")
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
@@ -476,6 +516,8 @@ def main():
         r = flow_curve(L=128, steps=4000, n_speeds=4) if a.quick else flow_curve(steps=1000000, every=100)
     elif a.study == "two_time":  # relaxation time per species: flow curves for three tau_B
         r = two_time_flow_curve(L=64, steps=4000, n_speeds=4) if a.quick else two_time_flow_curve()
+    elif a.study == "mrt":  # multiple relaxation times beside BGK: Newtonian and demixing flow curves
+        r = mrt_flow_curve(L=32, steps=4000, n_speeds=4) if a.quick else mrt_flow_curve()
     elif a.study == "readings":
         r = (kolmogorov_readings(L=64, steps=4000, u0s=(0.1, 0.3), sweep_rho0s=(0.7, 0.75, 0.8, 0.85))
              if a.quick else kolmogorov_readings())

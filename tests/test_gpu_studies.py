@@ -65,3 +65,15 @@ def test_two_time_flow_curve_small():
     for c in r["curves"].values():
         assert len(c["sigma_xy"]) == 4 and all(finite(v) for v in c["sigma_xy"] + c["shear_rate"])
     assert r["curves"]["0.7"]["sigma_xy"][-1] != r["curves"]["1.5"]["sigma_xy"][-1]
+
+
+def test_mrt_flow_curve_small():
+    """Multiple relaxation times beside BGK in one batch: in the mixed fluid
+    (G_AB = 0.3) the Newtonian ratio sigma/S is rho nu with nu = (1/s_nu - 1/2)/3,
+    a quarter of the BGK value at tau = 1 for s_nu = 1.6 (tau still 1)."""
+    from paper_1004_5058_gb300 import studies
+    r = studies.mrt_flow_curve(L=32, steps=3000, every=10, n_speeds=4)
+    assert set(r["curves"]) == {c[0] for c in studies.MRT_CONFIGS} and r["mlups"] > 0
+    for label, nu in (("BGK, G_AB 0.30", 1 / 6), ("MRT s_nu 1.6, G_AB 0.30", (1 / 1.6 - 0.5) / 3)):
+        for ratio in r["curves"][label]["sigma_over_S"][-2:]:
+            assert ratio == pytest.approx(1.2 * nu, rel=0.05)
