@@ -134,6 +134,28 @@ lb_status lb_create(const lb_cell_params* cells, int n_cells, lb_precision prec,
 lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b,
                          const double* ux, const double* uy);
 
+/* lb_init_fields in two halves, so that the host-to-device copy of the next
+ * run's fields overlaps the time steps of the current one (serving many runs
+ * of one handle back to back; the paper has no counterpart).
+ * lb_stage_fields copies the fields (layout and NULL rules of lb_init_fields)
+ * into the handle's staging buffer on a copy stream of its own and returns
+ * without waiting; the copy starts once the previous lb_init_fields_staged has
+ * read the buffer, and runs beside whatever the handle's stream is doing.  The
+ * host arrays must stay valid and unchanged until the lb_init_fields_staged
+ * that consumes them returns; with page-locked host memory the copy is
+ * asynchronous (pageable memory is copied through a driver bounce buffer and
+ * may make the call wait).  A second lb_stage_fields before
+ * lb_init_fields_staged replaces the staged fields; lb_init_fields discards
+ * them.  The first call allocates the staging buffer.
+ * lb_init_fields_staged waits on the host for the staged copy, then enqueues
+ * f = f^eq of the staged fields on the handle's stream and returns without
+ * synchronising; counters and time averages reset as in lb_init_fields.
+ * Errors: LB_ERR_INVALID (rho_a or rho_b NULL), LB_ERR_STATE (nothing staged),
+ * LB_ERR_NOMEM, LB_ERR_CUDA. */
+lb_status lb_stage_fields(lb_handle* h, const double* rho_a, const double* rho_b,
+                          const double* ux, const double* uy);
+lb_status lb_init_fields_staged(lb_handle* h);
+
 /* Loads populations from host memory: f [n_cells][2][9][ny][nx] float64
  * (species A then B, D2Q9 order 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
  * 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)).  Rounded to the storage precision.

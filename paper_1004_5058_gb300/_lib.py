@@ -44,6 +44,8 @@ _F = C.POINTER(C.c_float)
 SIGNATURES = {
     "lb_create": (C.c_int, [C.POINTER(lb_cell_params), C.c_int, C.c_int, C.c_void_p, C.POINTER(_H)]),
     "lb_init_fields": (C.c_int, [_H, _D, _D, _D, _D]),
+    "lb_stage_fields": (C.c_int, [_H, _D, _D, _D, _D]),
+    "lb_init_fields_staged": (C.c_int, [_H]),
     "lb_set_populations": (C.c_int, [_H, _D]),
     "lb_get_populations": (C.c_int, [_H, _D]),
     "lb_step": (C.c_int, [_H, C.c_longlong]),

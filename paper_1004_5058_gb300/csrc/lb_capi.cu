@@ -56,6 +56,10 @@ struct lb_handle {
     double* red_part = nullptr;
     double* red_out = nullptr;
     double* staging = nullptr;         // [cell][4][ny][nx] float64
+    cudaStream_t copy_stream = nullptr;  // lb_stage_fields' copies (created on first use)
+    cudaEvent_t staged = nullptr;        // the last staged copy is complete
+    cudaEvent_t staging_read = nullptr;  // the last equilibrium launch has read the staging buffer
+    bool staged_pending = false;         // fields staged and not yet consumed
     long long t = 0, start = 0, every = 0, n_samples = 0;
     bool initialised = false;
     bool faulted = false;
@@ -122,6 +126,12 @@ static void release(lb_handle* h)
     cudaFree(h->staging);
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->batch_done) cudaEventDestroy(h->batch_done);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+    }
+    if (h->staged) cudaEventDestroy(h->staged);
+    if (h->staging_read) cudaEventDestroy(h->staging_read);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     cudaSetDevice(prev);
     delete h;
@@ -553,6 +563,10 @@ lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b,
     CK(h, cudaSetDevice(h->device));
     const size_t n = (size_t)h->nx * h->ny;
     if (!h->staging) CK(h, cudaMalloc(&h->staging, sizeof(double) * 4 * n * h->n_cells));
+    if (h->copy_stream) {  // a staged copy in flight writes the same buffer: let it land, then drop it
+        CK(h, cudaStreamSynchronize(h->copy_stream));
+        h->staged_pending = false;
+    }
     const double* src[4] = {rho_a, rho_b, ux, uy};
     for (int a = 0; a < 4; ++a) {
         double* dst = h->staging + a * n;
@@ -573,6 +587,70 @@ lb_status lb_init_fields(lb_handle* h, const double* rho_a, const double* rho_b,
     CK(h, cudaStreamSynchronize(h->stream));
     h->batch_pending = false;
     return LB_OK;
+}
+
+lb_status lb_stage_fields(lb_handle* h, const double* rho_a, const double* rho_b, const double* ux,
+                          const double* uy)
+{
+    Trace trace("lb_stage_fields");
+    if (!h) return LB_ERR_INVALID;
+    if (!rho_a || !rho_b) return fail(h, LB_ERR_INVALID, "lb_stage_fields: rho_a and rho_b are required");
+    CK(h, cudaSetDevice(h->device));
+    const size_t n = (size_t)h->nx * h->ny;
+    if (!h->staging) {
+        cudaError_t e = cudaMalloc(&h->staging, sizeof(double) * 4 * n * h->n_cells);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->staging = nullptr;
+            return fail(h, LB_ERR_NOMEM, "lb_stage_fields: staging buffer: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!h->copy_stream) {
+        CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->staging_read, cudaEventDisableTiming));
+        CK(h, cudaEventRecord(h->staging_read, h->stream));  // nothing has read it yet
+    }
+    // the buffer is free once the last equilibrium launch that reads it has run
+    CK(h, cudaStreamWaitEvent(h->copy_stream, h->staging_read, 0));
+    const double* src[4] = {rho_a, rho_b, ux, uy};
+    for (int a = 0; a < 4; ++a) {
+        double* dst = h->staging + a * n;
+        if (src[a])
+            CK(h, cudaMemcpy2DAsync(dst, 4 * n * sizeof(double), src[a], n * sizeof(double), n * sizeof(double),
+                                    h->n_cells, cudaMemcpyHostToDevice, h->copy_stream));
+        else
+            CK(h, cudaMemset2DAsync(dst, 4 * n * sizeof(double), 0, n * sizeof(double), h->n_cells,
+                                    h->copy_stream));
+    }
+    CK(h, cudaEventRecord(h->staged, h->copy_stream));
+    h->staged_pending = true;
+    return LB_OK;
+}
+
+lb_status lb_init_fields_staged(lb_handle* h)
+{
+    Trace trace("lb_init_fields_staged");
+    if (!h) return LB_ERR_INVALID;
+    if (!h->staged_pending) return fail(h, LB_ERR_STATE, "lb_init_fields_staged: no fields staged (lb_stage_fields)");
+    CK(h, cudaSetDevice(h->device));
+    // the host arrays are free once this returns; an earlier batch's error mirror
+    // lands before the counters below are reset
+    CK(h, cudaEventSynchronize(h->staged));
+    if (h->batch_pending) {
+        CK(h, cudaEventSynchronize(h->batch_done));
+        h->batch_pending = false;
+    }
+    h->staged_pending = false;
+    CK(h, cudaStreamWaitEvent(h->stream, h->staged, 0));
+    CK(h, with_type(h, [&](auto* tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        return launch_equilibrium<T>(h->staging, (T*)fview(h, 0), h->g, h->d_cells, h->stream);
+    }));
+    CK(h, cudaEventRecord(h->staging_read, h->stream));
+    h->launches += 1;
+    h->cur = 0;
+    return reset_counters(h);
 }
 
 lb_status lb_set_populations(lb_handle* h, const double* f)

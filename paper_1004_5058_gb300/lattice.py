@@ -123,6 +123,23 @@ class Lattice:
         self._chk(self.lib.lb_init_fields(self.h, _dp(ra), _dp(rb), _dp(u), _dp(v)))
         return self
 
+    def stage_fields(self, rho_a, rho_b, ux=None, uy=None):
+        """Start the host-to-device copy of the next run's fields on the handle's
+        copy stream (lb_stage_fields) and return; init_fields_staged() then
+        sets f = f^eq from them.  The arrays are held here until then; pass
+        page-locked arrays for an asynchronous copy."""
+        arrs = tuple(self._field(a) for a in (rho_a, rho_b, ux, uy))
+        self._chk(self.lib.lb_stage_fields(self.h, *(_dp(a) for a in arrs)))
+        self._staged_refs = arrs
+        return self
+
+    def init_fields_staged(self):
+        """f = f^eq of the staged fields, enqueued without synchronising
+        (lb_init_fields_staged); counters reset as in init_fields."""
+        self._chk(self.lib.lb_init_fields_staged(self.h))
+        self._staged_refs = None
+        return self
+
     def set_populations(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.n_cells, 2, 9, self.ny, self.nx)
         self._chk(self.lib.lb_set_populations(self.h, _dp(f)))

@@ -72,6 +72,7 @@ def test_gpu_arm_line():
     assert abs(rf["achieved"] / rf["peak"] - rf["frac"]) < 1e-9
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == 4 * 2 * 256 * 256 * 8 and e["d2h_bytes_per_step"] > 0
+    assert e["serial"]["value"] > 0 and e["pipelining"]
     assert d["gpu_launches"] >= 3 * 20
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert set(d["clocks"] or {}) >= {"sm_mhz", "sm_max_mhz", "reasons"} or d["clocks"] is None

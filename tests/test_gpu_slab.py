@@ -133,3 +133,14 @@ def test_slab_errors():
         with pytest.raises(LBError) as e:
             whole.slab_get(LB_SLAB_EDGE_LO, buf.data_ptr())
         assert e.value.status == LB_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("bc,world", [(0, 3), (1, 2)])
+def test_slabs_multiple_relaxation_times_bitwise(bc, world):
+    """The multiple-relaxation-time collision runs in slabs as in the whole cell."""
+    cell, ra, rb, ux, uy = setup(bc)
+    cell.s_e, cell.s_eps, cell.s_q, cell.s_nu = 1.4, 1.1, 1.2, 1.1
+    fields = (ra, rb, ux, uy)
+    whole, _, _ = run_whole(cell, "fp32", fields, 25)
+    got, _, _ = run_slabs(cell, "fp32", fields, 25, world)
+    assert np.array_equal(got, whole)
