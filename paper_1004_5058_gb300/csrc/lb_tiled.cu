@@ -70,9 +70,12 @@ struct TiledPlan {
 };
 
 // Row-slot ring depth: about three rows in flight beyond the three in use.
+// FP64 rows are consumed at the FP64 pipe's pace (a seventh of the FP32 rate),
+// so one row in flight covers the memory latency, and the smaller ring lets two
+// CTAs share an SM.
 __host__ __device__ constexpr int ring_depth(int tx, int elem)
 {
-    return (6 * al128(18 * tx * elem) + 12 * al128(18 * (16 / elem) * elem) <= 96 * 1024) ? 6 : 5;
+    return elem == 8 ? 4 : (6 * al128(18 * tx * elem) + 12 * al128(18 * (16 / elem) * elem) <= 96 * 1024) ? 6 : 5;
 }
 // Words between the species-A and species-B psi/rho rings, chosen so that a
 // half-warp reading A and the other half reading B hit disjoint banks.
@@ -475,6 +478,13 @@ __global__ void __launch_bounds__(tiled_threads(TX),
         for (int k = 0; k < 4; ++k) {
             ok = wait_row(k) && ok;
             psi_stage_slot((int)((nrow + (uint32_t)k) % (uint32_t)D), k);
+        }
+        if constexpr (D < 5) {
+            // a four-slot ring holds rows 0..3 only: rows 4 and 5 go into the slots of
+            // rows 0 and 1 once every thread has staged those (the loop below waits
+            // for row j + 4 before its own barrier)
+            __syncthreads();
+            if (producer) issue_upto(nrow + 2u + (uint32_t)D);
         }
         int r0 = 0;  // ring row of logical row j (rows j .. j+4 are read by the collision of row j+2)
         // slot and mbarrier phase of logical row j + 4 (global row nrow + j + 4),
