@@ -160,3 +160,29 @@ def test_largest_tiled_cell():
     bg[ny - 40:ny - 14, nx - 40:nx - 14] = bg[0, 0]
     assert np.ptp(bg) == 0.0  # the untouched background is bitwise uniform
     assert abs(mass[0, 0] - (0.6 * nx * ny + bump.sum())) <= 1e-6 * 0.6 * nx * ny
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp16", 5e-5)])
+def test_bench_batch_8x1024_multiple_relaxation_times(prec, tol):
+    """The bench batch with the multiple-relaxation-time collision (bench.py
+    --mrt 1.4,1.1,1.2,1.1), in the bench's tile: two cells against the oracle
+    after 1 step and one after 10; mass of every cell after 100 steps."""
+    from paper_1004_5058_gb300 import Lattice
+    cells, ra, rb, ux, uy = couette_batch(8, 1024)
+    for c in cells:
+        c.s_e, c.s_eps, c.s_q, c.s_nu = 1.4, 1.1, 1.2, 1.1
+    with Lattice(cells, prec) as lat:
+        lat.init_fields(ra, rb, ux, uy).set_kernel("tiled", 128, 147)
+        lat.step(1)
+        a1, b1, u1, _ = lat.fields()
+        lat.step(9)
+        a10, _, u10, _ = lat.fields()
+        lat.step(90)
+        mass, _ = lat.reductions()
+    for c in (0, 7):
+        oa, ob, ou, _ = oracle_fields(cells[c], ra[c], rb[c], ux[c], uy[c], 1)
+        assert max_abs(a1[c], oa) <= tol and max_abs(b1[c], ob) <= tol and max_abs(u1[c], ou) <= tol
+    oa, _, ou, _ = oracle_fields(cells[3], ra[3], rb[3], ux[3], uy[3], 10)
+    assert max_abs(a10[3], oa) <= 3 * tol and max_abs(u10[3], ou) <= 3 * tol
+    m0 = ra.reshape(8, -1).sum(axis=1)
+    assert np.all(np.abs(mass[:, 0] - m0) / m0 <= (1e-6 if prec == "fp32" else 1e-4))
