@@ -659,3 +659,30 @@ def test_mrt_shear_viscosity_is_set_by_s_nu(tau, s_nu):
     rate = -math.log(amp() / a0) / (r.t - t0)
     assert rate == pytest.approx((1 / s_nu - 0.5) / 3 * k * k, rel=2e-2)
     assert abs(rate / ((tau - 0.5) / 3 * k * k) - 1) > 0.5
+
+
+@pytest.mark.parametrize("tau,rates", [(1.0, dict(s_nu=1.6, s_q=1.1, s_e=1.3)), (0.8, dict(s_nu=0.9, s_eps=1.5))])
+def test_mrt_couette_linear_profile_and_stress(tau, rates):
+    """G = 0 Couette with multiple relaxation times: halfway bounce-back gives
+    the linear profile, and the wall stress is rho nu 2U/ny with the viscosity of
+    the stress moments, nu = (1/s_nu - 1/2)/3 (tau only shifts the force, and
+    there is none here).  Unlike BGK, where the linear profile is exact, rates
+    that differ from 1/tau leave a relative deviation of order U^2 near the walls
+    (the u^2 terms of the e and p_xx equilibria relax at their own rates: 1.4e-10
+    at U = 1e-4, 1.4e-8 at 1e-3, 1.4e-6 at 1e-2 for s_nu = 0.9, tau = 0.8), so the
+    wall speed is small here."""
+    nx, ny, U = 4, 16, 1e-4
+    c = I.make_cell("ideal", nx=nx, ny=ny, tau=tau, bc=1, u_wall=U, **rates)
+    ra = np.full((ny, nx), 0.6)
+    rb = np.full((ny, nx), 0.6)
+    ux, uy = I.couette_velocity(nx, ny, U)
+    nu = (1.0 / rates["s_nu"] - 0.5) / 3.0
+    n_steps = int(40 * ny * ny / (nu * math.pi ** 2))
+    r = lb.Run(c, ra, rb, ux[0], uy[0])
+    r.set_sampling(n_steps - 100, 10)
+    r.step(n_steps)
+    sigma, S, _, ub = r.shear()
+    y = np.arange(ny)
+    np.testing.assert_allclose(ub, U * (2 * (y + 0.5) / ny - 1), rtol=0, atol=1e-8 * U)
+    assert S == pytest.approx(2 * U / ny, rel=1e-8)
+    assert sigma == pytest.approx(1.2 * nu * 2 * U / ny, rel=1e-8)
