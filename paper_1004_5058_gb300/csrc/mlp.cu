@@ -1,15 +1,15 @@
-// Flow-curve surrogate kernels (include/lbhb_mlp.h): BF16 tensor-core GEMMs
-// with FP32 accumulation (mma.sync m16n8k16) and fused epilogues for the
-// forward pass, the backward pass and Adam on FP32 master weights.
+// Flow-curve surrogate kernels (include/lbhb_mlp.h): BF16 tensor-core products
+// (mma.sync m16n8k16) with FP32 accumulation for the forward pass, serving,
+// and a training step (forward, loss, backward) fused into one kernel per slab
+// of the batch, followed by an ordered reduction with Adam on FP32 master
+// weights.
 //
-// Every product is written as C[m][n] = sum_k A[m][k] B[n][k] with both operands
-// K-contiguous ("NT"): the forward pass multiplies activations [batch][in] by
-// weights [out][in]; the backward pass by a transposed weight copy [in][out];
-// the weight gradients multiply transposed activation and gradient copies
-// [features][batch], which the epilogues write alongside the normal layout.
-// Batch rows beyond the live batch are written as zeros, so padded rows and
-// columns never contribute.  Weight gradients use split-K partial sums reduced
-// in a fixed order, so results are reproducible.
+// The layered forward pass (mlp_forward) writes every product as C[m][n] =
+// sum_k A[m][k] B[n][k] with both operands K-contiguous ("NT"): activations
+// [batch][in] times weights [out][in], with fused bias/tanh epilogues.  Batch
+// rows beyond the live batch are written as zeros, so padded rows and columns
+// never contribute.  Gradients are sums of per-CTA partials reduced in a fixed
+// order, so results are reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -43,16 +43,14 @@ __host__ __device__ constexpr LayerDef layer_def(int l)
            : l == 2 ? LayerDef{HID, HID, HID, HID, OFF_W3, OFF_B3}
                     : LayerDef{HID, HID, NOUT, NOUTP, OFF_W4, OFF_B4};
 }
-constexpr int KSPLIT = 256;  // batch rows per split-K partial of a weight gradient
 
-enum { EPI_TANH = 0, EPI_OUT = 1, EPI_DTANH = 2, EPI_PARTIAL = 3 };
+enum { EPI_TANH = 0, EPI_OUT = 1 };
 
 struct Epi {
     const float* bias;  // EPI_TANH, EPI_OUT: [N]
-    bf16* out_b;        // EPI_TANH, EPI_DTANH: [rows][ld_out]
-    bf16* out_t;        // EPI_TANH, EPI_DTANH: [N][ld_t] (transposed copy)
-    float* out_f;       // EPI_OUT: [rows][ld_out]; EPI_PARTIAL: [split][M][N]
-    const bf16* hprev;  // EPI_DTANH: activation whose tanh derivative is applied, [rows][ld_out]
+    bf16* out_b;        // EPI_TANH: [rows][ld_out]
+    bf16* out_t;        // EPI_TANH: [N][ld_t] (transposed copy)
+    float* out_f;       // EPI_OUT: [rows][ld_out]
     int ld_out, ld_t;
     int rows_live;      // batch rows that hold data; later rows are written as zero
     int rows_buf;       // rows the buffers have
@@ -137,20 +135,12 @@ __global__ void __launch_bounds__(128) gemm_nt(const bf16* __restrict__ A, int l
                 const int col = n0 + wn * 32 + ni * 8 + 2 * t4 + (r & 1);
                 if (col >= N) continue;
                 float v = acc[mi][ni][r];
-                if (EPI == EPI_PARTIAL) {
-                    if (row < M) ep.out_f[((long long)blockIdx.z * M + row) * N + col] = v;
-                    continue;
-                }
                 if (row >= ep.rows_buf) continue;
                 const bool live = row < ep.rows_live;
-                if (EPI == EPI_TANH) {
+                if (EPI == EPI_TANH)
                     v = live ? tanhf(v + ep.bias[col]) : 0.f;
-                } else if (EPI == EPI_OUT) {
+                else
                     v = live ? v + ep.bias[col] : 0.f;
-                } else {  // EPI_DTANH
-                    const float h = __bfloat162float(ep.hprev[(long long)row * ep.ld_out + col]);
-                    v = live ? v * (1.f - h * h) : 0.f;
-                }
                 if (EPI == EPI_OUT) {
                     ep.out_f[(long long)row * ep.ld_out + col] = v;
                 } else {
@@ -179,101 +169,6 @@ __global__ void normalise_kernel(const float* __restrict__ x, int B, int Bbuf, c
 __device__ __forceinline__ float bce_logits(float z, float y)
 {
     return fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
-}
-
-// dL/dy for y = (stress/scale, logit); per-block loss partials (FP64).
-__global__ void loss_grad_kernel(const float* __restrict__ out, const float* __restrict__ target,
-                                 const float* __restrict__ label, int B, int Bbuf, float inv_scale, float lam,
-                                 bf16* __restrict__ d, bf16* __restrict__ dt, double* __restrict__ part)
-{
-    __shared__ double red[256];
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    double l = 0.0;
-    if (b < Bbuf) {
-        float d0 = 0.f, d1 = 0.f;
-        if (b < B) {
-            const float y0 = out[(long long)b * NOUTP + 0], y1 = out[(long long)b * NOUTP + 1];
-            const float t = target[b] * inv_scale, lab = label[b];
-            const float e = y0 - t;
-            l = (double)(e * e) + (double)lam * (double)bce_logits(y1, lab);
-            d0 = 2.f * e / (float)B;
-            const float sg = 1.f / (1.f + expf(-y1));
-            d1 = lam * (sg - lab) / (float)B;
-        }
-        for (int c = 0; c < NOUTP; ++c) {
-            const float v = c == 0 ? d0 : (c == 1 ? d1 : 0.f);
-            const bf16 hv = __float2bfloat16_rn(v);
-            d[(long long)b * NOUTP + c] = hv;
-            dt[(long long)c * Bbuf + b] = hv;
-        }
-    }
-    red[threadIdx.x] = l;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
-
-__global__ void loss_finish_kernel(const double* __restrict__ part, int n, int B, float* __restrict__ loss_f,
-                                   double* __restrict__ loss_d)
-{
-    if (threadIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    s /= (double)B;
-    if (loss_f) *loss_f = (float)s;
-    if (loss_d) *loss_d = s;
-}
-
-// grad[offW + o*in + i] = sum_s part[s][o][i] for the live block (o < out, i < in).
-__global__ void reduce_wgrad_kernel(const float* __restrict__ part, int S, int Mo, int Ni, int out, int in,
-                                    float* __restrict__ grad)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= out * in) return;
-    const int o = k / in, i = k % in;
-    float s = 0.f;
-    for (int p = 0; p < S; ++p) s += part[((long long)p * Mo + o) * Ni + i];
-    grad[k] = s;
-}
-
-// grad_b[o] = sum over live batch rows of d[o][b] (transposed gradient rows): a
-// block of BIAS_THREADS per output o, each thread a strided part of the batch,
-// then a fixed-shape tree (the same order every call).
-constexpr int BIAS_THREADS = 256;
-__global__ void __launch_bounds__(BIAS_THREADS) bias_grad_kernel(const bf16* __restrict__ dt, int Bbuf, int B,
-                                                                 float* __restrict__ grad)
-{
-    const int o = blockIdx.x;
-    float s = 0.f;
-    for (int b = threadIdx.x; b < B; b += BIAS_THREADS) s += __bfloat162float(dt[(long long)o * Bbuf + b]);
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) s += __shfl_down_sync(0xffffffffu, s, w);
-    __shared__ float warp_sum[BIAS_THREADS / 32];
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-#pragma unroll
-        for (int k = 0; k < BIAS_THREADS / 32; ++k) t += warp_sum[k];
-        grad[o] = t;
-    }
-}
-
-__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                            float c1, float c2)
-{
-    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const float gk = g[k];
-    const float mk = b1 * m[k] + (1.f - b1) * gk;
-    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
-    m[k] = mk;
-    v[k] = vk;
-    p[k] -= lr * (mk * c1) / (sqrtf(vk * c2) + eps);
 }
 
 // FP32 masters -> padded BF16 weights [out_p][in_p], their transposes, padded FP32 biases.
@@ -464,6 +359,349 @@ __global__ void __launch_bounds__(128) serve_fused_kernel(ServeArgs a)
     }
 }
 
+// ------------------------------------------------------------ training --
+// Loss gradient and backpropagation in one kernel: a CTA takes a slab of 64
+// batch rows (each warp 16) through the normalisation, the forward pass, the
+// loss and the backward pass with every activation in shared memory, and adds
+// the slab's contribution to every weight and bias gradient into its own row
+// of FP32 partial sums; grad_finish_kernel then sums the rows in a fixed order
+// (reproducible) and, for a training step, applies Adam and refreshes the BF16
+// weight copies.  The products are the layered kernels': BF16 operands, FP32
+// accumulation, activations and pre-activation gradients rounded to BF16.
+//   forward   H_l = tanh(X_l W_l^T + b_l) (rows past the batch are zero)
+//   loss      (y0 - t)^2 + lam BCE(y1, label), mean over the batch
+//   backward  dW_l = D_l^T X_l, db_l = column sums of D_l,
+//             D_{l-1} = (D_l W_l) * (1 - H_{l-1}^2)
+// The weight gradients multiply two row-major slab buffers along the batch
+// (the contraction index is their row), so both operands are loaded with
+// ldmatrix.trans.  Each pre-activation gradient overwrites, row by row, the
+// activation it was computed from once every warp has used that activation.
+constexpr int TR_ROWS = 64;          // batch rows per slab
+constexpr int TR_LD = HID + 8;       // padded 128-wide rows (activations, weights)
+constexpr int TR_LDZ = KIN + 8;      // padded 16-wide rows (inputs, output gradient)
+constexpr int TR_MAX_CTAS = 304;     // persistent CTAs at most (two per SM), one partial row each
+// inputs, output gradient, three activations and one weight buffer: 90 KB, two CTAs per SM
+constexpr size_t TR_SMEM = sizeof(bf16) * (2 * TR_ROWS * TR_LDZ + 3 * TR_ROWS * TR_LD + HID * TR_LD);
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const bf16* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+
+// A rows x cols BF16 matrix (cols a multiple of 8) into a padded shared buffer.
+__device__ __forceinline__ void stage_matrix(bf16* Ws, const bf16* W, int rows, int cols, int tid)
+{
+    for (int e = tid; e < rows * (cols / 8); e += 128) {
+        const int r = e / (cols / 8), c8 = (e % (cols / 8)) * 8;
+        cp_async16(&Ws[r * TR_LD + c8], W + (long long)r * cols + c8);
+    }
+}
+
+struct TrainArgs {
+    const float *x, *target, *label;
+    int B;
+    const bf16* W[4];   // [out_p][in_p]
+    const bf16* Wt[4];  // [in_p][out_p]
+    const float* bias[4];
+    const float *center, *half;
+    float inv_scale, lam;
+    float* part;        // [gridDim.x][NPARAM] partial gradients
+    double* loss_part;  // [gridDim.x]
+};
+
+// One warp's 16 x N product of its rows of `in` (K wide) with the staged weights
+// Ws [N][K]: acc[n-tile][4], K-steps of 16 in increasing order.
+template <int NT>
+__device__ __forceinline__ void rows_times_weights(float (&acc)[NT][4], const bf16* in, int ld_in, int K,
+                                                   const bf16* Ws, int r0, int g, int t4)
+{
+#pragma unroll
+    for (int ni = 0; ni < NT; ++ni)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[ni][r] = 0.f;
+    for (int ks = 0; ks < K; ks += 16) {
+        const uint32_t a0 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g) * ld_in + ks + 2 * t4]);
+        const uint32_t a1 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g + 8) * ld_in + ks + 2 * t4]);
+        const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g) * ld_in + ks + 2 * t4 + 8]);
+        const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g + 8) * ld_in + ks + 2 * t4 + 8]);
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni) {
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Ws[(ni * 8 + g) * TR_LD + ks + 2 * t4]);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Ws[(ni * 8 + g) * TR_LD + ks + 2 * t4 + 8]);
+            mma_bf16(acc[ni], a0, a1, a2, a3, b0, b1);
+        }
+    }
+}
+
+// A weight-gradient block dW[m0 + 16 MT][n0 + 8 NT] = sum over the slab's 64
+// rows b of D[b][o] X[b][i]: A = D^T and B = X loaded with ldmatrix.trans from
+// the row-major slab buffers (NT even).
+template <int MT, int NT>
+__device__ __forceinline__ void slab_outer(float (&acc)[MT][NT][4], const bf16* D, int ldD, int m0, const bf16* X,
+                                           int ldX, int n0, int lane)
+{
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[mi][ni][r] = 0.f;
+    const int j = lane >> 3, rr = lane & 7;
+#pragma unroll
+    for (int k0 = 0; k0 < TR_ROWS; k0 += 16) {
+        uint32_t a[MT][4];
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi)  // matrices (m 0-7|8-15) x (k 0-7|8-15): a0..a3
+            ldsm_x4_trans(a[mi], D + (k0 + rr + ((j >> 1) & 1) * 8) * ldD + m0 + mi * 16 + (j & 1) * 8);
+#pragma unroll
+        for (int np = 0; np < NT / 2; ++np) {  // two n-tiles: (k 0-7|8-15) x (n 0-7|8-15)
+            uint32_t b[4];
+            ldsm_x4_trans(b, X + (k0 + rr + (j & 1) * 8) * ldX + n0 + np * 16 + (j >> 1) * 8);
+#pragma unroll
+            for (int mi = 0; mi < MT; ++mi) {
+                mma_bf16(acc[mi][2 * np], a[mi][0], a[mi][1], a[mi][2], a[mi][3], b[0], b[1]);
+                mma_bf16(acc[mi][2 * np + 1], a[mi][0], a[mi][1], a[mi][2], a[mi][3], b[2], b[3]);
+            }
+        }
+    }
+}
+
+// Adds (first slab: stores) a weight-gradient block to the CTA's partial row;
+// entries outside the live out x in block are skipped.
+template <int MT, int NT>
+__device__ __forceinline__ void put_wgrad(float* row, const float (&acc)[MT][NT][4], int l, int m0, int n0, int g,
+                                          int t4, bool first)
+{
+    const LayerDef L = layer_def(l);
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int o = m0 + mi * 16 + g + (r >= 2 ? 8 : 0), i = n0 + ni * 8 + 2 * t4 + (r & 1);
+                if (o >= L.out || i >= L.in) continue;
+                float* p = row + L.offW + (long long)o * L.in + i;
+                *p = first ? acc[mi][ni][r] : *p + acc[mi][ni][r];
+            }
+}
+
+// Bias gradient of layer l: column sums of the slab's D (rows in increasing order).
+__device__ __forceinline__ void put_bgrad(float* row, const bf16* D, int ld, int l, int tid, bool first)
+{
+    const LayerDef L = layer_def(l);
+    if (tid >= L.out) return;
+    float s = 0.f;
+    for (int b = 0; b < TR_ROWS; ++b) s += __bfloat162float(D[b * ld + tid]);
+    float* p = row + L.offB + tid;
+    *p = first ? s : *p + s;
+}
+
+// D_{l-1} = (D_l W_l) * (1 - H^2) for the warp's rows, written over H (BF16).
+template <int NT>
+__device__ __forceinline__ void back_rows(const bf16* D, int ldD, int K, const bf16* Wts, bf16* H, int r0, int g,
+                                          int t4, int b0, int B)
+{
+    float acc[NT][4];
+    rows_times_weights<NT>(acc, D, ldD, K, Wts, r0, g, t4);
+#pragma unroll
+    for (int ni = 0; ni < NT; ++ni)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int row = r0 + g + (r >= 2 ? 8 : 0), col = ni * 8 + 2 * t4 + (r & 1);
+            const float h = __bfloat162float(H[row * TR_LD + col]);
+            const float v = b0 + row < B ? acc[ni][r] * (1.f - h * h) : 0.f;
+            H[row * TR_LD + col] = __float2bfloat16_rn(v);
+        }
+}
+
+__global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
+{
+    extern __shared__ __align__(16) unsigned char tr_smem[];
+    bf16* const Zs = reinterpret_cast<bf16*>(tr_smem);        // [64][TR_LDZ] inputs
+    bf16* const D4 = Zs + TR_ROWS * TR_LDZ;                     // [64][TR_LDZ] output gradient
+    bf16* const Hs = D4 + TR_ROWS * TR_LDZ;                     // 3 x [64][TR_LD] activations -> gradients
+    bf16* const Ws = Hs + 3 * TR_ROWS * TR_LD;                // the weights in use
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3, r0 = warp * 16;
+    float* const prow = a.part + (long long)blockIdx.x * NPARAM;
+    __shared__ double loss_w[4];
+    double loss_acc = 0.0;
+    const int n_slabs = (a.B + TR_ROWS - 1) / TR_ROWS;
+    for (int slab = blockIdx.x; slab < n_slabs; slab += gridDim.x) {
+        const bool first = slab == (int)blockIdx.x;
+        const int b0 = slab * TR_ROWS;
+        // weights in use order W1, W2, W3, W4, Wt4, Wt3, Wt2, one at a time (the
+        // other CTA on the SM computes meanwhile)
+        __syncthreads();  // the previous slab is done with the buffers
+        stage_matrix(Ws, a.W[0], HID, KIN, tid);
+        cp_async_commit();
+        for (int e = tid; e < TR_ROWS * KIN; e += 128) {
+            const int r = e / KIN, c = e % KIN, b = b0 + r;
+            float v = 0.f;
+            if (b < a.B && c < NIN) v = (a.x[b * NIN + c] - a.center[c]) / a.half[c];
+            Zs[r * TR_LDZ + c] = __float2bfloat16_rn(v);
+        }
+        // ---- forward
+        for (int l = 0; l < 4; ++l) {
+            cp_async_wait<0>();
+            __syncthreads();  // layer l's weights and inputs visible
+            const bf16* in = l == 0 ? Zs : Hs + (l - 1) * TR_ROWS * TR_LD;
+            const int ld_in = l == 0 ? TR_LDZ : TR_LD, K = l == 0 ? KIN : HID;
+            if (l < 3) {
+                float acc[HID / 8][4];
+                rows_times_weights<HID / 8>(acc, in, ld_in, K, Ws, r0, g, t4);
+                bf16* out = Hs + l * TR_ROWS * TR_LD;
+#pragma unroll
+                for (int ni = 0; ni < HID / 8; ++ni)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int row = r0 + g + (r >= 2 ? 8 : 0), col = ni * 8 + 2 * t4 + (r & 1);
+                        const float v = b0 + row < a.B ? tanhf(acc[ni][r] + a.bias[l][col]) : 0.f;
+                        out[row * TR_LD + col] = __float2bfloat16_rn(v);
+                    }
+            } else {
+                float acc[NOUTP / 8][4];
+                rows_times_weights<NOUTP / 8>(acc, in, ld_in, K, Ws, r0, g, t4);
+                // the loss and its gradient: columns 0 (stress / scale) and 1 (logit) of
+                // n-tile 0 sit with the t4 == 0 lanes
+                for (int e = lane; e < 16 * TR_LDZ; e += 32)
+                    D4[(r0 + e / TR_LDZ) * TR_LDZ + e % TR_LDZ] = __float2bfloat16_rn(0.f);
+                __syncwarp();
+                if (t4 == 0) {
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int row = r0 + g + 8 * h2, b = b0 + row;
+                        if (b >= a.B) continue;
+                        const float y0 = acc[0][2 * h2] + a.bias[3][0], y1 = acc[0][2 * h2 + 1] + a.bias[3][1];
+                        const float t = a.target[b] * a.inv_scale, lab = a.label[b];
+                        const float e = y0 - t;
+                        loss_acc += (double)(e * e) + (double)a.lam * (double)bce_logits(y1, lab);
+                        const float sg = 1.f / (1.f + expf(-y1));
+                        D4[row * TR_LDZ + 0] = __float2bfloat16_rn(2.f * e / (float)a.B);
+                        D4[row * TR_LDZ + 1] = __float2bfloat16_rn(a.lam * (sg - lab) / (float)a.B);
+                    }
+                }
+            }
+            __syncthreads();  // every warp is done with the weights (and, after layer 4, D4 and H3 are complete)
+            if (l < 3)
+                stage_matrix(Ws, a.W[l + 1], layer_def(l + 1).out_p, layer_def(l + 1).in_p, tid);
+            else
+                stage_matrix(Ws, a.Wt[3], HID, NOUTP, tid);  // Wt4 [128][16]
+            cp_async_commit();
+        }
+        // ---- backward, layer 4: dW4 (16 x 128) from D4 and H3, db4
+        bf16* const H1 = Hs;
+        bf16* const H2 = Hs + TR_ROWS * TR_LD;
+        bf16* const H3 = Hs + 2 * TR_ROWS * TR_LD;
+        {
+            float acc[1][4][4];
+            slab_outer<1, 4>(acc, D4, TR_LDZ, 0, H3, TR_LD, warp * 32, lane);
+            put_wgrad<1, 4>(prow, acc, 3, 0, warp * 32, g, t4, first);
+            put_bgrad(prow, D4, TR_LDZ, 3, tid, first);
+        }
+        cp_async_wait<0>();  // Wt4
+        __syncthreads();     // H3 read by every warp's dW4; Wt4 visible
+        back_rows<HID / 8>(D4, TR_LDZ, NOUTP, Ws, H3, r0, g, t4, b0, a.B);  // D3 over H3
+        __syncthreads();  // D3 complete; the weight buffer is free
+        stage_matrix(Ws, a.Wt[2], HID, HID, tid);  // Wt3
+        cp_async_commit();
+        // layer 3: dW3 from D3 and H2, then D2 over H2
+        {
+            float acc[2][HID / 8][4];
+            slab_outer<2, HID / 8>(acc, H3, TR_LD, warp * 32, H2, TR_LD, 0, lane);
+            put_wgrad<2, HID / 8>(prow, acc, 2, warp * 32, 0, g, t4, first);
+            put_bgrad(prow, H3, TR_LD, 2, tid, first);
+        }
+        cp_async_wait<0>();  // Wt3
+        __syncthreads();
+        back_rows<HID / 8>(H3, TR_LD, HID, Ws, H2, r0, g, t4, b0, a.B);  // D2 over H2
+        __syncthreads();
+        stage_matrix(Ws, a.Wt[1], HID, HID, tid);  // Wt2
+        cp_async_commit();
+        // layer 2: dW2 from D2 and H1, then D1 over H1
+        {
+            float acc[2][HID / 8][4];
+            slab_outer<2, HID / 8>(acc, H2, TR_LD, warp * 32, H1, TR_LD, 0, lane);
+            put_wgrad<2, HID / 8>(prow, acc, 1, warp * 32, 0, g, t4, first);
+            put_bgrad(prow, H2, TR_LD, 1, tid, first);
+        }
+        cp_async_wait<0>();  // Wt2
+        __syncthreads();
+        back_rows<HID / 8>(H2, TR_LD, HID, Ws, H1, r0, g, t4, b0, a.B);  // D1 over H1
+        __syncthreads();
+        // layer 1: dW1 (128 x 16) from D1 and the inputs
+        {
+            float acc[2][KIN / 8][4];
+            slab_outer<2, KIN / 8>(acc, H1, TR_LD, warp * 32, Zs, TR_LDZ, 0, lane);
+            put_wgrad<2, KIN / 8>(prow, acc, 0, warp * 32, 0, g, t4, first);
+            put_bgrad(prow, H1, TR_LD, 0, tid, first);
+        }
+    }
+    // the CTA's loss: lane sums, then warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_down_sync(0xffffffffu, loss_acc, o);
+    if (lane == 0) loss_w[warp] = loss_acc;
+    __syncthreads();
+    if (tid == 0) a.loss_part[blockIdx.x] = (loss_w[0] + loss_w[1]) + (loss_w[2] + loss_w[3]);
+}
+
+// Sums the CTAs' partial rows in order.  mode 0: gradient into grad.  mode 1: an
+// Adam step on the FP32 masters p (m, v its moments) and the refreshed BF16
+// weight copies and FP32 biases of that parameter.  Thread 0 of block 0 also
+// finishes the loss (mean over the batch).
+struct FinishArgs {
+    const float* part;
+    const double* loss_part;
+    int n_rows, B;
+    float* grad;
+    float *p, *m, *v;
+    float lr, b1, b2, eps, c1, c2;
+    bf16* W[4];
+    bf16* Wt[4];
+    float* bias[4];
+    float* loss_f;
+    double* loss_d;
+};
+
+__global__ void grad_finish_kernel(FinishArgs a, int mode)
+{
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k == 0) {
+        double s = 0.0;
+        for (int c = 0; c < a.n_rows; ++c) s += a.loss_part[c];
+        s /= (double)a.B;
+        if (a.loss_f) *a.loss_f = (float)s;
+        if (a.loss_d) *a.loss_d = s;
+    }
+    if (k >= NPARAM) return;
+    float gk = 0.f;
+    for (int c = 0; c < a.n_rows; ++c) gk += a.part[(long long)c * NPARAM + k];
+    if (mode == 0) {
+        a.grad[k] = gk;
+        return;
+    }
+    const float mk = a.b1 * a.m[k] + (1.f - a.b1) * gk;
+    const float vk = a.b2 * a.v[k] + (1.f - a.b2) * gk * gk;
+    a.m[k] = mk;
+    a.v[k] = vk;
+    const float pk = a.p[k] - a.lr * (mk * a.c1) / (sqrtf(vk * a.c2) + a.eps);
+    a.p[k] = pk;
+    for (int l = 0; l < 4; ++l) {  // the parameter's BF16 weight entries or FP32 bias
+        const LayerDef L = layer_def(l);
+        if (k >= L.offW && k < L.offB) {
+            const int o = (int)((k - L.offW) / L.in), i = (int)((k - L.offW) % L.in);
+            const bf16 hv = __float2bfloat16_rn(pk);
+            a.W[l][o * L.in_p + i] = hv;
+            a.Wt[l][i * L.out_p + o] = hv;
+        } else if (k >= L.offB && k < L.offB + L.out) {
+            a.bias[l][k - L.offB] = pk;
+        }
+    }
+}
+
 struct mlp_handle {
     mlp_config cfg{};
     cudaStream_t stream = nullptr;
@@ -477,9 +715,9 @@ struct mlp_handle {
     bf16 *Z = nullptr, *Zt = nullptr;
     bf16 *H[3] = {}, *Ht[3] = {};
     float* OUT = nullptr;
-    bf16 *D[4] = {}, *Dt[4] = {};  // gradients w.r.t. pre-activations of layers 1..3, and the output
-    float* part = nullptr;         // split-K partials
-    double* loss_part = nullptr;
+    float* part = nullptr;         // [tr_rows][NPARAM] partial gradients of train_fused_kernel
+    int tr_rows = 0;               // its CTAs at most (one partial row each)
+    double* loss_part = nullptr;   // [tr_rows]
     double* loss_d = nullptr;
     float *center = nullptr, *half = nullptr;
     int* over_budget = nullptr;  // [MAX_BINS]
@@ -557,42 +795,61 @@ cudaError_t forward(mlp_handle* h, const float* x, int B)
     return cudaSuccess;
 }
 
-// Loss gradient and backpropagation into h->G (flat FP32 gradient).
-cudaError_t backward(mlp_handle* h, const float* target, const float* label, int B, float* loss_f, double* loss_d)
+// Loss, gradient (mode 0: into h->G) or gradient and Adam step (mode 1): the
+// fused training kernel over slabs of 64 rows, then the ordered reduction.
+cudaError_t fused_step(mlp_handle* h, const float* x, const float* target, const float* label, int B, int mode,
+                       float* loss_f, double* loss_d)
 {
-    const int Br = rows8(B), bb = h->bbuf;
-    const int nblk = (bb + 255) / 256;
-    loss_grad_kernel<<<nblk, 256, 0, h->stream>>>(h->OUT, target, label, B, bb, (float)(1.0 / h->cfg.sigma_scale),
-                                                   (float)h->cfg.lam, h->D[3], h->Dt[3], h->loss_part);
-    loss_finish_kernel<<<1, 32, 0, h->stream>>>(h->loss_part, nblk, B, loss_f, loss_d);
-    h->launches += 2;
-    for (int l = 3; l >= 0; --l) {
-        const LayerDef L = layer_def(l);
-        const bf16* xt = l == 0 ? h->Zt : h->Ht[l - 1];  // layer input, transposed [in_p][bb]
-        // weight gradient: dW[o][i] = sum_b D_l[b][o] X[b][i]
-        Epi ep{};
-        ep.out_f = h->part;
-        cudaError_t e = gemm<EPI_PARTIAL>(h, h->Dt[l], bb, xt, bb, L.out_p, L.in_p, Br, KSPLIT, ep);
-        if (e != cudaSuccess) return e;
-        const int S = (Br + KSPLIT - 1) / KSPLIT;
-        reduce_wgrad_kernel<<<(L.out * L.in + 255) / 256, 256, 0, h->stream>>>(h->part, S, L.out_p, L.in_p, L.out,
-                                                                                L.in, h->G + L.offW);
-        bias_grad_kernel<<<L.out, BIAS_THREADS, 0, h->stream>>>(h->Dt[l], bb, B, h->G + L.offB);
-        h->launches += 2;
-        if (l > 0) {
-            // D_{l-1} = (D_l W_l) * (1 - h_{l-1}^2)
-            Epi ed{};
-            ed.out_b = h->D[l - 1];
-            ed.out_t = h->Dt[l - 1];
-            ed.hprev = h->H[l - 1];
-            ed.ld_out = HID;
-            ed.ld_t = bb;
-            ed.rows_live = B;
-            ed.rows_buf = bb;
-            e = gemm<EPI_DTANH>(h, h->D[l], L.out_p, h->Wt[l], L.out_p, Br, L.in_p, L.out_p, L.out_p, ed);
-            if (e != cudaSuccess) return e;
-        }
+    TrainArgs ta{};
+    ta.x = x;
+    ta.target = target;
+    ta.label = label;
+    ta.B = B;
+    for (int l = 0; l < 4; ++l) {
+        ta.W[l] = h->W[l];
+        ta.Wt[l] = h->Wt[l];
+        ta.bias[l] = h->bias[l];
     }
+    ta.center = h->center;
+    ta.half = h->half;
+    ta.inv_scale = (float)(1.0 / h->cfg.sigma_scale);
+    ta.lam = (float)h->cfg.lam;
+    ta.part = h->part;
+    ta.loss_part = h->loss_part;
+    const int slabs = (B + TR_ROWS - 1) / TR_ROWS;
+    const int rows = slabs < h->tr_rows ? slabs : h->tr_rows;  // every CTA gets at least one slab
+    train_fused_kernel<<<rows, 128, TR_SMEM, h->stream>>>(ta);
+    h->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    FinishArgs fa{};
+    fa.part = h->part;
+    fa.loss_part = h->loss_part;
+    fa.n_rows = rows;
+    fa.B = B;
+    fa.grad = h->G;
+    fa.p = h->P;
+    fa.m = h->M;
+    fa.v = h->V;
+    if (mode == 1) {
+        h->adam_t++;
+        const double b1 = h->cfg.beta1, b2 = h->cfg.beta2;
+        fa.lr = (float)h->cfg.lr;
+        fa.b1 = (float)b1;
+        fa.b2 = (float)b2;
+        fa.eps = (float)h->cfg.eps;
+        fa.c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)h->adam_t)));
+        fa.c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)h->adam_t)));
+    }
+    for (int l = 0; l < 4; ++l) {
+        fa.W[l] = h->W[l];
+        fa.Wt[l] = h->Wt[l];
+        fa.bias[l] = h->bias[l];
+    }
+    fa.loss_f = loss_f;
+    fa.loss_d = loss_d;
+    grad_finish_kernel<<<(int)((NPARAM + 255) / 256), 256, 0, h->stream>>>(fa, mode);
+    h->launches++;
     return cudaGetLastError();
 }
 
@@ -649,7 +906,7 @@ lb_status mlp_create(const mlp_config* cfg, void* cuda_stream, mlp_handle** out)
     }
     h->bbuf = (cfg->max_batch + 63) / 64 * 64;
     const int bb = h->bbuf;
-    h->splits = (bb + KSPLIT - 1) / KSPLIT;
+    h->tr_rows = std::min(TR_MAX_CTAS, bb / TR_ROWS);
     if (e == cudaSuccess) e = alloc(h, &h->P, NPARAM);
     if (e == cudaSuccess) e = alloc(h, &h->M, NPARAM);
     if (e == cudaSuccess) e = alloc(h, &h->V, NPARAM);
@@ -664,19 +921,17 @@ lb_status mlp_create(const mlp_config* cfg, void* cuda_stream, mlp_handle** out)
     for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
         e = alloc(h, &h->H[l], (size_t)bb * HID);
         if (e == cudaSuccess) e = alloc(h, &h->Ht[l], (size_t)bb * HID);
-        if (e == cudaSuccess) e = alloc(h, &h->D[l], (size_t)bb * HID);
-        if (e == cudaSuccess) e = alloc(h, &h->Dt[l], (size_t)bb * HID);
     }
-    if (e == cudaSuccess) e = alloc(h, &h->D[3], (size_t)bb * NOUTP);
-    if (e == cudaSuccess) e = alloc(h, &h->Dt[3], (size_t)bb * NOUTP);
     if (e == cudaSuccess) e = alloc(h, &h->OUT, (size_t)bb * NOUTP);
-    if (e == cudaSuccess) e = alloc(h, &h->part, (size_t)h->splits * HID * HID);
-    if (e == cudaSuccess) e = alloc(h, &h->loss_part, (size_t)(bb + 255) / 256);
+    if (e == cudaSuccess) e = alloc(h, &h->part, (size_t)h->tr_rows * NPARAM);
+    if (e == cudaSuccess) e = alloc(h, &h->loss_part, (size_t)h->tr_rows);
     if (e == cudaSuccess) e = alloc(h, &h->loss_d, 1);
     if (e == cudaSuccess) e = alloc(h, &h->center, NIN);
     if (e == cudaSuccess) e = alloc(h, &h->half, NIN);
     if (e == cudaSuccess)  // the fused serving kernel keeps activations and weights in shared memory
         e = cudaFuncSetAttribute(serve_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SRV_SMEM);
+    if (e == cudaSuccess)  // and so does the fused training kernel
+        e = cudaFuncSetAttribute(train_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM);
     if (e == cudaSuccess) e = alloc(h, &h->over_budget, MAX_BINS);
     if (e == cudaSuccess) {
         float c[NIN], hr[NIN];
@@ -735,8 +990,7 @@ lb_status mlp_gradients(mlp_handle* h, const float* x, const float* target_stres
 {
     if (!h || !x || !target_stress || !label || !grad) return invalid("mlp: NULL handle or buffer");
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
-    cudaError_t e = forward(h, x, batch);
-    if (e == cudaSuccess) e = backward(h, target_stress, label, batch, nullptr, h->loss_d);
+    cudaError_t e = fused_step(h, x, target_stress, label, batch, 0, nullptr, h->loss_d);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad, h->G, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, h->stream);
     double l = 0.0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, h->loss_d, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -750,20 +1004,7 @@ lb_status mlp_train_step(mlp_handle* h, const float* x, const float* target_stre
 {
     if (!h || !x || !target_stress || !label) return invalid("mlp: NULL handle or buffer");
     if (check_batch(h, batch) != LB_OK) return LB_ERR_INVALID;
-    cudaError_t e = forward(h, x, batch);
-    if (e == cudaSuccess) e = backward(h, target_stress, label, batch, loss_dev, nullptr);
-    if (e == cudaSuccess) {
-        h->adam_t++;
-        const double b1 = h->cfg.beta1, b2 = h->cfg.beta2;
-        const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)h->adam_t)));
-        const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)h->adam_t)));
-        adam_kernel<<<(int)((NPARAM + 255) / 256), 256, 0, h->stream>>>(h->P, h->M, h->V, h->G, NPARAM,
-                                                                        (float)h->cfg.lr, (float)b1, (float)b2,
-                                                                        (float)h->cfg.eps, c1, c2);
-        h->launches++;
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = refresh(h);
+    const cudaError_t e = fused_step(h, x, target_stress, label, batch, 1, loss_dev, nullptr);
     return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }
 
