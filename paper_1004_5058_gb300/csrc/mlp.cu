@@ -528,6 +528,9 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
     const int g = lane >> 2, t4 = lane & 3, r0 = warp * 16;
     float* const prow = a.part + (long long)blockIdx.x * NPARAM;
     __shared__ double loss_w[4];
+    __shared__ float bias_s[3 * HID + 2];  // b1..b3 and the output layer's two
+    for (int e = tid; e < 3 * HID + 2; e += 128)
+        bias_s[e] = e < 3 * HID ? a.bias[e / HID][e % HID] : a.bias[3][e - 3 * HID];
     double loss_acc = 0.0;
     const int n_slabs = (a.B + TR_ROWS - 1) / TR_ROWS;
     for (int slab = blockIdx.x; slab < n_slabs; slab += gridDim.x) {
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         const int row = r0 + g + (r >= 2 ? 8 : 0), col = ni * 8 + 2 * t4 + (r & 1);
-                        const float v = b0 + row < a.B ? tanhf(acc[ni][r] + a.bias[l][col]) : 0.f;
+                        const float v = b0 + row < a.B ? tanhf(acc[ni][r] + bias_s[l * HID + col]) : 0.f;
                         out[row * TR_LD + col] = __float2bfloat16_rn(v);
                     }
             } else {
@@ -575,7 +578,7 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
                     for (int h2 = 0; h2 < 2; ++h2) {
                         const int row = r0 + g + 8 * h2, b = b0 + row;
                         if (b >= a.B) continue;
-                        const float y0 = acc[0][2 * h2] + a.bias[3][0], y1 = acc[0][2 * h2 + 1] + a.bias[3][1];
+                        const float y0 = acc[0][2 * h2] + bias_s[3 * HID], y1 = acc[0][2 * h2 + 1] + bias_s[3 * HID + 1];
                         const float t = a.target[b] * a.inv_scale, lab = a.label[b];
                         const float e = y0 - t;
                         loss_acc += (double)(e * e) + (double)a.lam * (double)bce_logits(y1, lab);
@@ -677,8 +680,17 @@ __global__ void grad_finish_kernel(FinishArgs a, int mode)
         if (a.loss_d) *a.loss_d = s;
     }
     if (k >= NPARAM) return;
-    float gk = 0.f;
-    for (int c = 0; c < a.n_rows; ++c) gk += a.part[(long long)c * NPARAM + k];
+    // eight interleaved sums (rows c = j mod 8), combined in a fixed tree: eight
+    // loads in flight per thread, the same order on every call
+    float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int c = 0;
+    for (; c + 8 <= a.n_rows; c += 8)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s8[j] += a.part[(long long)(c + j) * NPARAM + k];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (c + j < a.n_rows) s8[j] += a.part[(long long)(c + j) * NPARAM + k];
+    const float gk = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
     if (mode == 0) {
         a.grad[k] = gk;
         return;
