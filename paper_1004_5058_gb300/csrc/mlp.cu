@@ -383,6 +383,12 @@ constexpr int TR_MAX_CTAS = 304;     // persistent CTAs at most (two per SM), on
 // inputs, output gradient, three activations and one weight buffer: 90 KB, two CTAs per SM
 constexpr size_t TR_SMEM = sizeof(bf16) * (2 * TR_ROWS * TR_LDZ + 3 * TR_ROWS * TR_LD + HID * TR_LD);
 
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const bf16* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const bf16* p)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -412,25 +418,27 @@ struct TrainArgs {
 };
 
 // One warp's 16 x N product of its rows of `in` (K wide) with the staged weights
-// Ws [N][K]: acc[n-tile][4], K-steps of 16 in increasing order.
+// Ws [N][K]: acc[n-tile][4], K-steps of 16 in increasing order (NT even).  The
+// operand fragments come from ldmatrix: the A tile as four 8 x 8 matrices (rows
+// 0-7 | 8-15) x (k 0-7 | 8-15), two n-tiles of B per load.
 template <int NT>
 __device__ __forceinline__ void rows_times_weights(float (&acc)[NT][4], const bf16* in, int ld_in, int K,
-                                                   const bf16* Ws, int r0, int g, int t4)
+                                                   const bf16* Ws, int r0, int lane)
 {
 #pragma unroll
     for (int ni = 0; ni < NT; ++ni)
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc[ni][r] = 0.f;
+    const int j = lane >> 3, rr = lane & 7;
     for (int ks = 0; ks < K; ks += 16) {
-        const uint32_t a0 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g) * ld_in + ks + 2 * t4]);
-        const uint32_t a1 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g + 8) * ld_in + ks + 2 * t4]);
-        const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g) * ld_in + ks + 2 * t4 + 8]);
-        const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&in[(r0 + g + 8) * ld_in + ks + 2 * t4 + 8]);
+        uint32_t a[4];
+        ldsm_x4(a, in + (r0 + rr + (j & 1) * 8) * ld_in + ks + (j >> 1) * 8);
 #pragma unroll
-        for (int ni = 0; ni < NT; ++ni) {
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Ws[(ni * 8 + g) * TR_LD + ks + 2 * t4]);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Ws[(ni * 8 + g) * TR_LD + ks + 2 * t4 + 8]);
-            mma_bf16(acc[ni], a0, a1, a2, a3, b0, b1);
+        for (int np = 0; np < NT / 2; ++np) {
+            uint32_t b[4];  // (n 0-7, k 0-7 | 8-15), (n 8-15, k 0-7 | 8-15) of the n-tile pair
+            ldsm_x4(b, Ws + (np * 16 + rr + (j >> 1) * 8) * TR_LD + ks + (j & 1) * 8);
+            mma_bf16(acc[2 * np], a[0], a[1], a[2], a[3], b[0], b[1]);
+            mma_bf16(acc[2 * np + 1], a[0], a[1], a[2], a[3], b[2], b[3]);
         }
     }
 }
@@ -480,11 +488,23 @@ __device__ __forceinline__ void put_wgrad(float* row, const float (&acc)[MT][NT]
 #pragma unroll
         for (int ni = 0; ni < NT; ++ni)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int o = m0 + mi * 16 + g + (r >= 2 ? 8 : 0), i = n0 + ni * 8 + 2 * t4 + (r & 1);
+            for (int h = 0; h < 2; ++h) {  // rows g and g + 8: the pair (i, i + 1) of adjacent columns
+                const int o = m0 + mi * 16 + g + 8 * h, i = n0 + ni * 8 + 2 * t4;
                 if (o >= L.out || i >= L.in) continue;
                 float* p = row + L.offW + (long long)o * L.in + i;
-                *p = first ? acc[mi][ni][r] : *p + acc[mi][ni][r];
+                const float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+                if (i + 1 < L.in && ((L.offW + (long long)o * L.in + i) & 1) == 0) {  // one 8-byte access
+                    float2* p2 = reinterpret_cast<float2*>(p);
+                    if (first) {
+                        *p2 = make_float2(v0, v1);
+                    } else {
+                        const float2 q = *p2;
+                        *p2 = make_float2(q.x + v0, q.y + v1);
+                    }
+                } else {
+                    p[0] = first ? v0 : p[0] + v0;
+                    if (i + 1 < L.in) p[1] = first ? v1 : p[1] + v1;
+                }
             }
 }
 
@@ -505,7 +525,7 @@ __device__ __forceinline__ void back_rows(const bf16* D, int ldD, int K, const b
                                           int t4, int b0, int B)
 {
     float acc[NT][4];
-    rows_times_weights<NT>(acc, D, ldD, K, Wts, r0, g, t4);
+    rows_times_weights<NT>(acc, D, ldD, K, Wts, r0, (g << 2) | t4);
 #pragma unroll
     for (int ni = 0; ni < NT; ++ni)
 #pragma unroll
@@ -555,7 +575,7 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
             const int ld_in = l == 0 ? TR_LDZ : TR_LD, K = l == 0 ? KIN : HID;
             if (l < 3) {
                 float acc[HID / 8][4];
-                rows_times_weights<HID / 8>(acc, in, ld_in, K, Ws, r0, g, t4);
+                rows_times_weights<HID / 8>(acc, in, ld_in, K, Ws, r0, lane);
                 bf16* out = Hs + l * TR_ROWS * TR_LD;
 #pragma unroll
                 for (int ni = 0; ni < HID / 8; ++ni)
@@ -567,7 +587,7 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
                     }
             } else {
                 float acc[NOUTP / 8][4];
-                rows_times_weights<NOUTP / 8>(acc, in, ld_in, K, Ws, r0, g, t4);
+                rows_times_weights<NOUTP / 8>(acc, in, ld_in, K, Ws, r0, lane);
                 // the loss and its gradient: columns 0 (stress / scale) and 1 (logit) of
                 // n-tile 0 sit with the t4 == 0 lanes
                 for (int e = lane; e < 16 * TR_LDZ; e += 32)
@@ -669,9 +689,27 @@ struct FinishArgs {
     double* loss_d;
 };
 
-__global__ void grad_finish_kernel(FinishArgs a, int mode)
+constexpr int FIN_PARAMS = 64, FIN_SPLIT = 4;  // parameters per block, threads per parameter
+__global__ void __launch_bounds__(FIN_PARAMS * FIN_SPLIT) grad_finish_kernel(FinishArgs a, int mode)
 {
-    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // thread (q, j): parameter k = blockIdx.x * FIN_PARAMS + j, rows c = q, q + 4, ...
+    // in eight interleaved sums; the four quarters combine in a fixed order
+    const int j = threadIdx.x % FIN_PARAMS, q = threadIdx.x / FIN_PARAMS;
+    const long long k = (long long)blockIdx.x * FIN_PARAMS + j;
+    __shared__ float quarter[FIN_SPLIT][FIN_PARAMS];
+    if (k < NPARAM) {
+        float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int c = q;
+        for (; c + 7 * FIN_SPLIT < a.n_rows; c += 8 * FIN_SPLIT)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s8[u] += a.part[(long long)(c + u * FIN_SPLIT) * NPARAM + k];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c + u * FIN_SPLIT < a.n_rows) s8[u] += a.part[(long long)(c + u * FIN_SPLIT) * NPARAM + k];
+        quarter[q][j] = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+    }
+    __syncthreads();
+    if (q != 0) return;
     if (k == 0) {
         double s = 0.0;
         for (int c = 0; c < a.n_rows; ++c) s += a.loss_part[c];
@@ -680,17 +718,7 @@ __global__ void grad_finish_kernel(FinishArgs a, int mode)
         if (a.loss_d) *a.loss_d = s;
     }
     if (k >= NPARAM) return;
-    // eight interleaved sums (rows c = j mod 8), combined in a fixed tree: eight
-    // loads in flight per thread, the same order on every call
-    float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int c = 0;
-    for (; c + 8 <= a.n_rows; c += 8)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) s8[j] += a.part[(long long)(c + j) * NPARAM + k];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if (c + j < a.n_rows) s8[j] += a.part[(long long)(c + j) * NPARAM + k];
-    const float gk = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+    const float gk = (quarter[0][j] + quarter[1][j]) + (quarter[2][j] + quarter[3][j]);
     if (mode == 0) {
         a.grad[k] = gk;
         return;
@@ -860,7 +888,8 @@ cudaError_t fused_step(mlp_handle* h, const float* x, const float* target, const
     }
     fa.loss_f = loss_f;
     fa.loss_d = loss_d;
-    grad_finish_kernel<<<(int)((NPARAM + 255) / 256), 256, 0, h->stream>>>(fa, mode);
+    grad_finish_kernel<<<(int)((NPARAM + FIN_PARAMS - 1) / FIN_PARAMS), FIN_PARAMS * FIN_SPLIT, 0, h->stream>>>(fa,
+                                                                                                         mode);
     h->launches++;
     return cudaGetLastError();
 }
