@@ -22,7 +22,8 @@ The exchange only moves opaque messages.  A slab object provides
   get(part) -> message        put(part, message)        step()
   empty(part) -> a receive buffer of the message's size
 (SlabLattice below over the CUDA library; the tests also drive an FP64 oracle
-slab through the same exchange).
+slab through the same exchange).  StreamExchange is the one-device form without
+host waits: all slabs on one stream, preallocated message buffers.
 """
 from __future__ import annotations
 
@@ -130,19 +131,58 @@ class DistExchange:
         return self
 
 
+class StreamExchange:
+    """All slabs of a cell on one device and one CUDA stream: every message
+    packing, unpacking and time step is stream-ordered, so a step enqueues its
+    whole exchange without waiting on the host (the slabs must share the
+    stream: SlabLattice(..., stream=s) with one s).  Each slab keeps one
+    preallocated device buffer per message part."""
+
+    def __init__(self, slabs: Sequence, periodic: bool):
+        self.slabs = list(slabs)
+        self.periodic = periodic
+        streams = {s.lat.stream_ptr for s in self.slabs}
+        if len(streams) != 1:
+            raise ValueError("StreamExchange needs every slab on the same stream")
+        self.bufs = [{p: s.empty(p) for p in (EDGE_LO, EDGE_HI, FLOW_LO, FLOW_HI)} for s in self.slabs]
+
+    def _trade(self, lo: int, hi: int):
+        world = len(self.slabs)
+        links = [neighbours(self.periodic, r, world) for r in range(world)]
+        for s, b, (below, above) in zip(self.slabs, self.bufs, links):
+            if below is not None:
+                s.lat.slab_get(lo, b[lo].data_ptr())
+            if above is not None:
+                s.lat.slab_get(hi, b[hi].data_ptr())
+        for s, (below, above) in zip(self.slabs, links):
+            if below is not None:
+                s.lat.slab_put(lo, self.bufs[below][hi].data_ptr())  # what the slab below sent upwards
+            if above is not None:
+                s.lat.slab_put(hi, self.bufs[above][lo].data_ptr())  # what the slab above sent downwards
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            self._trade(EDGE_LO, EDGE_HI)
+            for s in self.slabs:
+                s.lat.step(1)
+            self._trade(FLOW_LO, FLOW_HI)
+        return self
+
+
 class SlabLattice:
     """A slab of the CUDA library (lb_create_slab) with its messages in torch
-    device buffers, for LocalExchange / DistExchange.  The library's copies run
-    on the handle's stream; get() waits for them and put() waits for the
-    current torch stream first, so messages may be handed to other streams,
-    handles or NCCL."""
+    device buffers, for LocalExchange / DistExchange / StreamExchange.  The
+    library's copies run on the handle's stream (`stream`: a torch stream or a
+    cudaStream_t address; default the library's own); get() waits for them and
+    put() waits for the current torch stream first, so messages may be handed
+    to other streams, handles or NCCL."""
 
-    def __init__(self, cells, y0: int, rows: int, precision: str = "fp32", device=None):
+    def __init__(self, cells, y0: int, rows: int, precision: str = "fp32", device=None, stream=None):
         import torch
         from .lattice import Lattice
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        self.lat = Lattice(cells, precision, slab=(y0, rows))
+        self.lat = Lattice(cells, precision, slab=(y0, rows), stream=stream)
         self.y0, self.rows = y0, rows
 
     def empty(self, part: int):

@@ -378,6 +378,58 @@ def two_time_flow_curve(L: int = 256, steps: int = 500000, every: int = 50, n_sp
     return out
 
 
+def slab_throughput(n: int = 4096, steps: int = 400, worlds=(2, 4, 8), precision: str = "fp32",
+                    u_wall: float = 1e-3, seed: int = 1004):
+    """One Couette cell of n x n as the whole cell and as `world` horizontal
+    slabs on this one device, all on one stream with the stream-ordered
+    exchange (slabs.StreamExchange): site updates per second of each, timed
+    with CUDA events around `steps` steps after a warm-up, and whether the slabs'
+    final populations equal the whole cell's bit for bit.  The slabs' kernels
+    are those of a multi-device split; what one device cannot show is the
+    transfer between devices."""
+    import torch
+    from .slabs import SlabLattice, StreamExchange, split_rows
+    cell = I.make_cell("paper", nx=n, ny=n, g_ab=0.405, bc=1, u_wall=u_wall)
+    ra, rb = I.random_fields(n, n, seed=seed)
+    ux, uy = I.couette_velocity(n, n, u_wall)
+    fields = (ra, rb, ux, uy)
+    stream = torch.cuda.Stream()
+
+    def timed(run):
+        run(10)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        run(steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) * 1e-3
+
+    out = {"n": n, "steps": steps, "precision": precision, "runs": []}
+    with Lattice([cell], precision, stream=stream) as lat:
+        lat.init_fields(*fields)
+        dt = timed(lambda k: lat.step(k))
+        whole = lat.get_populations()[0]
+        out["whole"] = {"seconds": dt, "mlups": n * n * steps / dt / 1e6, "kernel": lat.kernel()}
+    for world in worlds:
+        parts = split_rows(n, world)
+        slabs = [SlabLattice([cell], y0, rows, precision, stream=stream) for y0, rows in parts]
+        try:
+            for s_, (y0, rows) in zip(slabs, parts):
+                s_.lat.init_fields(*[a[:, y0:y0 + rows] for a in fields])
+            ex = StreamExchange(slabs, periodic=False)
+            dt = timed(lambda k: ex.step(k))
+            got = np.concatenate([s_.lat.get_populations()[0] for s_ in slabs], axis=2)
+            out["runs"].append({"world": world, "seconds": dt, "mlups": n * n * steps / dt / 1e6,
+                                "relative_to_whole": out["whole"]["seconds"] / dt,
+                                "launches_per_step": sum(s_.lat.kernel_launches for s_ in slabs) / (steps + 10),
+                                "bitwise_equal_to_whole": bool(np.array_equal(got, whole))})
+        finally:
+            for s_ in slabs:
+                s_.close()
+    return out
+
+
 MRT_CONFIGS = (("BGK, G_AB 0.30", 0.30, {}), ("MRT s_nu 1.6, G_AB 0.30", 0.30, {"s_nu": 1.6}),
                ("BGK, G_AB 0.405", 0.405, {}), ("MRT s_q 1.2, G_AB 0.405", 0.405, {"s_q": 1.2}))
 
@@ -497,7 +549,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["precision", "precision_mixed", "flow_curve", "flow_curve_sequential",
                                       "flow_curve_long", "couette_1024", "surrogate", "kolmogorov",
-                                      "kolmogorov_rho0", "two_time", "train_rate", "readings", "mrt"])
+                                      "kolmogorov_rho0", "two_time", "train_rate", "readings", "mrt", "slabs"])
     ap.add_argument("--batch", type=int, default=10240, help="train_rate: batch size")
     ap.add_argument("--quick", action="store_true", help="small sizes for a smoke run")
     ap.add_argument("--out", default="")
@@ -516,6 +568,8 @@ def main():
         r = flow_curve(L=128, steps=4000, n_speeds=4) if a.quick else flow_curve(steps=1000000, every=100)
     elif a.study == "two_time":  # relaxation time per species: flow curves for three tau_B
         r = two_time_flow_curve(L=64, steps=4000, n_speeds=4) if a.quick else two_time_flow_curve()
+    elif a.study == "slabs":  # one cell as slabs on this device, stream-ordered exchange
+        r = slab_throughput(n=256, steps=50, worlds=(2, 4)) if a.quick else slab_throughput()
     elif a.study == "mrt":  # multiple relaxation times beside BGK: Newtonian and demixing flow curves
         r = mrt_flow_curve(L=32, steps=4000, n_speeds=4) if a.quick else mrt_flow_curve()
     elif a.study == "readings":

@@ -144,3 +144,26 @@ def test_slabs_multiple_relaxation_times_bitwise(bc, world):
     whole, _, _ = run_whole(cell, "fp32", fields, 25)
     got, _, _ = run_slabs(cell, "fp32", fields, 25, world)
     assert np.array_equal(got, whole)
+
+
+@pytest.mark.parametrize("bc,world", [(0, 2), (0, 4), (1, 3)])
+def test_stream_exchange_equals_whole_cell_bitwise(bc, world):
+    """All slabs on one stream, the exchange stream-ordered (no host waits):
+    the same rows as the whole cell, bit for bit."""
+    import torch
+    from paper_1004_5058_gb300.slabs import SlabLattice, StreamExchange, split_rows
+    cell, ra, rb, ux, uy = setup(bc)
+    fields = (ra, rb, ux, uy)
+    whole, _, _ = run_whole(cell, "fp32", fields, 25)
+    stream = torch.cuda.Stream()
+    parts = split_rows(cell.ny, world)
+    slabs = [SlabLattice([cell], y0, rows, "fp32", stream=stream) for y0, rows in parts]
+    try:
+        for s, (y0, rows) in zip(slabs, parts):
+            s.lat.init_fields(*[a[:, y0:y0 + rows] for a in fields])
+        StreamExchange(slabs, periodic=bc == 0).step(25)
+        got = np.concatenate([s.lat.get_populations()[0] for s in slabs], axis=2)
+    finally:
+        for s in slabs:
+            s.close()
+    assert np.array_equal(got, whole)
