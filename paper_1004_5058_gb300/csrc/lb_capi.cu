@@ -605,11 +605,23 @@ lb_status lb_stage_fields(lb_handle* h, const double* rho_a, const double* rho_b
             return fail(h, LB_ERR_NOMEM, "lb_stage_fields: staging buffer: %s", cudaGetErrorString(e));
         }
     }
-    if (!h->copy_stream) {
-        CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
-        CK(h, cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming));
-        CK(h, cudaEventCreateWithFlags(&h->staging_read, cudaEventDisableTiming));
-        CK(h, cudaEventRecord(h->staging_read, h->stream));  // nothing has read it yet
+    if (!h->copy_stream) {  // all three or none, so a failed set-up leaves nothing half made
+        cudaStream_t cs = nullptr;
+        cudaEvent_t done = nullptr, read = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&read, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(read, h->stream);  // nothing has read the buffer yet
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (read) cudaEventDestroy(read);
+            if (done) cudaEventDestroy(done);
+            if (cs) cudaStreamDestroy(cs);
+            return fail(h, LB_ERR_CUDA, "lb_stage_fields: copy stream: %s", cudaGetErrorString(e));
+        }
+        h->copy_stream = cs;
+        h->staged = done;
+        h->staging_read = read;
     }
     // the buffer is free once the last equilibrium launch that reads it has run
     CK(h, cudaStreamWaitEvent(h->copy_stream, h->staging_read, 0));
