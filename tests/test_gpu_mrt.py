@@ -209,3 +209,46 @@ def test_checkpoint_carries_the_rates_and_reads_version_2(tmp_path):
         ref = d.get_populations()
     assert np.array_equal(got, ref)
     assert not np.array_equal(got, fa)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mrt_fp16_stochastic_rounding_keeps_mass(kernel):
+    """The multiple-relaxation-time collision in FP16 storage: over 3000 steps of
+    a near-uniform mixed state, stochastic rounding keeps the species masses to
+    2e-6 and well below round to nearest, and both stay close to the FP64 oracle
+    (the bounds of the BGK test)."""
+    cell = I.make_cell("paper", nx=64, ny=64, **RATES)
+    ra, rb = I.random_fields(64, 64, seed=21)
+    m0 = np.array([ra.sum(), rb.sum()])
+    (r,) = oracle_runs([cell], ra, rb, steps=3000)
+    oa = r.fields()[0]
+    drift, dev = {}, {}
+    for prec in ("fp16", "fp16sr"):
+        with lattice([cell], prec, kernel) as lat:
+            lat.init_fields(ra, rb).step(3000)
+            mass, _ = lat.reductions()
+            ga = lat.fields()[0]
+        drift[prec] = np.abs(mass[0] - m0) / m0
+        dev[prec] = max_abs(ga[0], oa)
+    assert np.all(drift["fp16sr"] <= 2e-6)
+    assert np.max(drift["fp16sr"]) < 0.2 * np.max(drift["fp16"])
+    assert dev["fp16sr"] <= 2e-3 and dev["fp16"] <= 2e-3
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mrt_kolmogorov_sine_start_against_oracle(kernel):
+    """The paper's Kolmogorov start (sine densities, 128^2) under the MRT
+    collision, 300 steps with the sampled line profile, FP64 against the oracle."""
+    L = 128
+    cell = I.make_cell("paper", nx=L, ny=L, g_ab=0.405, f0=I.kolmogorov_f0(0.1, L), **RATES)
+    ra, rb = I.sine_fields(L, L, noise=1e-3, seed=3)
+    with lattice([cell], "fp64", kernel) as lat:
+        lat.init_fields(ra, rb).set_sampling(100, 10).step(300)
+        ga, gb, gu, _ = lat.fields()
+        ub, ns = lat.profile()
+    (r,) = oracle_runs([cell], ra, rb, steps=300, sampling=(100, 10))
+    oa, ob, ou, _ = r.fields()
+    assert max_abs(ga[0], oa) <= 1e-12 and max_abs(gb[0], ob) <= 1e-12 and max_abs(gu[0], ou) <= 1e-12
+    _, _, _, oub = r.shear()
+    assert ns == 20
+    np.testing.assert_allclose(ub[0], oub, rtol=0, atol=1e-13)

@@ -686,3 +686,24 @@ def test_mrt_couette_linear_profile_and_stress(tau, rates):
     np.testing.assert_allclose(ub, U * (2 * (y + 0.5) / ny - 1), rtol=0, atol=1e-8 * U)
     assert S == pytest.approx(2 * U / ny, rel=1e-8)
     assert sigma == pytest.approx(1.2 * nu * 2 * U / ny, rel=1e-8)
+
+
+@pytest.mark.parametrize("tau,s_nu", [(1.0, 1.6), (0.8, 0.9)])
+def test_mrt_kolmogorov_laminar_amplitude(tau, s_nu):
+    """G = 0 Kolmogorov flow under multiple relaxation times: the laminar peak
+    speed is F0 / (rho nu k^2) with the stress moments' viscosity
+    nu = (1/s_nu - 1/2)/3, while tau (through j's rate and the force shift)
+    only carries the force in."""
+    ny = 64
+    k = 2 * math.pi / ny
+    nu = (1.0 / s_nu - 0.5) / 3.0
+    F0 = 1.2 * nu * k * k * 1e-3  # for a peak speed of 1e-3
+    c = I.make_cell("ideal", nx=4, ny=ny, tau=tau, f0=F0, s_nu=s_nu)
+    r = lb.Run(c, np.full((ny, 4), 0.6), np.full((ny, 4), 0.6))
+    t_relax = ny * ny / (nu * 4 * math.pi ** 2)
+    r.set_sampling(int(40 * t_relax), 10)
+    r.step(int(50 * t_relax))
+    _, _, _, ub = r.shear()
+    y = np.arange(ny)
+    amp = 2.0 / ny * np.sum(ub * np.sin(k * y))
+    assert amp == pytest.approx(1e-3, rel=2e-2)
