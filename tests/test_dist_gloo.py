@@ -224,3 +224,59 @@ def test_package_slab_exchange_in_process():
             LocalExchange(slabs, periodic=cell.bc == 0).step(8)
             got = np.concatenate([s.f[:, :, 2:rows + 2] for s, (_, rows) in zip(slabs, parts)], axis=2)
             assert np.array_equal(got, ref), (bc, world)
+
+
+class _PointerLattice:
+    """The pointer-level face of a slab handle (lb_slab_get / lb_slab_put into
+    buffers given by address, one step per call) over an oracle slab, for the
+    stream-ordered exchange, which moves messages between preallocated buffers."""
+
+    stream_ptr = 1  # every slab "on one stream"
+
+    def __init__(self, oslab):
+        self.o = oslab
+
+    def slab_get(self, part, ptr):
+        import ctypes
+        src = np.ascontiguousarray(self.o.f[self.o._where(part, False)])
+        ctypes.memmove(ptr, src.ctypes.data, src.nbytes)
+
+    def slab_put(self, part, ptr):
+        import ctypes
+        shape = self.o.f[self.o._where(part, True)].shape
+        n = int(np.prod(shape))
+        self.o.f[self.o._where(part, True)] = np.ctypeslib.as_array(
+            (ctypes.c_double * n).from_address(ptr)).reshape(shape)
+
+    def step(self, n):
+        assert n == 1
+        self.o.step()
+
+
+class _PointerSlab:
+    def __init__(self, oslab):
+        self.o, self.lat = oslab, _PointerLattice(oslab)
+
+    def empty(self, part):
+        return self.o.empty(part)
+
+
+def test_stream_exchange_pairs_messages_in_process():
+    """The one-device exchange without host waits (StreamExchange: one buffer per
+    slab and message part, gets of every slab first, then the puts from the
+    neighbours' buffers) over oracle slabs: equal to the whole-cell oracle bit for
+    bit, 2 to 4 slabs, periodic and Couette."""
+    from oracle import lb
+    from paper_1004_5058_gb300.slabs import StreamExchange, split_rows
+    from tests.test_oracle_slab import case
+    for bc in (0, 1):
+        cell, f0 = case(bc)
+        ref = f0
+        for _ in range(8):
+            ref, _, _ = lb.step(cell, ref)
+        for world in (2, 3, 4):
+            parts = split_rows(cell.ny, world)
+            oslabs = [_OracleSlab(cell, y0, rows, f0) for y0, rows in parts]
+            StreamExchange([_PointerSlab(o) for o in oslabs], periodic=cell.bc == 0).step(8)
+            got = np.concatenate([o.f[:, :, 2:rows + 2] for o, (_, rows) in zip(oslabs, parts)], axis=2)
+            assert np.array_equal(got, ref), (bc, world)
