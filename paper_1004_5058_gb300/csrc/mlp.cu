@@ -66,6 +66,17 @@ __device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, u
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// The hidden layers' activation, tanh, on the special-function unit
+// (tanh.approx.f32: relative error about 2^-11, a quarter of the BF16 rounding
+// the activation then takes).  Every kernel here uses it, so the layered
+// forward pass, serving and training compute one function.
+__device__ __forceinline__ float act_tanh(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // C[m][n] = sum_{k in split} A[m][k] B[n][k]; 64x64 tile per CTA, 4 warps of
 // 32x32, BK = 32.  K, the split chunk and both leading dimensions are multiples
 // of 8 (16-byte vector loads).
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(128) gemm_nt(const bf16* __restrict__ A, int l
                 if (row >= ep.rows_buf) continue;
                 const bool live = row < ep.rows_live;
                 if (EPI == EPI_TANH)
-                    v = live ? tanhf(v + ep.bias[col]) : 0.f;
+                    v = live ? act_tanh(v + ep.bias[col]) : 0.f;
                 else
                     v = live ? v + ep.bias[col] : 0.f;
                 if (EPI == EPI_OUT) {
@@ -319,7 +330,7 @@ __global__ void __launch_bounds__(128) serve_fused_kernel(ServeArgs a)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int row = r0 + g + (r >= 2 ? 8 : 0), col = ni * 8 + 2 * t4 + (r & 1);
-                    out[row * SRV_LD + col] = __float2bfloat16_rn(tanhf(acc[ni][r] + a.bias[l][col]));
+                    out[row * SRV_LD + col] = __float2bfloat16_rn(act_tanh(acc[ni][r] + a.bias[l][col]));
                 }
             __syncwarp();  // a warp reads back only its own rows
             bf16* t = in;
@@ -478,11 +489,11 @@ __device__ __forceinline__ void slab_outer(float (&acc)[MT][NT][4], const bf16* 
 
 // Adds (first slab: stores) a weight-gradient block to the CTA's partial row;
 // entries outside the live out x in block are skipped.
-template <int MT, int NT>
-__device__ __forceinline__ void put_wgrad(float* row, const float (&acc)[MT][NT][4], int l, int m0, int n0, int g,
-                                          int t4, bool first)
+template <int MT, int NT, int LS>
+__device__ __forceinline__ void put_wgrad(float* row, const float (&acc)[MT][NT][4], long long offW, int m0, int n0,
+                                          int g, int t4, bool first)
 {
-    const LayerDef L = layer_def(l);
+    constexpr LayerDef L = layer_def(LS);  // the block's shape; offW places it
 #pragma unroll
     for (int mi = 0; mi < MT; ++mi)
 #pragma unroll
@@ -491,9 +502,9 @@ __device__ __forceinline__ void put_wgrad(float* row, const float (&acc)[MT][NT]
             for (int h = 0; h < 2; ++h) {  // rows g and g + 8: the pair (i, i + 1) of adjacent columns
                 const int o = m0 + mi * 16 + g + 8 * h, i = n0 + ni * 8 + 2 * t4;
                 if (o >= L.out || i >= L.in) continue;
-                float* p = row + L.offW + (long long)o * L.in + i;
+                float* p = row + offW + (long long)o * L.in + i;
                 const float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
-                if (i + 1 < L.in && ((L.offW + (long long)o * L.in + i) & 1) == 0) {  // one 8-byte access
+                if (i + 1 < L.in && ((offW + (long long)o * L.in + i) & 1) == 0) {  // one 8-byte access
                     float2* p2 = reinterpret_cast<float2*>(p);
                     if (first) {
                         *p2 = make_float2(v0, v1);
@@ -567,7 +578,9 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
             if (b < a.B && c < NIN) v = (a.x[b * NIN + c] - a.center[c]) / a.half[c];
             Zs[r * TR_LDZ + c] = __float2bfloat16_rn(v);
         }
-        // ---- forward
+        // ---- forward.  One copy of each layer's code: a CTA runs the kernel's body
+        // once per slab, so its instruction fetches grow with the code's length
+#pragma unroll 1
         for (int l = 0; l < 4; ++l) {
             cp_async_wait<0>();
             __syncthreads();  // layer l's weights and inputs visible
@@ -582,7 +595,7 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         const int row = r0 + g + (r >= 2 ? 8 : 0), col = ni * 8 + 2 * t4 + (r & 1);
-                        const float v = b0 + row < a.B ? tanhf(acc[ni][r] + bias_s[l * HID + col]) : 0.f;
+                        const float v = b0 + row < a.B ? act_tanh(acc[ni][r] + bias_s[l * HID + col]) : 0.f;
                         out[row * TR_LD + col] = __float2bfloat16_rn(v);
                     }
             } else {
@@ -617,49 +630,43 @@ __global__ void __launch_bounds__(128, 2) train_fused_kernel(TrainArgs a)
         }
         // ---- backward, layer 4: dW4 (16 x 128) from D4 and H3, db4
         bf16* const H1 = Hs;
-        bf16* const H2 = Hs + TR_ROWS * TR_LD;
         bf16* const H3 = Hs + 2 * TR_ROWS * TR_LD;
         {
             float acc[1][4][4];
             slab_outer<1, 4>(acc, D4, TR_LDZ, 0, H3, TR_LD, warp * 32, lane);
-            put_wgrad<1, 4>(prow, acc, 3, 0, warp * 32, g, t4, first);
+            put_wgrad<1, 4, 3>(prow, acc, OFF_W4, 0, warp * 32, g, t4, first);
             put_bgrad(prow, D4, TR_LDZ, 3, tid, first);
         }
         cp_async_wait<0>();  // Wt4
         __syncthreads();     // H3 read by every warp's dW4; Wt4 visible
         back_rows<HID / 8>(D4, TR_LDZ, NOUTP, Ws, H3, r0, g, t4, b0, a.B);  // D3 over H3
         __syncthreads();  // D3 complete; the weight buffer is free
-        stage_matrix(Ws, a.Wt[2], HID, HID, tid);  // Wt3
-        cp_async_commit();
-        // layer 3: dW3 from D3 and H2, then D2 over H2
-        {
-            float acc[2][HID / 8][4];
-            slab_outer<2, HID / 8>(acc, H3, TR_LD, warp * 32, H2, TR_LD, 0, lane);
-            put_wgrad<2, HID / 8>(prow, acc, 2, warp * 32, 0, g, t4, first);
-            put_bgrad(prow, H3, TR_LD, 2, tid, first);
+        // layers 3 and 2 (index l = 2, 1) share one copy of the code: dW_l from D_l
+        // (over H_l) and H_{l-1}, then D_{l-1} over H_{l-1} with Wt_l
+        static_assert(layer_def(1).in == layer_def(2).in && layer_def(1).out == layer_def(2).out,
+                      "the two hidden-to-hidden layers have one shape");
+#pragma unroll 1
+        for (int l = 2; l >= 1; --l) {
+            bf16* const Dl = Hs + l * TR_ROWS * TR_LD;
+            bf16* const Hp = Hs + (l - 1) * TR_ROWS * TR_LD;
+            stage_matrix(Ws, a.Wt[l], HID, HID, tid);
+            cp_async_commit();
+            {
+                float acc[2][HID / 8][4];
+                slab_outer<2, HID / 8>(acc, Dl, TR_LD, warp * 32, Hp, TR_LD, 0, lane);
+                put_wgrad<2, HID / 8, 1>(prow, acc, layer_def(l).offW, warp * 32, 0, g, t4, first);
+                put_bgrad(prow, Dl, TR_LD, l, tid, first);
+            }
+            cp_async_wait<0>();  // Wt_l
+            __syncthreads();
+            back_rows<HID / 8>(Dl, TR_LD, HID, Ws, Hp, r0, g, t4, b0, a.B);
+            __syncthreads();
         }
-        cp_async_wait<0>();  // Wt3
-        __syncthreads();
-        back_rows<HID / 8>(H3, TR_LD, HID, Ws, H2, r0, g, t4, b0, a.B);  // D2 over H2
-        __syncthreads();
-        stage_matrix(Ws, a.Wt[1], HID, HID, tid);  // Wt2
-        cp_async_commit();
-        // layer 2: dW2 from D2 and H1, then D1 over H1
-        {
-            float acc[2][HID / 8][4];
-            slab_outer<2, HID / 8>(acc, H2, TR_LD, warp * 32, H1, TR_LD, 0, lane);
-            put_wgrad<2, HID / 8>(prow, acc, 1, warp * 32, 0, g, t4, first);
-            put_bgrad(prow, H2, TR_LD, 1, tid, first);
-        }
-        cp_async_wait<0>();  // Wt2
-        __syncthreads();
-        back_rows<HID / 8>(H2, TR_LD, HID, Ws, H1, r0, g, t4, b0, a.B);  // D1 over H1
-        __syncthreads();
         // layer 1: dW1 (128 x 16) from D1 and the inputs
         {
             float acc[2][KIN / 8][4];
             slab_outer<2, KIN / 8>(acc, H1, TR_LD, warp * 32, Zs, TR_LDZ, 0, lane);
-            put_wgrad<2, KIN / 8>(prow, acc, 0, warp * 32, 0, g, t4, first);
+            put_wgrad<2, KIN / 8, 0>(prow, acc, OFF_W1, warp * 32, 0, g, t4, first);
             put_bgrad(prow, H1, TR_LD, 0, tid, first);
         }
     }
