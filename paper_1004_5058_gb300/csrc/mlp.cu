@@ -66,10 +66,12 @@ __device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, u
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// The hidden layers' activation, tanh, on the special-function unit
-// (tanh.approx.f32: relative error about 2^-11, a quarter of the BF16 rounding
-// the activation then takes).  Every kernel here uses it, so the layered
-// forward pass, serving and training compute one function.
+// tanh on the special-function unit (tanh.approx.f32: relative error about
+// 2^-11, a quarter of the BF16 rounding the activation then takes), for the
+// training kernel's forward pass.  There its one instruction keeps the kernel's
+// code short (a CTA runs the body once, so the code's length is fetch time);
+// serving and the layered pass, whose bodies are short anyway, measured faster
+// with tanhf and keep it.
 __device__ __forceinline__ float act_tanh(float x)
 {
     float y;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(128) gemm_nt(const bf16* __restrict__ A, int l
                 if (row >= ep.rows_buf) continue;
                 const bool live = row < ep.rows_live;
                 if (EPI == EPI_TANH)
-                    v = live ? act_tanh(v + ep.bias[col]) : 0.f;
+                    v = live ? tanhf(v + ep.bias[col]) : 0.f;
                 else
                     v = live ? v + ep.bias[col] : 0.f;
                 if (EPI == EPI_OUT) {
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(128) serve_fused_kernel(ServeArgs a)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int row = r0 + g + (r >= 2 ? 8 : 0), col = ni * 8 + 2 * t4 + (r & 1);
-                    out[row * SRV_LD + col] = __float2bfloat16_rn(act_tanh(acc[ni][r] + a.bias[l][col]));
+                    out[row * SRV_LD + col] = __float2bfloat16_rn(tanhf(acc[ni][r] + a.bias[l][col]));
                 }
             __syncwarp();  // a warp reads back only its own rows
             bf16* t = in;
@@ -716,15 +718,21 @@ __global__ void __launch_bounds__(FIN_PARAMS * FIN_SPLIT) grad_finish_kernel(Fin
         quarter[q][j] = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
     }
     __syncthreads();
-    if (q != 0) return;
-    if (k == 0) {
+    if (blockIdx.x == 0 && q == 1 && j < 32) {
+        // the loss, by one otherwise idle warp: lane sums over rows lane, lane + 32, ...,
+        // then a butterfly over the lanes (a fixed order, so the same every call)
         double s = 0.0;
-        for (int c = 0; c < a.n_rows; ++c) s += a.loss_part[c];
-        s /= (double)a.B;
-        if (a.loss_f) *a.loss_f = (float)s;
-        if (a.loss_d) *a.loss_d = s;
+        for (int c = j; c < a.n_rows; c += 32) s += a.loss_part[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (j == 0) {
+            s /= (double)a.B;
+            if (a.loss_f) *a.loss_f = (float)s;
+            if (a.loss_d) *a.loss_d = s;
+        }
+        return;
     }
-    if (k >= NPARAM) return;
+    if (q != 0 || k >= NPARAM) return;
     const float gk = (quarter[0][j] + quarter[1][j]) + (quarter[2][j] + quarter[3][j]);
     if (mode == 0) {
         a.grad[k] = gk;
