@@ -65,6 +65,42 @@ def test_null_and_invalid_arguments_rejected_before_device_work(lib):
     lib.mlp_destroy(None)
 
 
+def test_every_handle_call_refuses_a_null_handle(lib):
+    """Each call that takes a handle, given NULL (and zeros or NULLs for the
+    rest), returns LB_ERR_INVALID before any device work; the queries return
+    their documented neutral values and the destructors do nothing."""
+    from paper_1004_5058_gb300 import _lib as L
+    neutral = {"lb_steps_done": 0, "lb_kernel_launches": 0, "mlp_kernel_launches": 0, "lb_stream": None,
+               "lb_destroy": None, "mlp_destroy": None}
+    seen = 0
+    for name, (res, args) in L.SIGNATURES.items():
+        if not args or args[0] is not L._H:
+            continue  # creators, the fit and the handle-free reduction take no handle
+        zeros = [0.0 if a is C.c_double else 0 if a in (C.c_int, C.c_longlong) else None for a in args[1:]]
+        got = getattr(lib, name)(None, *zeros)
+        if name == "lb_last_error":
+            assert got, name  # a static message
+        elif name in neutral:
+            assert got == neutral[name], (name, got)
+        else:
+            assert got == L.LB_ERR_INVALID, (name, got)
+        seen += 1
+    assert seen >= 35
+
+
+def test_slab_geometry_rejected_before_device_work(lib):
+    """lb_create_slab refuses rows that do not fit the cell (and periodic slabs
+    too tall for their four ghost rows) before touching a device."""
+    from paper_1004_5058_gb300 import _lib as L
+    h = L._H()
+    cell = L.lb_cell_params(64, 32, 1.0, 0.83, -9, 8.1, -8, 7.1, 0.045, 0, 0, 0.6, 0.6, 0)
+    for y0, rows in ((0, 1), (-1, 8), (28, 8), (0, 29)):  # too few rows, outside, past the top, no room for ghosts
+        assert lib.lb_create_slab(C.byref(cell), 1, 0, y0, rows, None, C.byref(h)) == L.LB_ERR_INVALID, (y0, rows)
+        assert not h.value
+        assert b"lb_create_slab" in lib.lb_last_error(None)
+    assert lib.lb_create_slab(C.byref(cell), 1, 0, 0, -3, None, C.byref(h)) == L.LB_ERR_INVALID
+
+
 def test_hb_fit_recovers_noiseless_law(lib):
     from paper_1004_5058_gb300 import hb_fit
     S = np.logspace(-5, -2, 16)
